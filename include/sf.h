@@ -1,0 +1,209 @@
+/*
+ * sf.h -- C ABI of libsf, a B300 (sm_103a) implementation of the per-frame
+ * predictor-update loop of "Real-time Structure Flow" (Adarve & Mahony,
+ * arXiv 2406.18031, Sec. 4 and Fig. 3).
+ *
+ * The filter estimates, at every pixel, the structure flow w (the scene's
+ * 3-D velocity relative to the camera scaled by inverse range, rad/s;
+ * Sec. 3.1, Eq. 10) and the inverse depth rho = lambda_ref / lambda (Eq. 8)
+ * from a stream of grayscale images and range maps.  Each frame:
+ *   prediction   -- upwind finite-difference transport of the previous
+ *                   state over N sub-iterations (Sec. 4.4, Sec. 4.6);
+ *   update       -- brightness and inverse-depth model fits (Sec. 4.2,
+ *                   4.3), a per-pixel 3x3 least-squares solve (Sec. 4.5,
+ *                   Eqs. 42-50), inverse-depth blend (Eq. 52) and 5x5
+ *                   smoothing, on every level of an image pyramid;
+ *   reconstruct  -- w_h = up(w_{h+1}) + dw_h down to full resolution
+ *                   (Eq. 26).
+ *
+ * Conventions
+ *   - Images are H x W, row-major, contiguous float32.  Pixel (i, j) is row
+ *     i, column j.  The camera is a pinhole (fx, fy, cx, cy in pixels); the
+ *     ray of pixel (i, j) passes through ((j + 0.5 - cx)/fx, (i + 0.5 -
+ *     cy)/fy, 1).  Level h (1 = full resolution) is the pinhole grid with
+ *     the intrinsics divided by 2^(h-1).
+ *   - All pointers marked "device" must be CUDA device (or managed) memory
+ *     on the current device; "host" pointers are ordinary host memory
+ *     (pinned memory makes the copies asynchronous).  The library never
+ *     frees memory it did not allocate.
+ *   - Every call returns SF_OK (0), a negative error code, or a positive
+ *     warning.  Nothing throws across the ABI.  Calls that take a stream
+ *     enqueue work on it and return without waiting unless stated.
+ *   - Calls on one context must not run concurrently from several host
+ *     threads; different contexts are independent.
+ */
+#ifndef SF_H
+#define SF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SF_MAX_LEVELS 4
+
+/* return codes */
+#define SF_OK 0
+#define SF_EINVAL (-1)      /* invalid argument or configuration            */
+#define SF_ENOMEM (-2)      /* device or host allocation failed             */
+#define SF_ECUDA (-3)       /* a CUDA runtime call failed                   */
+#define SF_ETIMEOUT (-4)    /* a bounded device wait gave up                */
+#define SF_ENONFINITE (-5)  /* the state became NaN or infinite             */
+#define SF_WARN_CFL 1       /* a prediction broke dt*max|speed| <= 1 (Eq. 67) */
+
+/* sf_params.flags */
+#define SF_DOMINANT_LITERAL 1 /* dominant speed = neighbour of SMALLER |u|, the
+                                 literal text of Eqs. 55-56 (default: larger) */
+#define SF_SOURCE_SPLIT 2     /* apply the source term -f<eta,w> with dt/2 in
+                                 each axis pass (once per sub-iteration, as in
+                                 Eq. 53) instead of dt in both printed passes */
+#define SF_CHECK_CFL 4        /* record SF_WARN_CFL when Eq. 67 is violated   */
+#define SF_CHECK_FINITE 8     /* record SF_ENONFINITE for NaN/Inf output flow */
+
+typedef struct sf_params {
+    float fx, fy, cx, cy;          /* level-1 pinhole intrinsics, pixels              */
+    int iters[SF_MAX_LEVELS];      /* N_h, propagation sub-iterations of level h (index
+                                      0 = level 1); 0 selects ceil(max_flow / 2^(h-1)) */
+    float max_flow;                /* largest expected flow, px/frame at level 1      */
+    int smooth_iters[SF_MAX_LEVELS]; /* S_h, 5x5 smoothing passes after each solve    */
+    float gamma[5];                /* gains gamma1..gamma5 of Eqs. 42, 47, 51; the
+                                      prior weight of level h is gamma[2] * (2^(h-1)/fx)^2 */
+    float lambda_ref;              /* reference range of Eq. 8, metres (1.0)          */
+    int flags;                     /* SF_* flags above                                */
+} sf_params;
+
+typedef struct sf_ctx sf_ctx;      /* opaque; owns all device state of one stream     */
+
+/* Fill *p with defaults for an H x W image with `levels` pyramid levels:
+ * fx = fy = W/2 (90 degree field of view), principal point at the centre,
+ * max_flow = 1, iters = 0 (derive from max_flow), smooth = 2 at level 1 and
+ * 4 above (Tables 2-4), gamma = (1, 1, 1e-2, 1, 1), lambda_ref = 1,
+ * flags = SF_CHECK_CFL.  Returns SF_EINVAL for a NULL pointer. */
+int sf_params_default(sf_params* p, int H, int W, int levels);
+
+/* Create a filter for H x W frames with `levels` levels (1..SF_MAX_LEVELS = 4;
+ * the coarse levels are built on the fly, 4^(h-1) input reads per pixel).
+ * H and W must be divisible by 2^(levels-1); every level must be at least
+ * 8 x 8.  Allocates all device state on the current device (about 128 bytes
+ * per level-1 pixel, the coarser levels adding a third).  *out receives the
+ * context; on error *out is NULL. */
+int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out);
+
+/* Forget the state: the next sf_step initialises (Sec. 5.2: zero initial
+ * flow) and returns zero flow. */
+int sf_reset(sf_ctx* c);
+
+/* One frame k -> k+1 on `stream` (a cudaStream_t; NULL = legacy default).
+ *   image        device, H x W float32, brightness (any affine scale; [0, 1] typical)
+ *   range        device, H x W float32, range lambda along the ray in metres;
+ *                lambda <= 0, NaN or Inf means "no measurement" at that pixel
+ *   dt           frame time in seconds (> 0); a change of dt between frames
+ *                rescales the state, which is kept in rad/frame
+ *   flow_out     device, 3 x H x W float32 (x, y, z planes) structure flow in
+ *                rad/s, or NULL
+ *   invdepth_out device, H x W float32 inverse depth, or NULL
+ * Inputs must stay valid, and outputs untouched, until the stream reaches
+ * the step.  Asynchronous: no host synchronisation. */
+int sf_step(sf_ctx* c, const float* image, const float* range, float dt,
+            float* flow_out, float* invdepth_out, void* stream);
+
+/* sf_step on HOST buffers: copies image and range to the device, runs the
+ * step and copies the outputs back, all on `stream`, then waits for the
+ * stream.  Pinned host buffers make the copies run at full speed. */
+int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt,
+                 float* flow_out, float* invdepth_out, void* stream);
+
+/* Synchronise the device and return the sticky status recorded since the
+ * last call (and clear it): SF_ENONFINITE, then SF_WARN_CFL, else SF_OK. */
+int sf_status(sf_ctx* c);
+
+/* Checkpoint access to level h (0-based) on `stream`.  dst/src are device
+ * buffers of 8 x H_h x W_h float32 planes: w (3), rho, dw (3), Y-hat.  At
+ * the top level w is the state; below it w is the reconstructed flow.
+ * Flow planes are in rad/frame at frame time *dt_prev (get: written if not
+ * NULL; set: read, must be > 0).  sf_set_state marks the context as
+ * initialised. */
+int sf_get_state(sf_ctx* c, int level, float* dst, float* dt_prev, void* stream);
+int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* stream);
+
+/* Number of kernel launches one sf_step enqueues after the first frame (the
+ * propagation launches, the update launch and the reconstruction
+ * launches); a negative code for a NULL context. */
+int sf_kernels_per_step(const sf_ctx* c);
+
+/* Per-launch device timing.  sf_profile(c, 1) makes every following sf_step
+ * record a CUDA event pair around each of its kernel launches, on the
+ * step's stream; sf_profile(c, 0) stops it.  sf_profile_read waits for the
+ * recorded work, writes for each launch slot of a step (the propagation
+ * launches, the update, the reconstruction launches; n slots at most) the
+ * summed milliseconds into ms[slot] and the number of timed launches into
+ * *count, forgets the records, and returns the number of slots. */
+int sf_profile(sf_ctx* c, int enable);
+int sf_profile_read(sf_ctx* c, float* ms, int* count, int n);
+
+/* Release everything the context owns.  NULL is a no-op. */
+void sf_destroy(sf_ctx* c);
+
+/* Static description of a return code. */
+const char* sf_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points.  Each runs one stage of the frame on caller-owned
+ * device buffers with the same kernels that sf_step uses, so that every
+ * stage can be checked on its own.  They upload a small launch descriptor
+ * and wait for `stream` once to do so; the kernels themselves stay
+ * asynchronous.  State planes are interleaved
+ * H x W x 4 float32 ("float4"): s0 = (w_x, w_y, w_z, rho), s1 = (dw_x, dw_y,
+ * dw_z, Y).  w and dw are in rad/frame.
+ * ---------------------------------------------------------------------- */
+
+typedef struct sf_grid {
+    int H, W;                /* level size                                   */
+    float fx, fy, cx, cy;    /* level intrinsics (level-1 values / 2^(h-1))  */
+} sf_grid;
+
+/* Prediction of one level (Sec. 4.4, Sec. 4.6, Eqs. 53-66): N sub-iterations
+ * with dt = 1/N.  Top level: s1_in and s1_out are NULL; w and rho are
+ * transported by w (Eqs. 36-37).  Lower level: w, dw, rho and Y are
+ * transported by w (Eqs. 38-41).  wscale multiplies w and dw on load (frame
+ * time change).  status (device int, may be NULL) receives bit 1 when
+ * Eq. 67 is violated.  Inputs and outputs must not overlap.  When N is
+ * larger than one launch can fuse, the sub-iterations are split over several
+ * launches that pass the fields through stream-ordered scratch memory
+ * (cudaMallocAsync). */
+int sf_propagate(const sf_grid* g, int N, int flags, float wscale,
+                 const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
+                 int* status, void* stream);
+
+/* Update of one level (Sec. 4.2, 4.3, 4.5; Eqs. 30-34, 42-52) with S
+ * smoothing passes.  `level` is 1-based; the level's image and inverse
+ * depth are built from the level-1 inputs (H1 x W1 device arrays) by 2x2
+ * means (no-measurement children excluded from the depth mean).
+ *   top: the unknown is w (prior p0.xyz; temporal terms use Y-hat = s1_cur.w
+ *        and rho = s0_cur.w); writes s0_new = (w, rho), s1_new = (0, Y-hat).
+ *   lower: the unknown is dw (prior p1.xyz; temporal terms use p1.w and
+ *        p0.w); writes s1_new = (dw, Y-hat) and s0_new.w = rho; s0_new.xyz is
+ *        left for sf_reconstruct.
+ *   init != 0: the first frame (w = dw = 0, rho = rho-hat, Y-hat = model);
+ *        s0_cur, s1_cur, p0, p1 are not read.
+ * gamma[2] is the level's prior weight as used (already scaled).  diag (may
+ * be NULL): H x W x 12 float32 per pixel: Y-hat, d_eta Y-hat (3), rho-hat
+ * (0 = none), d_eta rho-hat (3), unsmoothed solution (3), 0. */
+int sf_update(const sf_grid* g, int level, int top, int S, int init, const float* gamma,
+              float lambda_ref, const float* image, const float* range, int H1, int W1,
+              const float* s0_cur, const float* s1_cur, const float* p0, const float* p1,
+              float* s0_new, float* s1_new, float* diag, void* stream);
+
+/* Reconstruction (Eq. 26) of levels < top from new states: for h = top-1 ..
+ * 1, w_h = bilinear x2 up(w_{h+1}) + dw_h written to s0[h].xyz; then the
+ * outputs of level 1: flow_out = w_1 / dt (3 x H x W) and invdepth_out =
+ * rho_1, either may be NULL.  s0[h], s1[h] are the levels' device planes
+ * (index 0 = level 1); grids[h] their sizes.  status bit 2 (device int, may
+ * be NULL) is set when check_finite and a flow value is not finite. */
+int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const float* const* s1,
+                   float dt, float* flow_out, float* invdepth_out, int check_finite,
+                   int* status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H */

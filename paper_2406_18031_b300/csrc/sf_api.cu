@@ -1,0 +1,717 @@
+// sf_api.cu -- host side of libsf: contexts, launch plans and the C ABI of
+// include/sf.h.  All device work is issued on the caller's stream; nothing
+// here synchronises except sf_status, sf_step_host and the checkpoint calls'
+// own documented waits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sf.h"
+#include "sf_kernels.cuh"
+
+using namespace sfdev;
+
+namespace {
+
+// tile shapes and the largest number of sub-iterations fused in one launch
+constexpr int kPropTX = 32, kPropTY = 32;
+constexpr int kNfMaxLower = 8;   // 48 x 48 region x 72 B = 166 KB of shared memory
+constexpr int kNfMaxTop = 12;    // 56 x 56 region x 40 B = 125 KB
+constexpr int kUpdTX = 32, kUpdTY = 32;
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+Grid make_grid(const sf_grid& s)
+{
+    Grid g;
+    g.H = s.H;
+    g.W = s.W;
+    g.ax = 1.0f / s.fx;
+    g.bx = (0.5f - s.cx) / s.fx;
+    g.ay = 1.0f / s.fy;
+    g.by = (0.5f - s.cy) / s.fy;
+    g.a = 1.0f / s.fx;
+    return g;
+}
+
+int set_smem_attr(const void* fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return SF_OK;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return SF_ECUDA;
+    return SF_OK;
+}
+
+int last_error()
+{
+    return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+// A launch of k_propagate or k_update: device copies of its jobs and work list.
+struct Plan {
+    void* jobs = nullptr;     // device PropJob[] or UpdJob[]
+    int4* work = nullptr;     // device work items (job, tile row, tile col, 0)
+    int nwork = 0;
+    size_t smem = 0;
+    bool c8 = false;          // propagate: any 8-channel job (all jobs share one instantiation)
+};
+
+template <class Job>
+int upload_plan(const std::vector<Job>& jobs, const std::vector<int4>& work, Plan& p, cudaStream_t st)
+{
+    p.nwork = (int)work.size();
+    if (cudaMalloc(&p.jobs, jobs.size() * sizeof(Job)) != cudaSuccess) return SF_ENOMEM;
+    if (cudaMalloc(&p.work, work.size() * sizeof(int4)) != cudaSuccess) return SF_ENOMEM;
+    if (cudaMemcpyAsync(p.jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SF_ECUDA;
+    if (cudaMemcpyAsync(p.work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SF_ECUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+void free_plan(Plan& p)
+{
+    cudaFree(p.jobs);
+    cudaFree(p.work);
+    p = Plan();
+}
+
+void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
+{
+    for (int ty = 0; ty < H; ty += TY)
+        for (int tx = 0; tx < W; tx += TX) work.push_back(make_int4(job, ty, tx, 0));
+}
+
+int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
+{
+    if (p.nwork == 0) return SF_OK;
+    if (p.c8) {
+        if (set_smem_attr((const void*)k_propagate<true>, p.smem)) return SF_ECUDA;
+        k_propagate<true><<<p.nwork, kThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
+                                                             status, kPropTX, kPropTY);
+    } else {
+        if (set_smem_attr((const void*)k_propagate<false>, p.smem)) return SF_ECUDA;
+        k_propagate<false><<<p.nwork, kThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
+                                                              status, kPropTX, kPropTY);
+    }
+    return last_error();
+}
+
+int launch_update(const Plan& p, const UpdArgs& a, cudaStream_t st)
+{
+    if (p.nwork == 0) return SF_OK;
+    if (set_smem_attr((const void*)k_update, p.smem)) return SF_ECUDA;
+    k_update<<<p.nwork, kThreads, p.smem, st>>>((const UpdJob*)p.jobs, p.work, a, kUpdTX, kUpdTY);
+    return last_error();
+}
+
+int launch_reconstruct(const ReconArgs& a, cudaStream_t st)
+{
+    const int n = a.H * a.W;
+    const int blocks = std::min(ceil_div(n, kThreads), 148 * 8);
+    k_reconstruct<<<blocks, kThreads, 0, st>>>(a);
+    return last_error();
+}
+
+size_t upd_smem(int S)
+{
+    size_t a, b, c, total;
+    upd_layout(kUpdTX, kUpdTY, S, &a, &b, &c, &total);
+    return total;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// context
+// ----------------------------------------------------------------------------
+
+struct sf_level_state {
+    sf_grid grid;
+    int N, S;
+    float gamma[5];       // gamma[2] scaled for this level
+    float4* s0[2];        // state, double buffered by frame parity
+    float4* s1[2];
+    float4* p0;           // prediction k+
+    float4* p1;
+    float4* t0;           // intermediate fields between propagation launches
+    float4* t1;
+    void* block;          // single allocation holding the eight planes
+};
+
+struct sf_ctx {
+    int H, W, L;
+    sf_params p;
+    int parity;
+    int initialised;
+    float dt_prev;
+    int* status;                 // device status word
+    sf_level_state lv[SF_MAX_LEVELS];
+    std::vector<Plan> prop;      // one per propagation launch of a frame
+    Plan upd;
+    Plan init;
+    // per-launch profiling (sf_profile)
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev_pool;   // pairs, reused after sf_profile_read
+    std::vector<int> ev_slot;           // slot of each recorded pair
+    size_t ev_used = 0;
+    // staging for sf_step_host
+    float* stage_image = nullptr;
+    float* stage_range = nullptr;
+    float* stage_flow = nullptr;
+    float* stage_inv = nullptr;
+};
+
+namespace {
+
+void destroy_ctx(sf_ctx* c)
+{
+    if (!c) return;
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& pl : c->prop) free_plan(pl);
+    free_plan(c->upd);
+    free_plan(c->init);
+    for (int h = 0; h < c->L; ++h) cudaFree(c->lv[h].block);
+    cudaFree(c->status);
+    cudaFree(c->stage_image);
+    cudaFree(c->stage_range);
+    cudaFree(c->stage_flow);
+    cudaFree(c->stage_inv);
+    delete c;
+}
+
+int build_plans(sf_ctx* c, cudaStream_t st)
+{
+    const int L = c->L;
+    // ---- propagation: level h runs ceil(N_h / nfmax) launches; launch k holds
+    // segment k of every level that has one.  The last segment writes the
+    // prediction planes, earlier ones alternate so that this holds.
+    int nseg[SF_MAX_LEVELS], maxseg = 0;
+    for (int h = 0; h < L; ++h) {
+        const int nfmax = (h == L - 1) ? kNfMaxTop : kNfMaxLower;
+        nseg[h] = ceil_div(c->lv[h].N, nfmax);
+        maxseg = std::max(maxseg, nseg[h]);
+    }
+    c->prop.resize(maxseg);
+    for (int k = 0; k < maxseg; ++k) {
+        std::vector<PropJob> jobs;
+        std::vector<int4> work;
+        size_t smem = 0;
+        bool c8 = false;
+        // lower levels first: they carry the most work per tile
+        for (int h = 0; h < L; ++h) {
+            if (k >= nseg[h]) continue;
+            sf_level_state& lv = c->lv[h];
+            const bool top = (h == L - 1);
+            const int base = lv.N / nseg[h], extra = lv.N % nseg[h];
+            const int nf = base + (k < extra ? 1 : 0);
+            PropJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.g = make_grid(lv.grid);
+            auto out_of = [&](int seg, float4*& o0, float4*& o1) {
+                const bool to_pred = ((nseg[h] - 1 - seg) % 2) == 0;
+                o0 = to_pred ? lv.p0 : lv.t0;
+                o1 = to_pred ? lv.p1 : lv.t1;
+            };
+            if (k == 0) {
+                j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+                j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
+                j.apply_wscale = 1;
+            } else {
+                float4 *o0, *o1;
+                out_of(k - 1, o0, o1);
+                j.in0[0] = j.in0[1] = o0;
+                j.in1[0] = j.in1[1] = top ? nullptr : o1;
+            }
+            out_of(k, j.out0, j.out1);
+            if (top) j.out1 = nullptr;
+            j.nf = nf;
+            j.dt = 1.0f / (float)lv.N;
+            j.tiles_x = ceil_div(lv.grid.W, kPropTX);
+            jobs.push_back(j);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kPropTX, kPropTY);
+            c8 |= !top;
+        }
+        // one instantiation per launch: a mixed launch runs the top level through
+        // the 8-channel path (it ignores dw and Y when in1 is null)
+        for (auto& j : jobs) smem = std::max(smem, prop_smem_bytes(kPropTX, kPropTY, j.nf, c8));
+        c->prop[k].c8 = c8;
+        c->prop[k].smem = smem;
+        int r = upload_plan(jobs, work, c->prop[k], st);
+        if (r) return r;
+    }
+    // ---- update (and the first-frame initialisation): every level in one launch
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool init = pass == 1;
+        std::vector<UpdJob> jobs;
+        std::vector<int4> work;
+        size_t smem = 0;
+        for (int h = 0; h < L; ++h) {
+            sf_level_state& lv = c->lv[h];
+            UpdJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.g = make_grid(lv.grid);
+            j.level = h + 1;
+            j.top = (h == L - 1);
+            j.S = init ? 0 : lv.S;
+            j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
+            for (int q = 0; q < 2; ++q) {
+                j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q];
+                j.s0_new[q] = lv.s0[q]; j.s1_new[q] = lv.s1[q];
+            }
+            j.p0 = lv.p0;
+            j.p1 = lv.p1;
+            j.diag = nullptr;
+            j.tiles_x = ceil_div(lv.grid.W, kUpdTX);
+            jobs.push_back(j);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kUpdTX, kUpdTY);
+            smem = std::max(smem, upd_smem(j.S));
+        }
+        Plan& pl = init ? c->init : c->upd;
+        pl.smem = smem;
+        int r = upload_plan(jobs, work, pl, st);
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+// event pair around launch slot `slot` (no-op unless profiling)
+struct ProfScope {
+    sf_ctx* c;
+    cudaStream_t st;
+    size_t pair;
+    ProfScope(sf_ctx* c_, int slot, cudaStream_t st_) : c(c_), st(st_), pair((size_t)-1)
+    {
+        if (!c->profiling) return;
+        if (2 * c->ev_used + 2 > c->ev_pool.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            c->ev_pool.push_back(a);
+            c->ev_pool.push_back(b);
+        }
+        pair = c->ev_used++;
+        if (c->ev_slot.size() < c->ev_used) c->ev_slot.resize(c->ev_used);
+        c->ev_slot[pair] = slot;
+        cudaEventRecord(c->ev_pool[2 * pair], st);
+    }
+    ~ProfScope()
+    {
+        if (pair != (size_t)-1) cudaEventRecord(c->ev_pool[2 * pair + 1], st);
+    }
+};
+
+// reconstruction cascade and outputs of a frame whose new state has parity q
+int run_reconstruct(sf_ctx* c, int q, float dt, float* flow_out, float* inv_out, cudaStream_t st)
+{
+    int slot = (int)c->prop.size() + 1;
+    const int L = c->L;
+    for (int h = L - 2; h >= -1; --h) {
+        // h >= 0: reconstruct level h from level h+1; h == -1 with L == 1: outputs only
+        if (h == -1 && L > 1) break;
+        const int lvl = h >= 0 ? h : 0;
+        sf_level_state& lv = c->lv[lvl];
+        ReconArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.H = lv.grid.H;
+        a.W = lv.grid.W;
+        a.s0 = lv.s0[q];
+        a.s1 = lv.s1[q];
+        if (h >= 0) {
+            a.Hc = c->lv[h + 1].grid.H;
+            a.Wc = c->lv[h + 1].grid.W;
+            a.s0c = c->lv[h + 1].s0[q];
+        }
+        if (lvl == 0) {
+            a.flow_out = flow_out;
+            a.invdepth_out = inv_out;
+            a.inv_dt = 1.0f / dt;
+            a.check_finite = (c->p.flags & SF_CHECK_FINITE) != 0;
+            a.status = c->status;
+        }
+        ProfScope ps(c, slot++, st);
+        int r = launch_reconstruct(a, st);
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+bool valid_ptr_align(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+
+extern "C" {
+
+int sf_params_default(sf_params* p, int H, int W, int levels)
+{
+    if (!p || H <= 0 || W <= 0 || levels < 1 || levels > SF_MAX_LEVELS) return SF_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->fx = p->fy = 0.5f * (float)W;
+    p->cx = 0.5f * (float)W;
+    p->cy = 0.5f * (float)H;
+    p->max_flow = 1.0f;
+    for (int h = 0; h < SF_MAX_LEVELS; ++h) {
+        p->iters[h] = 0;
+        p->smooth_iters[h] = h == 0 ? 2 : 4;
+    }
+    p->gamma[0] = 1.0f;
+    p->gamma[1] = 1.0f;
+    p->gamma[2] = 1e-2f;
+    p->gamma[3] = 1.0f;
+    p->gamma[4] = 1.0f;
+    p->lambda_ref = 1.0f;
+    p->flags = SF_CHECK_CFL;
+    return SF_OK;
+}
+
+int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!p || !out || levels < 1 || levels > SF_MAX_LEVELS || levels > kMaxLevelsDev) return SF_EINVAL;
+    const int m = 1 << (levels - 1);
+    if (H <= 0 || W <= 0 || H % m || W % m || H / m < 8 || W / m < 8) return SF_EINVAL;
+    if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->cx) || !std::isfinite(p->cy)) return SF_EINVAL;
+    if (!(p->lambda_ref > 0) || !(p->gamma[2] > 0) || !(p->gamma[4] > 0)) return SF_EINVAL;
+    for (int k = 0; k < 5; ++k)
+        if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
+    if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
+    for (int h = 0; h < levels; ++h) {
+        const float s = (float)(1 << h);
+        const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / s));
+        if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
+    }
+    sf_ctx* c = new (std::nothrow) sf_ctx();
+    if (!c) return SF_ENOMEM;
+    c->H = H; c->W = W; c->L = levels; c->p = *p;
+    c->parity = 0; c->initialised = 0; c->dt_prev = 0.0f;
+    int r = SF_OK;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return SF_ECUDA; }
+    for (int h = 0; h < levels && !r; ++h) {
+        sf_level_state& lv = c->lv[h];
+        const float s = (float)(1 << h);
+        lv.grid.H = H >> h;
+        lv.grid.W = W >> h;
+        lv.grid.fx = p->fx / s; lv.grid.fy = p->fy / s; lv.grid.cx = p->cx / s; lv.grid.cy = p->cy / s;
+        lv.N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / s));
+        lv.S = p->smooth_iters[h];
+        for (int k = 0; k < 5; ++k) lv.gamma[k] = p->gamma[k];
+        const double dmu_c = (double)s / (double)p->fx;   // reading R10
+        lv.gamma[2] = (float)(p->gamma[2] * dmu_c * dmu_c);
+        const size_t n = (size_t)lv.grid.H * lv.grid.W;
+        if (cudaMalloc(&lv.block, 8 * n * sizeof(float4)) != cudaSuccess) { lv.block = nullptr; r = SF_ENOMEM; break; }
+        cudaMemsetAsync(lv.block, 0, 8 * n * sizeof(float4), st);
+        float4* b = (float4*)lv.block;
+        lv.s0[0] = b; lv.s1[0] = b + n; lv.s0[1] = b + 2 * n; lv.s1[1] = b + 3 * n;
+        lv.p0 = b + 4 * n; lv.p1 = b + 5 * n; lv.t0 = b + 6 * n; lv.t1 = b + 7 * n;
+    }
+    if (!r && cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) { c->status = nullptr; r = SF_ENOMEM; }
+    if (!r) r = cudaMemsetAsync(c->status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = build_plans(c, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaStreamDestroy(st);
+    if (r) { destroy_ctx(c); return r; }
+    *out = c;
+    return SF_OK;
+}
+
+int sf_reset(sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    c->initialised = 0;
+    return SF_OK;
+}
+
+int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
+            void* stream)
+{
+    if (!c || !image || !range || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    UpdArgs a;
+    a.image = image; a.range = range; a.H1 = c->H; a.W1 = c->W; a.lambda_ref = c->p.lambda_ref;
+    a.parity = c->parity;
+    int r;
+    if (!c->initialised) {
+        a.init = 1;
+        r = launch_update(c->init, a, st);
+    } else {
+        a.init = 0;
+        const float wscale = dt / c->dt_prev;   // reading R9
+        for (size_t k = 0; k < c->prop.size(); ++k) {
+            ProfScope ps(c, (int)k, st);
+            r = launch_propagate(c->prop[k], c->parity, wscale, c->p.flags, c->status, st);
+            if (r) return r;
+        }
+        ProfScope ps(c, (int)c->prop.size(), st);
+        r = launch_update(c->upd, a, st);
+    }
+    if (r) return r;
+    r = run_reconstruct(c, c->parity ^ 1, dt, flow_out, invdepth_out, st);
+    if (r) return r;
+    c->parity ^= 1;
+    c->initialised = 1;
+    c->dt_prev = dt;
+    return SF_OK;
+}
+
+int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
+                 void* stream)
+{
+    if (!c || !image || !range) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->H * c->W;
+    if (!c->stage_image) {
+        if (cudaMalloc(&c->stage_image, n * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&c->stage_range, n * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&c->stage_flow, 3 * n * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&c->stage_inv, n * sizeof(float)) != cudaSuccess)
+            return SF_ENOMEM;
+    }
+    if (cudaMemcpyAsync(c->stage_image, image, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->stage_range, range, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SF_ECUDA;
+    int r = sf_step(c, c->stage_image, c->stage_range, dt, flow_out ? c->stage_flow : nullptr, invdepth_out ? c->stage_inv : nullptr,
+                    stream);
+    if (r) return r;
+    if (flow_out && cudaMemcpyAsync(flow_out, c->stage_flow, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SF_ECUDA;
+    if (invdepth_out && cudaMemcpyAsync(invdepth_out, c->stage_inv, n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SF_ECUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+int sf_status(sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
+    int s = 0;
+    if (cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
+    if (s & kStatusNonFinite) return SF_ENONFINITE;
+    if (s & kStatusCfl) return SF_WARN_CFL;
+    return SF_OK;
+}
+
+int sf_get_state(sf_ctx* c, int level, float* dst, float* dt_prev, void* stream)
+{
+    if (!c || level < 0 || level >= c->L || !dst) return SF_EINVAL;
+    sf_level_state& lv = c->lv[level];
+    const int n = lv.grid.H * lv.grid.W;
+    k_pack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(lv.s0[c->parity], lv.s1[c->parity],
+                                                                              dst, n);
+    if (dt_prev) *dt_prev = c->dt_prev;
+    return last_error();
+}
+
+int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* stream)
+{
+    if (!c || level < 0 || level >= c->L || !src || !(dt_prev > 0.0f)) return SF_EINVAL;
+    sf_level_state& lv = c->lv[level];
+    const int n = lv.grid.H * lv.grid.W;
+    k_unpack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(src, lv.s0[c->parity],
+                                                                                lv.s1[c->parity], n);
+    c->dt_prev = dt_prev;
+    c->initialised = 1;
+    return last_error();
+}
+
+int sf_profile(sf_ctx* c, int enable)
+{
+    if (!c) return SF_EINVAL;
+    c->profiling = enable != 0;
+    return SF_OK;
+}
+
+int sf_profile_read(sf_ctx* c, float* ms, int* count, int n)
+{
+    if (!c || (n > 0 && (!ms || !count))) return SF_EINVAL;
+    const int slots = (int)c->prop.size() + 1 + std::max(1, c->L - 1);
+    for (int k = 0; k < n; ++k) { ms[k] = 0.0f; count[k] = 0; }
+    for (size_t p = 0; p < c->ev_used; ++p) {
+        if (cudaEventSynchronize(c->ev_pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
+        const int s = c->ev_slot[p];
+        if (s < n) { ms[s] += t; count[s] += 1; }
+    }
+    c->ev_used = 0;
+    return slots;
+}
+
+int sf_kernels_per_step(const sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    return (int)c->prop.size() + 1 + std::max(1, c->L - 1);
+}
+
+void sf_destroy(sf_ctx* c) { destroy_ctx(c); }
+
+const char* sf_strerror(int code)
+{
+    switch (code) {
+    case SF_OK: return "ok";
+    case SF_EINVAL: return "invalid argument or configuration";
+    case SF_ENOMEM: return "out of memory";
+    case SF_ECUDA: return "CUDA runtime error";
+    case SF_ETIMEOUT: return "bounded device wait timed out";
+    case SF_ENONFINITE: return "non-finite value in the filter state";
+    case SF_WARN_CFL: return "prediction violated the CFL bound (Eq. 67)";
+    default: return "unknown status code";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stage entry points
+// ---------------------------------------------------------------------------
+
+int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* s0_in, const float* s1_in,
+                 float* s0_out, float* s1_out, int* status, void* stream)
+{
+    if (!g || g->H < 1 || g->W < 1 || N < 1 || !s0_in || !s0_out) return SF_EINVAL;
+    if ((s1_in == nullptr) != (s1_out == nullptr)) return SF_EINVAL;
+    if (!valid_ptr_align(s0_in) || !valid_ptr_align(s0_out) || !valid_ptr_align(s1_in) || !valid_ptr_align(s1_out))
+        return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool c8 = s1_in != nullptr;
+    const int nfmax = c8 ? kNfMaxLower : kNfMaxTop;
+    const int nseg = ceil_div(N, nfmax);
+    const size_t n = (size_t)g->H * g->W;
+    float4* scratch = nullptr;
+    if (nseg > 1) {
+        if (cudaMallocAsync((void**)&scratch, (c8 ? 2 : 1) * n * sizeof(float4), st) != cudaSuccess) return SF_ENOMEM;
+    }
+    int r = SF_OK;
+    const float4* in0 = (const float4*)s0_in;
+    const float4* in1 = (const float4*)s1_in;
+    for (int k = 0; k < nseg && !r; ++k) {
+        const bool to_out = ((nseg - 1 - k) % 2) == 0;
+        float4* o0 = to_out ? (float4*)s0_out : scratch;
+        float4* o1 = c8 ? (to_out ? (float4*)s1_out : scratch + n) : nullptr;
+        PropJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.g = make_grid(*g);
+        j.in0[0] = j.in0[1] = in0;
+        j.in1[0] = j.in1[1] = in1;
+        j.out0 = o0;
+        j.out1 = o1;
+        j.nf = N / nseg + (k < N % nseg ? 1 : 0);
+        j.apply_wscale = k == 0;
+        j.dt = 1.0f / (float)N;
+        j.tiles_x = ceil_div(g->W, kPropTX);
+        std::vector<int4> work;
+        add_tiles(work, 0, g->H, g->W, kPropTX, kPropTY);
+        Plan pl;
+        pl.c8 = c8;
+        pl.smem = prop_smem_bytes(kPropTX, kPropTY, j.nf, c8);
+        // the job and work list travel through stream-ordered scratch
+        void* mem = nullptr;
+        const size_t bytes = sizeof(PropJob) + work.size() * sizeof(int4);
+        if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) { r = SF_ENOMEM; break; }
+        std::vector<unsigned char> host(bytes);
+        std::memcpy(host.data(), &j, sizeof(PropJob));
+        std::memcpy(host.data() + sizeof(PropJob), work.data(), work.size() * sizeof(int4));
+        r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+        if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;  // host buffer lifetime
+        pl.jobs = mem;
+        pl.work = (int4*)((unsigned char*)mem + sizeof(PropJob));
+        pl.nwork = (int)work.size();
+        if (!r) r = launch_propagate(pl, 0, wscale, flags, status, st);
+        cudaFreeAsync(mem, st);
+        in0 = o0;
+        in1 = o1;
+    }
+    if (scratch) cudaFreeAsync(scratch, st);
+    return r;
+}
+
+int sf_update(const sf_grid* g, int level, int top, int S, int init, const float* gamma, float lambda_ref,
+              const float* image, const float* range, int H1, int W1, const float* s0_cur, const float* s1_cur,
+              const float* p0, const float* p1, float* s0_new, float* s1_new, float* diag, void* stream)
+{
+    if (!g || !gamma || !image || !range || !s0_new || !s1_new || level < 1 || level > kMaxLevelsDev || S < 0 ||
+        S > 16)
+        return SF_EINVAL;
+    if ((g->H << (level - 1)) > H1 || (g->W << (level - 1)) > W1) return SF_EINVAL;
+    if (!init && (!p0 || (top ? (!s0_cur || !s1_cur) : !p1))) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    UpdJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.g = make_grid(*g);
+    j.level = level;
+    j.top = top != 0;
+    j.S = S;
+    j.g1 = gamma[0]; j.g2 = gamma[1]; j.g3 = gamma[2]; j.g4 = gamma[3]; j.g5 = gamma[4];
+    j.s0_cur[0] = j.s0_cur[1] = (const float4*)s0_cur;
+    j.s1_cur[0] = j.s1_cur[1] = (const float4*)s1_cur;
+    j.p0 = (const float4*)p0;
+    j.p1 = (const float4*)p1;
+    j.s0_new[0] = j.s0_new[1] = (float4*)s0_new;
+    j.s1_new[0] = j.s1_new[1] = (float4*)s1_new;
+    j.diag = diag;
+    j.tiles_x = ceil_div(g->W, kUpdTX);
+    std::vector<int4> work;
+    add_tiles(work, 0, g->H, g->W, kUpdTX, kUpdTY);
+    const size_t bytes = sizeof(UpdJob) + work.size() * sizeof(int4);
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) return SF_ENOMEM;
+    std::vector<unsigned char> host(bytes);
+    std::memcpy(host.data(), &j, sizeof(UpdJob));
+    std::memcpy(host.data() + sizeof(UpdJob), work.data(), work.size() * sizeof(int4));
+    int r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    Plan pl;
+    pl.jobs = mem;
+    pl.work = (int4*)((unsigned char*)mem + sizeof(UpdJob));
+    pl.nwork = (int)work.size();
+    pl.smem = upd_smem(init ? 0 : S);
+    UpdArgs a;
+    a.image = image; a.range = range; a.H1 = H1; a.W1 = W1; a.lambda_ref = lambda_ref;
+    a.parity = 0;   // new planes are read at parity ^ 1; both slots point to the same buffer
+    a.init = init != 0;
+    if (!r) r = launch_update(pl, a, st);
+    cudaFreeAsync(mem, st);
+    return r;
+}
+
+int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const float* const* s1, float dt,
+                   float* flow_out, float* invdepth_out, int check_finite, int* status, void* stream)
+{
+    if (levels < 1 || levels > SF_MAX_LEVELS || !grids || !s0 || !s1 || !(dt > 0.0f)) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int h = levels - 2; h >= -1; --h) {
+        if (h == -1 && levels > 1) break;
+        const int lvl = h >= 0 ? h : 0;
+        ReconArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.H = grids[lvl].H;
+        a.W = grids[lvl].W;
+        a.s0 = (float4*)s0[lvl];
+        a.s1 = (const float4*)s1[lvl];
+        if (h >= 0) {
+            a.Hc = grids[h + 1].H;
+            a.Wc = grids[h + 1].W;
+            a.s0c = (const float4*)s0[h + 1];
+        }
+        if (lvl == 0) {
+            a.flow_out = flow_out;
+            a.invdepth_out = invdepth_out;
+            a.inv_dt = 1.0f / dt;
+            a.check_finite = check_finite;
+            a.status = status;
+        }
+        int r = launch_reconstruct(a, st);
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+}  // extern "C"

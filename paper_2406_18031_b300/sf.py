@@ -1,0 +1,241 @@
+"""ctypes binding of libsf (include/sf.h): argument marshalling only.
+
+Every step of the filter runs in the library's CUDA kernels; this module only
+converts torch tensors and Python values into the C ABI's pointers and
+structs.  There is no CPU path: if the library cannot be loaded, or a CUDA
+device is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libsf.so"
+
+MAX_LEVELS = 4
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, WARN_CFL = 0, -1, -2, -3, -4, -5, 1
+DOMINANT_LITERAL, SOURCE_SPLIT, CHECK_CFL, CHECK_FINITE = 1, 2, 4, 8
+
+
+class SFError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("iters", ctypes.c_int * MAX_LEVELS), ("max_flow", ctypes.c_float),
+                ("smooth_iters", ctypes.c_int * MAX_LEVELS), ("gamma", ctypes.c_float * 5),
+                ("lambda_ref", ctypes.c_float), ("flags", ctypes.c_int)]
+
+
+class CGrid(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+_lib = None
+
+EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
+           "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_update",
+           "sf_reconstruct"]
+
+
+def lib():
+    """Load libsf.so (built by ``paper_2406_18031_b300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2406_18031_b300.build`")
+        L = ctypes.CDLL(str(LIB_PATH))
+        i, f, vp = ctypes.c_int, ctypes.c_float, ctypes.c_void_p
+        P = ctypes.POINTER
+        L.sf_params_default.argtypes = [P(CParams), i, i, i]
+        L.sf_create.argtypes = [i, i, i, P(CParams), P(vp)]
+        L.sf_reset.argtypes = [vp]
+        L.sf_step.argtypes = [vp, vp, vp, f, vp, vp, vp]
+        L.sf_step_host.argtypes = [vp, vp, vp, f, vp, vp, vp]
+        L.sf_status.argtypes = [vp]
+        L.sf_get_state.argtypes = [vp, i, vp, P(f), vp]
+        L.sf_set_state.argtypes = [vp, i, vp, f, vp]
+        L.sf_kernels_per_step.argtypes = [vp]
+        L.sf_profile.argtypes = [vp, i]
+        L.sf_profile_read.argtypes = [vp, P(f), P(i), i]
+        L.sf_destroy.argtypes = [vp]
+        L.sf_destroy.restype = None
+        L.sf_strerror.argtypes = [i]
+        L.sf_strerror.restype = ctypes.c_char_p
+        L.sf_propagate.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
+        L.sf_update.argtypes = [P(CGrid), i, i, i, i, P(f), f, vp, vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sf_reconstruct.argtypes = [i, P(CGrid), P(vp), P(vp), f, vp, vp, i, vp, vp]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().sf_strerror(int(code)).decode()
+
+
+def _check(code, what):
+    if code < 0:
+        raise SFError(code, what)
+    return code
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous() or t.dtype.itemsize != 4:
+        raise ValueError("expected a contiguous 32-bit tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Params:
+    """Mirror of ``sf_params``; ``None`` fields take the library defaults."""
+    fx: float | None = None
+    fy: float | None = None
+    cx: float | None = None
+    cy: float | None = None
+    iters: list | None = None
+    max_flow: float | None = None
+    smooth: list | None = None
+    gamma: tuple | None = None
+    lambda_ref: float | None = None
+    flags: int | None = None
+
+    def to_c(self, H, W, levels) -> CParams:
+        c = CParams()
+        _check(lib().sf_params_default(ctypes.byref(c), H, W, levels), "sf_params_default")
+        for name in ("fx", "fy", "cx", "cy", "max_flow", "lambda_ref", "flags"):
+            v = getattr(self, name)
+            if v is not None:
+                setattr(c, name, v)
+        if self.iters is not None:
+            for k, v in enumerate(self.iters[:MAX_LEVELS]):
+                c.iters[k] = int(v)
+        if self.smooth is not None:
+            for k, v in enumerate(self.smooth[:MAX_LEVELS]):
+                c.smooth_iters[k] = int(v)
+        if self.gamma is not None:
+            for k, v in enumerate(self.gamma):
+                c.gamma[k] = float(v)
+        return c
+
+
+class Filter:
+    """One filter context (``sf_create`` .. ``sf_destroy``) on the current CUDA device."""
+
+    def __init__(self, H: int, W: int, levels: int, params: Params | None = None):
+        self.H, self.W, self.levels = H, W, levels
+        self.params = (params or Params()).to_c(H, W, levels)
+        h = ctypes.c_void_p()
+        _check(lib().sf_create(H, W, levels, ctypes.byref(self.params), ctypes.byref(h)), "sf_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def reset(self):
+        _check(lib().sf_reset(self._h), "sf_reset")
+
+    def step(self, image, rng, dt, flow_out=None, invdepth_out=None, stream=None):
+        """Asynchronous frame on CUDA tensors; returns the status code (>= 0)."""
+        return _check(lib().sf_step(self._h, _ptr(image), _ptr(rng), float(dt), _ptr(flow_out),
+                                    _ptr(invdepth_out), _stream(stream)), "sf_step")
+
+    def step_host(self, image: np.ndarray, rng: np.ndarray, dt, flow_out: np.ndarray | None = None,
+                  invdepth_out: np.ndarray | None = None, stream=None):
+        """Frame on host float32 arrays (copies included); waits for completion."""
+        def hp(a):
+            if a is None:
+                return None
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+            return ctypes.c_void_p(a.ctypes.data)
+        return _check(lib().sf_step_host(self._h, hp(image), hp(rng), float(dt), hp(flow_out), hp(invdepth_out),
+                                         _stream(stream)), "sf_step_host")
+
+    def kernels_per_step(self) -> int:
+        return _check(lib().sf_kernels_per_step(self._h), "sf_kernels_per_step")
+
+    def profile(self, enable: bool):
+        _check(lib().sf_profile(self._h, int(bool(enable))), "sf_profile")
+
+    def profile_read(self):
+        """(summed ms, launch count) per launch slot since the last read."""
+        n = 16
+        ms = (ctypes.c_float * n)(); cnt = (ctypes.c_int * n)()
+        slots = _check(lib().sf_profile_read(self._h, ms, cnt, n), "sf_profile_read")
+        return [(ms[k], cnt[k]) for k in range(min(slots, n))]
+
+    def status(self) -> int:
+        """OK, WARN_CFL or ENONFINITE recorded since the last call; raises on a failed call."""
+        code = lib().sf_status(self._h)
+        if code not in (OK, WARN_CFL, ENONFINITE):
+            raise SFError(code, "sf_status")
+        return code
+
+    def level_shape(self, h):
+        return self.H >> h, self.W >> h
+
+    def get_state(self, h, stream=None):
+        """Level h (0-based) state as an [8, H_h, W_h] CUDA tensor and dt_prev."""
+        import torch
+        Hh, Wh = self.level_shape(h)
+        dst = torch.empty((8, Hh, Wh), dtype=torch.float32, device="cuda")
+        dtp = ctypes.c_float()
+        _check(lib().sf_get_state(self._h, h, _ptr(dst), ctypes.byref(dtp), _stream(stream)), "sf_get_state")
+        return dst, dtp.value
+
+    def set_state(self, h, planes, dt_prev, stream=None):
+        _check(lib().sf_set_state(self._h, h, _ptr(planes.contiguous()), float(dt_prev), _stream(stream)),
+               "sf_set_state")
+
+
+def grid(H, W, fx, fy, cx, cy) -> CGrid:
+    return CGrid(int(H), int(W), float(fx), float(fy), float(cx), float(cy))
+
+
+def propagate(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
+              stream=None):
+    """Stage entry point ``sf_propagate`` on [H, W, 4] float32 CUDA tensors."""
+    return _check(lib().sf_propagate(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in), _ptr(s1_in),
+                                     _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)), "sf_propagate")
+
+
+def update(g: CGrid, level, top, S, init, gamma, lambda_ref, image, rng, s0_new, s1_new, s0_cur=None, s1_cur=None,
+           p0=None, p1=None, diag=None, stream=None):
+    """Stage entry point ``sf_update``; image/rng are the level-1 [H1, W1] inputs."""
+    gm = (ctypes.c_float * 5)(*gamma)
+    H1, W1 = image.shape
+    return _check(lib().sf_update(ctypes.byref(g), int(level), int(top), int(S), int(init), gm, float(lambda_ref),
+                                  _ptr(image), _ptr(rng), H1, W1, _ptr(s0_cur), _ptr(s1_cur), _ptr(p0), _ptr(p1),
+                                  _ptr(s0_new), _ptr(s1_new), _ptr(diag), _stream(stream)), "sf_update")
+
+
+def reconstruct(grids, s0, s1, dt, flow_out=None, invdepth_out=None, check_finite=False, status=None, stream=None):
+    """Stage entry point ``sf_reconstruct`` over per-level [H, W, 4] tensors."""
+    L = len(grids)
+    ga = (CGrid * L)(*grids)
+    p0 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s0])
+    p1 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s1])
+    return _check(lib().sf_reconstruct(L, ga, p0, p1, float(dt), _ptr(flow_out), _ptr(invdepth_out),
+                                       int(bool(check_finite)), _ptr(status), _stream(stream)), "sf_reconstruct")

@@ -1,0 +1,199 @@
+"""Whole-frame parity of sf_step against the FP64 oracle filter, and the
+library's status / checkpoint / edge-case behaviour."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_18031_b300 import scenes, sf
+from tests import gpu_util as gu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    oracle.set_threads(8)
+
+
+def _pair(seq, gamma=None, flags=0):
+    H, W = seq.shape
+    kw = dict(iters=seq.iters, smooth=seq.smooth)
+    if gamma is not None:
+        kw["gamma"] = gamma
+    g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy,
+                                               flags=flags | sf.CHECK_CFL | sf.CHECK_FINITE, **kw))
+    r = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, flags=flags, **kw))
+    return g, r
+
+
+def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX):
+    """Run both filters; returns per-frame (max px error, max rho error) and the final outputs."""
+    g, r = _pair(seq, flags=flags)
+    H, W = seq.shape
+    _, _, dmu = r.geometry(0)
+    flow = torch.empty((3, H, W), device="cuda")
+    inv = torch.empty((H, W), device="cuda")
+    errs = []
+    for k in range(frames):
+        dt = seq.dt if dts is None else dts[k]
+        kk = k % seq.frames
+        g.step(torch.from_numpy(seq.image[kk]).cuda(), torch.from_numpy(seq.range[kk]).cuda(), dt, flow, inv)
+        rf, ri = r.step(seq.image[kk], seq.range[kk], dt)
+        if check_every or k == frames - 1:
+            gf = flow.cpu().numpy().astype(np.float64)
+            e = float((np.abs(gf - rf) * dt / dmu[None]).max())
+            ei = float(np.abs(inv.cpu().numpy() - ri).max())
+            errs.append((e, ei))
+    st = g.status()
+    return errs, (flow.cpu().numpy(), inv.cpu().numpy()), (rf, ri), st
+
+
+def test_plane64_sequence_per_frame():
+    seq = scenes.plane64(frames=20)
+    errs, _, _, st = _run(seq, 20)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert st == sf.OK
+
+
+@pytest.mark.parametrize("flags", [0, oracle.SOURCE_SPLIT, oracle.DOMINANT_LITERAL])
+def test_two_level_scene_per_frame(flags):
+    seq = scenes.scene512(frames=8, H=128, W=160, max_flow=4.0, levels=2, iters=(4, 2), smooth=(2, 4))
+    errs, _, _, st = _run(seq, 8, flags=flags)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert st >= 0
+
+
+def test_three_level_driving_scene_with_sky():
+    seq = scenes.drive(frames=5, H=96, W=312, levels=3, iters=(8, 4, 2), smooth=(2, 4, 4))
+    assert np.isinf(seq.range).any()
+    errs, _, _, st = _run(seq, 5)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+
+
+def test_frame_time_change():
+    seq = scenes.plane64(frames=6)
+    dts = [seq.dt, seq.dt, seq.dt / 2, seq.dt / 2, seq.dt * 1.5, seq.dt]
+    errs, _, _, _ = _run(seq, 6, dts=dts)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", ["plane64", "two_level"])
+def test_hundred_frame_drift(case):
+    if case == "plane64":
+        seq = scenes.plane64(frames=100)
+    else:
+        seq = scenes.scene512(frames=100, H=96, W=96, max_flow=3.0, levels=2, iters=(3, 2), smooth=(2, 4))
+    errs, (gf, gi), (rf, ri), _ = _run(seq, 100, check_every=False)
+    assert gu.rel_l2(gf, rf) <= gu.DRIFT_TOL
+    assert gu.rel_l2(gi, ri) <= gu.DRIFT_TOL
+
+
+@pytest.mark.slow
+def test_full_size_512_two_levels():
+    # the benchmark's workload (512x512, 2 levels, N = [8, 4], S = [2, 4]) in the
+    # same launch configuration, three frames, every pixel
+    seq = scenes.scene512(frames=3)
+    errs, _, _, st = _run(seq, 3)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert st >= 0
+
+
+@pytest.mark.slow
+def test_full_size_driving_three_levels():
+    seq = scenes.drive(frames=2)
+    errs, _, _, _ = _run(seq, 2)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+
+
+def test_state_checkpoint_roundtrip():
+    seq = scenes.scene512(frames=4, H=64, W=96, max_flow=2.0, levels=2, iters=(2, 1), smooth=(2, 4))
+    g, r = _pair(seq)
+    H, W = seq.shape
+    for k in range(3):
+        g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt)
+        r.step(seq.image[k], seq.range[k], seq.dt)
+    for h in range(2):
+        st, dtp = g.get_state(h)
+        s = st.cpu().numpy()
+        ref = r.get_state(h)
+        _, _, dmu = r.geometry(h)
+        assert abs(dtp - seq.dt) <= 1e-7 * seq.dt       # stored as float32
+        assert gu.px_err(np.moveaxis(s[0:3], 0, -1), ref["w"], dmu) <= gu.FLOW_TOL_PX
+        assert gu.px_err(np.moveaxis(s[4:7], 0, -1), ref["dw"], dmu) <= gu.FLOW_TOL_PX
+        assert np.abs(s[3] - ref["rho"]).max() <= gu.RHO_TOL
+        assert np.abs(s[7] - ref["Yhat"]).max() <= gu.Y_TOL
+    # restore into a fresh context: the next frame matches the running one
+    g2, _ = _pair(seq)
+    for h in range(2):
+        st, dtp = g.get_state(h)
+        g2.set_state(h, st, dtp)
+    f1 = torch.empty((3, H, W), device="cuda"); f2 = torch.empty((3, H, W), device="cuda")
+    img, rg = torch.from_numpy(seq.image[3]).cuda(), torch.from_numpy(seq.range[3]).cuda()
+    g.step(img, rg, seq.dt, f1)
+    g2.step(img, rg, seq.dt, f2)
+    torch.cuda.synchronize()
+    assert torch.equal(f1, f2)
+
+
+def test_reset_returns_zero_flow_then_restarts():
+    seq = scenes.plane64(frames=3)
+    g, _ = _pair(seq)
+    flow = torch.empty((3, 64, 64), device="cuda")
+    for k in range(2):
+        g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, flow)
+    torch.cuda.synchronize()
+    assert flow.abs().max().item() > 0
+    g.reset()
+    g.step(torch.from_numpy(seq.image[2]).cuda(), torch.from_numpy(seq.range[2]).cuda(), seq.dt, flow)
+    torch.cuda.synchronize()
+    assert flow.abs().max().item() == 0.0
+
+
+def test_status_reports_cfl_and_nonfinite():
+    seq = scenes.plane64(frames=3)
+    H, W = seq.shape
+    g = sf.Filter(H, W, 1, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=[1],
+                                      flags=sf.CHECK_CFL | sf.CHECK_FINITE))
+    # a state of 3 px/frame with one sub-iteration breaks Eq. 67
+    planes = torch.zeros((8, H, W), device="cuda")
+    _, _, dmu = oracle.geometry(H, W, seq.fx, seq.fy, seq.cx, seq.cy)
+    planes[0] = torch.from_numpy(gu.f32(3.0 * dmu)).cuda()
+    planes[3] = 0.2
+    g.set_state(0, planes, seq.dt)
+    g.step(torch.from_numpy(seq.image[1]).cuda(), torch.from_numpy(seq.range[1]).cuda(), seq.dt)
+    assert g.status() == sf.WARN_CFL
+    assert g.status() == sf.OK            # cleared by the read
+    bad = torch.from_numpy(seq.image[2]).cuda()
+    bad[10, 10] = float("nan")
+    g.step(bad, torch.from_numpy(seq.range[2]).cuda(), seq.dt, torch.empty((3, H, W), device="cuda"))
+    assert g.status() == sf.ENONFINITE
+
+
+def test_host_buffer_step_matches_device_step():
+    seq = scenes.plane64(frames=3)
+    H, W = seq.shape
+    a, _ = _pair(seq)
+    b, _ = _pair(seq)
+    fa = torch.empty((3, H, W), device="cuda"); ia = torch.empty((H, W), device="cuda")
+    fb = np.empty((3, H, W), np.float32); ib = np.empty((H, W), np.float32)
+    for k in range(3):
+        a.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, fa, ia)
+        b.step_host(seq.image[k], seq.range[k], seq.dt, fb, ib)
+    torch.cuda.synchronize()
+    assert np.array_equal(fa.cpu().numpy(), fb) and np.array_equal(ia.cpu().numpy(), ib)
+
+
+@pytest.mark.parametrize("H,W,levels", [(8, 8, 1), (16, 24, 2), (32, 40, 3), (40, 56, 2)])
+def test_small_and_ragged_grids(H, W, levels):
+    seq = scenes.plane64(frames=4, H=H, W=W, levels=levels, iters=[2] * levels)
+    errs, _, _, _ = _run(seq, 4)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
