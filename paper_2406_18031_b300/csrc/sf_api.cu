@@ -18,10 +18,9 @@ using namespace sfdev;
 
 namespace {
 
-// tile shapes and the largest number of sub-iterations fused in one launch
-constexpr int kPropTX = 32, kPropTY = 32;
-constexpr int kNfMaxLower = 8;   // 48 x 48 region x 72 B = 166 KB of shared memory
-constexpr int kNfMaxTop = 12;    // 56 x 56 region x 40 B = 125 KB
+// the largest number of sub-iterations fused in one propagation launch (its
+// square output tile is 64 - 2 nf pixels wide) and the update tile
+constexpr int kNfMax = 8;
 constexpr int kUpdTX = 32, kUpdTY = 32;
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
@@ -87,26 +86,30 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
         for (int tx = 0; tx < W; tx += TX) work.push_back(make_int4(job, ty, tx, 0));
 }
 
+template <bool C8, bool LIT>
+int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
+{
+    if (set_smem_attr((const void*)k_propagate<C8, LIT>, p.smem)) return SF_ECUDA;
+    k_propagate<C8, LIT><<<p.nwork, kPrThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
+                                                              status);
+    return last_error();
+}
+
 int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
-    if (p.c8) {
-        if (set_smem_attr((const void*)k_propagate<true>, p.smem)) return SF_ECUDA;
-        k_propagate<true><<<p.nwork, kThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
-                                                             status, kPropTX, kPropTY);
-    } else {
-        if (set_smem_attr((const void*)k_propagate<false>, p.smem)) return SF_ECUDA;
-        k_propagate<false><<<p.nwork, kThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
-                                                              status, kPropTX, kPropTY);
-    }
-    return last_error();
+    const bool lit = (flags & SF_DOMINANT_LITERAL) != 0;
+    if (p.c8) return lit ? launch_propagate_t<true, true>(p, parity, wscale, flags, status, st)
+                         : launch_propagate_t<true, false>(p, parity, wscale, flags, status, st);
+    return lit ? launch_propagate_t<false, true>(p, parity, wscale, flags, status, st)
+               : launch_propagate_t<false, false>(p, parity, wscale, flags, status, st);
 }
 
 int launch_update(const Plan& p, const UpdArgs& a, cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
     if (set_smem_attr((const void*)k_update, p.smem)) return SF_ECUDA;
-    k_update<<<p.nwork, kThreads, p.smem, st>>>((const UpdJob*)p.jobs, p.work, a, kUpdTX, kUpdTY);
+    k_update<<<p.nwork, kUpdThreads, p.smem, st>>>((const UpdJob*)p.jobs, p.work, a, kUpdTX, kUpdTY);
     return last_error();
 }
 
@@ -117,6 +120,10 @@ int launch_reconstruct(const ReconArgs& a, cudaStream_t st)
     k_reconstruct<<<blocks, kThreads, 0, st>>>(a);
     return last_error();
 }
+
+// offset of the work list behind a job in one stage-call upload: int4 loads
+// need 16-byte alignment whatever the size of the job struct
+inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
 size_t upd_smem(int S)
 {
@@ -193,8 +200,7 @@ int build_plans(sf_ctx* c, cudaStream_t st)
     // prediction planes, earlier ones alternate so that this holds.
     int nseg[SF_MAX_LEVELS], maxseg = 0;
     for (int h = 0; h < L; ++h) {
-        const int nfmax = (h == L - 1) ? kNfMaxTop : kNfMaxLower;
-        nseg[h] = ceil_div(c->lv[h].N, nfmax);
+        nseg[h] = ceil_div(c->lv[h].N, kNfMax);
         maxseg = std::max(maxseg, nseg[h]);
     }
     c->prop.resize(maxseg);
@@ -232,14 +238,14 @@ int build_plans(sf_ctx* c, cudaStream_t st)
             if (top) j.out1 = nullptr;
             j.nf = nf;
             j.dt = 1.0f / (float)lv.N;
-            j.tiles_x = ceil_div(lv.grid.W, kPropTX);
+            j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
             jobs.push_back(j);
-            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kPropTX, kPropTY);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
             c8 |= !top;
         }
         // one instantiation per launch: a mixed launch runs the top level through
-        // the 8-channel path (it ignores dw and Y when in1 is null)
-        for (auto& j : jobs) smem = std::max(smem, prop_smem_bytes(kPropTX, kPropTY, j.nf, c8));
+        // the 8-channel path (it skips dw and Y when in1 is null)
+        smem = prop_smem_bytes();
         c->prop[k].c8 = c8;
         c->prop[k].smem = smem;
         int r = upload_plan(jobs, work, c->prop[k], st);
@@ -251,7 +257,8 @@ int build_plans(sf_ctx* c, cudaStream_t st)
         std::vector<UpdJob> jobs;
         std::vector<int4> work;
         size_t smem = 0;
-        for (int h = 0; h < L; ++h) {
+        for (int hh = 0; hh < L; ++hh) {
+            const int h = L - 1 - hh;   // longest tiles first: the top level has the widest halo
             sf_level_state& lv = c->lv[h];
             UpdJob j;
             std::memset(&j, 0, sizeof(j));
@@ -260,6 +267,8 @@ int build_plans(sf_ctx* c, cudaStream_t st)
             j.top = (h == L - 1);
             j.S = init ? 0 : lv.S;
             j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
+            j.inv45 = 1.0f / (j.g4 + j.g5);
+            j.inv5 = 1.0f / j.g5;
             for (int q = 0; q < 2; ++q) {
                 j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q];
                 j.s0_new[q] = lv.s0[q]; j.s1_new[q] = lv.s1[q];
@@ -582,8 +591,7 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
         return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool c8 = s1_in != nullptr;
-    const int nfmax = c8 ? kNfMaxLower : kNfMaxTop;
-    const int nseg = ceil_div(N, nfmax);
+    const int nseg = ceil_div(N, kNfMax);
     const size_t n = (size_t)g->H * g->W;
     float4* scratch = nullptr;
     if (nseg > 1) {
@@ -606,23 +614,24 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
         j.nf = N / nseg + (k < N % nseg ? 1 : 0);
         j.apply_wscale = k == 0;
         j.dt = 1.0f / (float)N;
-        j.tiles_x = ceil_div(g->W, kPropTX);
+        j.tiles_x = ceil_div(g->W, prop_tile(j.nf));
         std::vector<int4> work;
-        add_tiles(work, 0, g->H, g->W, kPropTX, kPropTY);
+        add_tiles(work, 0, g->H, g->W, prop_tile(j.nf), prop_tile(j.nf));
         Plan pl;
         pl.c8 = c8;
-        pl.smem = prop_smem_bytes(kPropTX, kPropTY, j.nf, c8);
+        pl.smem = prop_smem_bytes();
         // the job and work list travel through stream-ordered scratch
         void* mem = nullptr;
-        const size_t bytes = sizeof(PropJob) + work.size() * sizeof(int4);
+        const size_t woff = work_offset(sizeof(PropJob));
+        const size_t bytes = woff + work.size() * sizeof(int4);
         if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) { r = SF_ENOMEM; break; }
         std::vector<unsigned char> host(bytes);
         std::memcpy(host.data(), &j, sizeof(PropJob));
-        std::memcpy(host.data() + sizeof(PropJob), work.data(), work.size() * sizeof(int4));
+        std::memcpy(host.data() + woff, work.data(), work.size() * sizeof(int4));
         r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
         if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;  // host buffer lifetime
         pl.jobs = mem;
-        pl.work = (int4*)((unsigned char*)mem + sizeof(PropJob));
+        pl.work = (int4*)((unsigned char*)mem + woff);
         pl.nwork = (int)work.size();
         if (!r) r = launch_propagate(pl, 0, wscale, flags, status, st);
         cudaFreeAsync(mem, st);
@@ -650,6 +659,9 @@ int sf_update(const sf_grid* g, int level, int top, int S, int init, const float
     j.top = top != 0;
     j.S = S;
     j.g1 = gamma[0]; j.g2 = gamma[1]; j.g3 = gamma[2]; j.g4 = gamma[3]; j.g5 = gamma[4];
+    if (!(j.g5 > 0.0f) || !(j.g4 >= 0.0f)) return SF_EINVAL;
+    j.inv45 = 1.0f / (j.g4 + j.g5);
+    j.inv5 = 1.0f / j.g5;
     j.s0_cur[0] = j.s0_cur[1] = (const float4*)s0_cur;
     j.s1_cur[0] = j.s1_cur[1] = (const float4*)s1_cur;
     j.p0 = (const float4*)p0;
@@ -660,17 +672,18 @@ int sf_update(const sf_grid* g, int level, int top, int S, int init, const float
     j.tiles_x = ceil_div(g->W, kUpdTX);
     std::vector<int4> work;
     add_tiles(work, 0, g->H, g->W, kUpdTX, kUpdTY);
-    const size_t bytes = sizeof(UpdJob) + work.size() * sizeof(int4);
+    const size_t woff = work_offset(sizeof(UpdJob));
+    const size_t bytes = woff + work.size() * sizeof(int4);
     void* mem = nullptr;
     if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) return SF_ENOMEM;
     std::vector<unsigned char> host(bytes);
     std::memcpy(host.data(), &j, sizeof(UpdJob));
-    std::memcpy(host.data() + sizeof(UpdJob), work.data(), work.size() * sizeof(int4));
+    std::memcpy(host.data() + woff, work.data(), work.size() * sizeof(int4));
     int r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
     if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
     Plan pl;
     pl.jobs = mem;
-    pl.work = (int4*)((unsigned char*)mem + sizeof(UpdJob));
+    pl.work = (int4*)((unsigned char*)mem + woff);
     pl.nwork = (int)work.size();
     pl.smem = upd_smem(init ? 0 : S);
     UpdArgs a;

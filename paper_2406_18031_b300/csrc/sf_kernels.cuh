@@ -40,147 +40,288 @@ struct PropJob {
     int tiles_x;
 };
 
-__host__ __device__ inline size_t prop_smem_bytes(int TX, int TY, int nf, bool c8)
+// Register-resident tiles: a CTA of kPrWarps warps holds a kPrW x kPrH region
+// (the output tile plus an nf-pixel halo on every side).  Warp w owns rows
+// [w kPrRows, (w+1) kPrRows) and lane l owns columns 2l and 2l+1 of them;
+// their 8 channels stay in registers for all nf sub-iterations.  Column-pass
+// neighbours come from the adjacent lanes (warp shuffles); row-pass
+// neighbours are in the same thread except across warps, where each warp
+// publishes its first and last row in shared memory.  Per-pixel geometry
+// (eta, cu) is computed once and parked in shared memory (read only by its
+// owner).
+constexpr int kPrRows = 4;
+constexpr int kPrWarps = 16;
+constexpr int kPrW = 64;
+constexpr int kPrH = kPrRows * kPrWarps;
+constexpr int kPrThreads = 32 * kPrWarps;
+
+__host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // square output tile edge
+
+__host__ __device__ inline size_t prop_smem_bytes()
 {
-    const size_t R = (size_t)(TX + 2 * nf) * (TY + 2 * nf);
-    return (c8 ? 4 : 2) * R * sizeof(float4) + 2 * R * sizeof(float);
+    return (size_t)kPrH * kPrW * sizeof(float4)                 // geometry
+           + 2 * (size_t)kPrWarps * 2 * kPrW * sizeof(float4)   // published rows: s0, s1
+           + (size_t)kPrWarps * 2 * kPrW * sizeof(float);       // published row speeds
 }
 
-// One axis pass over the window [wx0,wx1) x [wy0,wy1) of the region, reading
-// buffer (a0, a1, asp) and writing (b0, b1, bsp).  AXIS 0 = columns (u-hat,
-// Eqs. 59-62), 1 = rows (v-hat, Eqs. 63-66 with reading R2).  The speed
-// written for each pixel is the one the next pass needs (v after a column
-// pass, u after a row pass).
-template <bool C8, int AXIS>
-__device__ __forceinline__ bool axis_pass(const Grid& g, bool has1, int ox, int oy, int RX,
-                                          int wx0, int wx1, int wy0, int wy1,
-                                          const float4* __restrict__ a0, const float4* __restrict__ a1,
-                                          const float* __restrict__ asp,
-                                          float4* __restrict__ b0, float4* __restrict__ b1, float* __restrict__ bsp,
-                                          float dt, float sdt, int flags)
+struct PixGeo {
+    float ex, ey, ez, cu;
+};
+
+// eta and cu = |m'| / (a (1 - eta_x^2)) of the pixel at (x, y) (closed forms
+// at the top of sf_device.cuh)
+__device__ __forceinline__ PixGeo pix_geo(float x, float y, float a)
 {
-    bool bad = false;
-    const int ww = wx1 - wx0;
-    const int n = ww * (wy1 - wy0);
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-        const int ry = wy0 + idx / ww;
-        const int rx = wx0 + idx % ww;
-        const int i = oy + ry, j = ox + rx;
-        const int p = ry * RX + rx;
-        int pm, pp;
-        if (AXIS == 0) {
-            pm = j > 0 ? p - 1 : p;
-            pp = j < g.W - 1 ? p + 1 : p;
-        } else {
-            pm = i > 0 ? p - RX : p;
-            pp = i < g.H - 1 ? p + RX : p;
-        }
-        const float sh = dominant(asp[pm], asp[pp], flags);
-        bad |= dt * fabsf(sh) > 1.0f;
-        const int pn = sh > 0.0f ? pm : pp;  // upwind neighbour
-        const Geo geo = pixel_geometry(g, i, j);
-        const float4 f = a0[p];
-        const float4 fn = a0[pn];
-        const float src = fmaf(geo.ex, f.x, fmaf(geo.ey, f.y, geo.ez * f.z));  // <eta, w>
-        float4 o;
-        o.x = advance_src(f.x, fn.x, sh, src, dt, sdt);
-        o.y = advance_src(f.y, fn.y, sh, src, dt, sdt);
-        o.z = advance_src(f.z, fn.z, sh, src, dt, sdt);
-        o.w = advance_src(f.w, fn.w, sh, src, dt, sdt);
-        b0[p] = o;
-        if (C8 && has1) {
-            const float4 h = a1[p];
-            const float4 hn = a1[pn];
-            float4 q;
-            q.x = advance_src(h.x, hn.x, sh, src, dt, sdt);
-            q.y = advance_src(h.y, hn.y, sh, src, dt, sdt);
-            q.z = advance_src(h.z, hn.z, sh, src, dt, sdt);
-            q.w = advance_nosrc(h.w, hn.w, sh, dt);  // brightness has no source (Eq. 62)
-            b1[p] = q;
-        }
-        bsp[p] = AXIS == 0 ? row_speed(geo, o.x, o.y, o.z) : col_speed(geo, o.x, o.y, o.z);
-    }
-    return bad;
+    const float y2p1 = fmaf(y, y, 1.0f);
+    const float n2 = fmaf(x, x, y2p1);
+    const float r = rsqrtf(n2);
+    const float xa = x + a;
+    const float n2p = fmaf(xa, xa, y2p1);
+    PixGeo o;
+    o.ex = x * r;
+    o.ey = y * r;
+    o.ez = r;
+    o.cu = sqrtf(n2p) * n2 / (a * y2p1);
+    return o;
 }
 
-template <bool C8>
-__global__ void __launch_bounds__(kThreads)
+// One explicit Euler step of an axis pass (Eqs. 59-66) for the four channels
+// of a float4: f - dt [s D + f src] with D the upwind difference (Eqs. 57-58)
+// is A f - |c| (f - f_up) = (A - |c|) f + |c| f_up, c = dt s, A = 1 - sdt src;
+// at an image border the replicated neighbour gives D = 0 (kself = A, knb = 0).
+__device__ __forceinline__ float4 step4(float4 f, float4 up, float kself, float knb)
+{
+    return make_float4(fmaf(kself, f.x, knb * up.x), fmaf(kself, f.y, knb * up.y),
+                       fmaf(kself, f.z, knb * up.z), fmaf(kself, f.w, knb * up.w));
+}
+
+// the same for (dw, Y): Y carries no source term (Eq. 62): (1 - |c|) Y + |c| Y_up
+__device__ __forceinline__ float4 step4y(float4 f, float4 up, float kself, float knb, float kselfy)
+{
+    return make_float4(fmaf(kself, f.x, knb * up.x), fmaf(kself, f.y, knb * up.y),
+                       fmaf(kself, f.z, knb * up.z), fmaf(kselfy, f.w, knb * up.w));
+}
+
+__device__ __forceinline__ float4 shfl_up4(float4 v)
+{
+    return make_float4(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1),
+                       __shfl_up_sync(0xffffffffu, v.z, 1), __shfl_up_sync(0xffffffffu, v.w, 1));
+}
+
+__device__ __forceinline__ float4 shfl_down4(float4 v)
+{
+    return make_float4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
+                       __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
+}
+
+__device__ __forceinline__ float4 sel4(bool c, float4 a, float4 b)
+{
+    return make_float4(c ? a.x : b.x, c ? a.y : b.y, c ? a.z : b.z, c ? a.w : b.w);
+}
+
+// Coefficients of one pixel for one pass: upwind side (true = minus side),
+// weights on itself and on the upwind neighbour, and on itself for Y.
+struct Coef {
+    bool minus;
+    float kself, knb, kselfy;
+};
+
+template <bool LITERAL>
+__device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, bool has_minus, bool has_plus,
+                                             float src, float dt, float sdt, bool& bad, bool count)
+{
+    const float sh = dominant(s_minus, s_plus, LITERAL ? kDominantLiteral : 0);   // Eqs. 55-56
+    const float c = fabsf(dt * sh);
+    bad |= count && (c > 1.0f);                          // Eq. 67
+    Coef k;
+    k.minus = sh > 0.0f;                                 // Eqs. 57-58: backward difference
+    const bool has = k.minus ? has_minus : has_plus;     // replicated border: D = 0
+    const float A = fmaf(-sdt, src, 1.0f);
+    k.knb = has ? c : 0.0f;
+    k.kself = A - k.knb;
+    k.kselfy = 1.0f - k.knb;
+    return k;
+}
+
+template <bool C8, bool LITERAL>
+__global__ void __launch_bounds__(kPrThreads, 1)
 k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int parity, float wscale,
-            int flags, int* __restrict__ status, int TX, int TY)
+            int flags, int* __restrict__ status)
 {
     extern __shared__ float4 smem4[];
+    float4* geo = smem4;                                   // [kPrH][kPrW]
+    float4* pub0 = geo + kPrH * kPrW;                      // [kPrWarps][2][kPrW]
+    float4* pub1 = pub0 + kPrWarps * 2 * kPrW;
+    float* pubv = reinterpret_cast<float*>(pub1 + kPrWarps * 2 * kPrW);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 wk = work[blockIdx.x];
     const PropJob& J = jobs[wk.x];
     const Grid g = J.g;
     const int nf = J.nf;
-    const int RX = TX + 2 * nf, RY = TY + 2 * nf, R = RX * RY;
-    float4* A0 = smem4;
-    float4* A1 = C8 ? A0 + R : A0;
-    float4* B0 = C8 ? A1 + R : A0 + R;
-    float4* B1 = C8 ? B0 + R : B0;
-    float* Asp = reinterpret_cast<float*>(C8 ? B1 + R : B0 + R);
-    float* Bsp = Asp + R;
-
-    const int ox = wk.z - nf, oy = wk.y - nf;  // region origin, image coordinates
-    const int x0 = max(0, -ox), x1 = min(RX, g.W - ox);
-    const int y0 = max(0, -oy), y1 = min(RY, g.H - oy);
-    const bool edge_l = ox + x0 == 0, edge_r = ox + x1 == g.W;
-    const bool edge_t = oy + y0 == 0, edge_b = oy + y1 == g.H;
-
+    const int T = prop_tile(nf);
+    const int ox = wk.z - nf, oy = wk.y - nf;              // region origin, image coordinates
     const float4* __restrict__ in0 = J.in0[parity];
     const float4* __restrict__ in1 = J.in1[parity];
-    const bool has1 = C8 && in1 != nullptr;   // top level inside an 8-channel launch: w, rho only
+    const bool has1 = C8 && in1 != nullptr;               // the top level transports w and rho only
     const float ws = J.apply_wscale ? wscale : 1.0f;
-    {
-        const int ww = x1 - x0, n = ww * (y1 - y0);
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int ry = y0 + idx / ww, rx = x0 + idx % ww;
-            const int i = oy + ry, j = ox + rx;
-            const size_t gi = (size_t)i * g.W + j;
+    const float dt = J.dt;
+    const float sdt = (flags & kSourceSplit) ? 0.5f * dt : dt;
+
+    const int c0 = 2 * lane;                               // my region columns c0, c0 + 1
+    const int j0 = ox + c0, j1 = j0 + 1;                   // ... image columns
+    const int r0 = warp * kPrRows;                         // my first region row
+
+    float4 a[kPrRows][2];       // (w, rho)
+    float4 b[kPrRows][2];       // (dw, Y)
+    float sp[kPrRows][2];       // speed of the next pass of each pixel
+
+    // load (replicated coordinates outside the image: those pixels are never
+    // read by an in-image pixel, whose border neighbours are itself)
+#pragma unroll
+    for (int k = 0; k < kPrRows; ++k) {
+        const int i = oy + r0 + k;
+        const int ic = clampi(i, 0, g.H - 1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = j0 + q;
+            const size_t gi = (size_t)ic * g.W + clampi(j, 0, g.W - 1);
             float4 f = in0[gi];
             f.x *= ws; f.y *= ws; f.z *= ws;
-            A0[ry * RX + rx] = f;
+            a[k][q] = f;
             if (has1) {
                 float4 h = in1[gi];
                 h.x *= ws; h.y *= ws; h.z *= ws;
-                A1[ry * RX + rx] = h;
+                b[k][q] = h;
+            } else {
+                b[k][q] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const Geo geo = pixel_geometry(g, i, j);
-            Asp[ry * RX + rx] = col_speed(geo, f.x, f.y, f.z);
+            const PixGeo G = pix_geo(fmaf((float)j, g.ax, g.bx), fmaf((float)i, g.ay, g.by), g.a);
+            geo[(r0 + k) * kPrW + q * 32 + lane] = make_float4(G.ex, G.ey, G.ez, G.cu);
+            const float s = fmaf(G.ex, f.x, fmaf(G.ey, f.y, G.ez * f.z));
+            sp[k][q] = G.cu * fmaf(-G.ex, s, f.x);        // u of Eq. 54
         }
     }
-    __syncthreads();
 
-    const float dt = J.dt;
-    const float sdt = (flags & kSourceSplit) ? 0.5f * dt : dt;
-    int wx0 = x0, wx1 = x1, wy0 = y0, wy1 = y1;
+    // output tile in region coordinates; CFL counted there only (each image
+    // pixel belongs to exactly one tile, where its value is exact every pass)
+    const bool col_in[2] = {c0 >= nf && c0 < nf + T && j0 < g.W, c0 + 1 >= nf && c0 + 1 < nf + T && j1 < g.W};
     bool bad = false;
+
     for (int it = 0; it < nf; ++it) {
-        wx0 += edge_l ? 0 : 1;
-        wx1 -= edge_r ? 0 : 1;
-        bad |= axis_pass<C8, 0>(g, has1, ox, oy, RX, wx0, wx1, wy0, wy1, A0, A1, Asp, B0, B1, Bsp, dt, sdt, flags);
+        // ---------------- column pass (Eqs. 59-62), neighbours in adjacent lanes
+#pragma unroll
+        for (int k = 0; k < kPrRows; ++k) {
+            const int r = r0 + k;
+            const bool row_in = r >= nf && r < nf + T && oy + r < g.H;
+            const float uL = __shfl_up_sync(0xffffffffu, sp[k][1], 1);    // column c0 - 1
+            const float uR = __shfl_down_sync(0xffffffffu, sp[k][0], 1);  // column c0 + 2
+            const float4 G0 = geo[r * kPrW + lane], G1 = geo[r * kPrW + 32 + lane];
+            const float src0 = fmaf(G0.x, a[k][0].x, fmaf(G0.y, a[k][0].y, G0.z * a[k][0].z));
+            const float src1 = fmaf(G1.x, a[k][1].x, fmaf(G1.y, a[k][1].y, G1.z * a[k][1].z));
+            // replicated border: the neighbour beyond the image edge is the pixel itself
+            const bool m0 = j0 > 0, p0 = j0 < g.W - 1, m1 = j1 > 0, p1 = j1 < g.W - 1;
+            const float sm0 = m0 ? uL : sp[k][0], spp0 = p0 ? sp[k][1] : sp[k][0];
+            const float sm1 = m1 ? sp[k][0] : sp[k][1], spp1 = p1 ? uR : sp[k][1];
+            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0, p0, src0, dt, sdt, bad, row_in && col_in[0]);
+            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1, p1, src1, dt, sdt, bad, row_in && col_in[1]);
+            const float4 aL = shfl_up4(a[k][1]), aR = shfl_down4(a[k][0]);
+            const float4 na0 = step4(a[k][0], k0.minus ? aL : a[k][1], k0.kself, k0.knb);
+            const float4 na1 = step4(a[k][1], k1.minus ? a[k][0] : aR, k1.kself, k1.knb);
+            if (has1) {
+                const float4 bL = shfl_up4(b[k][1]), bR = shfl_down4(b[k][0]);
+                const float4 nb0 = step4y(b[k][0], sel4(k0.minus, bL, b[k][1]), k0.kself, k0.knb, k0.kselfy);
+                const float4 nb1 = step4y(b[k][1], sel4(k1.minus, b[k][0], bR), k1.kself, k1.knb, k1.kselfy);
+                b[k][0] = nb0; b[k][1] = nb1;
+            }
+            a[k][0] = na0; a[k][1] = na1;
+            sp[k][0] = G0.w * fmaf(G0.z, na0.y, -G0.y * na0.z);   // v of Eq. 54 for the row pass
+            sp[k][1] = G1.w * fmaf(G1.z, na1.y, -G1.y * na1.z);
+        }
+        // publish my first and last rows for the neighbouring warps
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = e ? kPrRows - 1 : 0;
+            const int base = (warp * 2 + e) * kPrW + lane;
+            pub0[base] = a[k][0]; pub0[base + 32] = a[k][1];
+            if (has1) { pub1[base] = b[k][0]; pub1[base + 32] = b[k][1]; }
+            pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
+        }
         __syncthreads();
-        wy0 += edge_t ? 0 : 1;
-        wy1 -= edge_b ? 0 : 1;
-        bad |= axis_pass<C8, 1>(g, has1, ox, oy, RX, wx0, wx1, wy0, wy1, B0, B1, Bsp, A0, A1, Asp, dt, sdt, flags);
-        __syncthreads();
+        // ---------------- row pass (Eqs. 63-66, reading R2), neighbours in rows k -+ 1
+        float4 prev_a[2], prev_b[2];
+        float prev_v[2];
+        {   // the row above my first row: the last row of the warp above (or myself at the region edge)
+            const int base = ((warp > 0 ? warp - 1 : warp) * 2 + (warp > 0 ? 1 : 0)) * kPrW + lane;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                prev_a[q] = warp > 0 ? pub0[base + 32 * q] : a[0][q];
+                prev_b[q] = (warp > 0 && has1) ? pub1[base + 32 * q] : b[0][q];
+                prev_v[q] = warp > 0 ? pubv[base + 32 * q] : sp[0][q];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPrRows; ++k) {
+            const int r = r0 + k, i = oy + r;
+            const bool row_in = r >= nf && r < nf + T && i < g.H;
+            float4 next_a[2], next_b[2];
+            float next_v[2];
+            if (k + 1 < kPrRows) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) { next_a[q] = a[k + 1][q]; next_b[q] = b[k + 1][q]; next_v[q] = sp[k + 1][q]; }
+            } else {
+                const bool below = warp + 1 < kPrWarps;
+                const int base = ((below ? warp + 1 : warp) * 2 + (below ? 0 : 1)) * kPrW + lane;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    next_a[q] = below ? pub0[base + 32 * q] : a[k][q];
+                    next_b[q] = (below && has1) ? pub1[base + 32 * q] : b[k][q];
+                    next_v[q] = below ? pubv[base + 32 * q] : sp[k][q];
+                }
+            }
+            const bool mi = i > 0, pi = i < g.H - 1;
+            float4 na[2], nb[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 G = geo[r * kPrW + q * 32 + lane];
+                const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
+                const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
+                const Coef kk = coefficients<LITERAL>(vm, vp, mi, pi, src, dt, sdt, bad, row_in && col_in[q]);
+                na[q] = step4(a[k][q], kk.minus ? prev_a[q] : next_a[q], kk.kself, kk.knb);
+                if (has1) nb[q] = step4y(b[k][q], sel4(kk.minus, prev_b[q], next_b[q]), kk.kself, kk.knb, kk.kselfy);
+                prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
+                a[k][q] = na[q];
+                if (has1) b[k][q] = nb[q];
+                // u of Eq. 54 for the next column pass
+                const float s = fmaf(G.x, na[q].x, fmaf(G.y, na[q].y, G.z * na[q].z));
+                sp[k][q] = G.w * fmaf(-G.x, s, na[q].x);
+            }
+        }
+        __syncthreads();   // the published rows are overwritten by the next column pass
     }
-    // the tile [nf, nf + TX) x [nf, nf + TY) is valid now; write its in-image part
-    {
-        const int tx0 = max(nf, x0), tx1 = min(nf + TX, x1);
-        const int ty0 = max(nf, y0), ty1 = min(nf + TY, y1);
-        const int ww = tx1 - tx0, n = ww * (ty1 - ty0);
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int ry = ty0 + idx / ww, rx = tx0 + idx % ww;
-            const size_t gi = (size_t)(oy + ry) * g.W + (ox + rx);
-            J.out0[gi] = A0[ry * RX + rx];
-            if (has1) J.out1[gi] = A1[ry * RX + rx];
+
+    // write the output tile (its in-image part)
+#pragma unroll
+    for (int k = 0; k < kPrRows; ++k) {
+        const int r = r0 + k, i = oy + r;
+        if (r < nf || r >= nf + T || i >= g.H) continue;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!col_in[q]) continue;
+            const size_t gi = (size_t)i * g.W + (j0 + q);
+            J.out0[gi] = a[k][q];
+            if (has1) J.out1[gi] = b[k][q];
         }
     }
     if ((flags & kCheckCfl) && status) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusCfl);
     }
 }
+
+// n / d for 0 <= n < 2^16 and 1 <= d < 2^16 with a precomputed multiplier
+// m = ceil(2^32 / d) (exact in that range); d == 1 has no 32-bit multiplier.
+__device__ __forceinline__ unsigned div_magic(int d) { return d > 1 ? 0xFFFFFFFFu / (unsigned)d + 1u : 0u; }
+__device__ __forceinline__ int fast_div(int n, unsigned m, int d) { return d > 1 ? (int)__umulhi((unsigned)n, m) : n; }
 
 // --------------------------------------------------------------------------
 // update
@@ -192,6 +333,7 @@ struct UpdJob {
     int top;
     int S;                 // smoothing passes
     float g1, g2, g3, g4, g5;
+    float inv45, inv5;     // 1 / (g4 + g5) and 1 / g5 (Eq. 52 with and without a measurement)
     const float4* s0_cur[2];
     const float4* s1_cur[2];
     const float4* p0;
@@ -262,15 +404,37 @@ __host__ __device__ inline void upd_layout(int TX, int TY, int S, size_t* off_F,
     const int SX = TX + 4 * S, SY = TY + 4 * S;        // solve region
     const int DX = SX + 4, DY = SY + 4;                // image region (model halo 2)
     const size_t data = (size_t)DX * DY + (size_t)(SX + 2) * (SY + 2) + 2 * (size_t)DY * SX;  // floats
-    const size_t tmp = 3 * (size_t)SX * SY;            // smoothing temporary, aliases the data region
+    const size_t tmp = 4 * (size_t)SX * SY;            // smoothing temporary (float4), aliases the data region
     const size_t first = ((data > tmp ? data : tmp) + 3) & ~(size_t)3;
-    *off_F = first;
-    *off_R = first + ((3 * (size_t)SX * SY + 3) & ~(size_t)3);
+    *off_F = first;                                    // solution, float4 per pixel
+    *off_R = first + 4 * (size_t)SX * SY;
     *off_Y = *off_R + (size_t)TX * TY;
     *total = (*off_Y + (size_t)TX * TY) * sizeof(float);
 }
 
-__global__ void __launch_bounds__(kThreads)
+constexpr int kUpdThreads = 512;
+
+// eta, dd = a/|m'| and 1 - eta_x^2 at pixel (i, j) without divisions
+__device__ __forceinline__ Geo update_geometry(const Grid& g, int i, int j)
+{
+    const float x = fmaf((float)j, g.ax, g.bx);
+    const float y = fmaf((float)i, g.ay, g.by);
+    const float y2p1 = fmaf(y, y, 1.0f);
+    const float n2 = fmaf(x, x, y2p1);
+    const float r = rsqrtf(n2);
+    const float xa = x + g.a;
+    const float n2p = fmaf(xa, xa, y2p1);
+    Geo o;
+    o.ex = x * r;
+    o.ey = y * r;
+    o.ez = r;
+    o.omx2 = y2p1 * (r * r);
+    o.dd = g.a * rsqrtf(n2p);
+    o.cu = 0.0f;
+    return o;
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
 k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs args, int TX, int TY)
 {
     extern __shared__ float smf[];
@@ -285,15 +449,16 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
     float* Rd = Yd + DX * DY;                         // [SY+2][SX+2] level inverse depth
     float* H0 = Rd + RXd * (SY + 2);                  // [DY][SX] sum g Y
     float* H1 = H0 + DY * SX;                         // [DY][SX] sum g d Y
-    float* F = smf + offF;                            // [SY][SX][3] solution
-    float* T = smf;                                   // smoothing temporary (aliases the above)
+    float4* F = reinterpret_cast<float4*>(smf + offF);   // [SY][SX] solution (.w unused)
+    float4* T = reinterpret_cast<float4*>(smf);          // smoothing temporary (aliases the above)
     float* Ro = smf + offR;                           // [TY][TX] new inverse depth
     float* Yo = smf + offY;                           // [TY][TX] new Y-hat
 
     const int sx0 = wk.z - 2 * S, sy0 = wk.y - 2 * S;  // solve-region origin (image coords)
     // 1. level data with replicated border
+    const unsigned mDX = div_magic(DX), mSX = div_magic(SX), mTX = div_magic(TX);
     for (int idx = threadIdx.x; idx < DX * DY; idx += blockDim.x) {
-        const int dy = idx / DX, dx = idx % DX;
+        const int dy = fast_div(idx, mDX, DX), dx = idx - dy * DX;
         const int i = clampi(sy0 - 2 + dy, 0, g.H - 1), j = clampi(sx0 - 2 + dx, 0, g.W - 1);
         float y, r;
         level_data(J.level, args, i, j, y, r);
@@ -303,7 +468,7 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
     __syncthreads();
     // 2. horizontal 5-tap passes (g = [1 4 6 4 1]/16, and g*d)
     for (int idx = threadIdx.x; idx < DY * SX; idx += blockDim.x) {
-        const int dy = idx / SX, sx = idx % SX;
+        const int dy = fast_div(idx, mSX, SX), sx = idx - dy * SX;
         const float* row = Yd + dy * DX + sx;  // taps at offsets -2..2 of column sx+2
         const float m2 = row[0], m1 = row[1], c = row[2], p1 = row[3], p2 = row[4];
         H0[idx] = (m2 + p2) * 0.0625f + (m1 + p1) * 0.25f + c * 0.375f;
@@ -313,7 +478,7 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
     // 3. models, solve, blend for every in-image pixel of the solve region
     const int parity = args.parity;
     for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) {
-        const int sy = idx / SX, sx = idx % SX;
+        const int sy = fast_div(idx, mSX, SX), sx = idx - sy * SX;
         const int i = sy0 + sy, j = sx0 + sx;
         if (i < 0 || i >= g.H || j < 0 || j >= g.W) continue;
         const float* c0 = H0 + sy * SX + sx;  // rows sy..sy+4 of the image region = offsets -2..2
@@ -339,7 +504,7 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
                 e2 = (hp && hm) ? (fabsf(dp) <= fabsf(dm) ? dp : dm) : (hp ? dp : (hm ? dm : 0.0f));
             }
         }
-        const Geo geo = pixel_geometry(g, i, j);
+        const Geo geo = update_geometry(g, i, j);
         const float exy = geo.ex * geo.ey, exz = geo.ex * geo.ez;
         // lifts dmu B d (Eqs. 31, 34, reading R4)
         const float gx = geo.dd * (geo.omx2 * d1);
@@ -397,12 +562,10 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
             x0 = px - fmaf(c1, rX, c2 * qX);
             x1 = py - fmaf(c1, rY, c2 * qY);
             x2 = pz - fmaf(c1, rZ, c2 * qZ);
-            const float G4 = valid ? J.g4 : 0.0f;  // Eq. 52
-            rho_new = fmaf(G4, rc, J.g5 * rpred) / (G4 + J.g5);
+            // Eq. 52; without a measurement gamma4 = 0
+            rho_new = valid ? fmaf(J.g4, rc, J.g5 * rpred) * J.inv45 : (J.g5 * rpred) * J.inv5;
         }
-        F[3 * idx + 0] = x0;
-        F[3 * idx + 1] = x1;
-        F[3 * idx + 2] = x2;
+        F[idx] = make_float4(x0, x1, x2, 0.0f);
         const int ty = sy - 2 * S, tx = sx - 2 * S;
         if (ty >= 0 && ty < TY && tx >= 0 && tx < TX) {
             Ro[ty * TX + tx] = rho_new;
@@ -428,16 +591,18 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
         // horizontal sums over rows of the current y window
         {
             const int ww = wx1 - wx0, n = ww * (wy1 - wy0);
+            const unsigned mw = div_magic(ww);
             for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-                const int sy = wy0 + idx / ww, sx = wx0 + idx % ww;
-                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+                const int qq = fast_div(idx, mw, ww);
+                const int sy = wy0 + qq, sx = wx0 + (idx - qq * ww);
+                const float4* row = F + sy * SX;
+                float4 acc = row[clampi(sx - 2, ix0, ix1)];
 #pragma unroll
-                for (int d = -2; d <= 2; ++d) {
-                    const int q = sy * SX + clampi(sx + d, ix0, ix1);
-                    a0 += F[3 * q]; a1 += F[3 * q + 1]; a2 += F[3 * q + 2];
+                for (int d = -1; d <= 2; ++d) {
+                    const float4 v = row[clampi(sx + d, ix0, ix1)];
+                    acc.x += v.x; acc.y += v.y; acc.z += v.z;
                 }
-                const int q = sy * SX + sx;
-                T[3 * q] = a0; T[3 * q + 1] = a1; T[3 * q + 2] = a2;
+                T[sy * SX + sx] = acc;
             }
         }
         __syncthreads();
@@ -445,18 +610,17 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
         wy1 -= eb ? 0 : 2;
         {
             const int ww = wx1 - wx0, n = ww * (wy1 - wy0);
+            const unsigned mw = div_magic(ww);
             for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-                const int sy = wy0 + idx / ww, sx = wx0 + idx % ww;
-                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+                const int qq = fast_div(idx, mw, ww);
+                const int sy = wy0 + qq, sx = wx0 + (idx - qq * ww);
+                float4 acc = T[clampi(sy - 2, iy0, iy1) * SX + sx];
 #pragma unroll
-                for (int d = -2; d <= 2; ++d) {
-                    const int q = clampi(sy + d, iy0, iy1) * SX + sx;
-                    a0 += T[3 * q]; a1 += T[3 * q + 1]; a2 += T[3 * q + 2];
+                for (int d = -1; d <= 2; ++d) {
+                    const float4 v = T[clampi(sy + d, iy0, iy1) * SX + sx];
+                    acc.x += v.x; acc.y += v.y; acc.z += v.z;
                 }
-                const int q = sy * SX + sx;
-                F[3 * q] = a0 * (1.0f / 25.0f);
-                F[3 * q + 1] = a1 * (1.0f / 25.0f);
-                F[3 * q + 2] = a2 * (1.0f / 25.0f);
+                F[sy * SX + sx] = make_float4(acc.x * (1.0f / 25.0f), acc.y * (1.0f / 25.0f), acc.z * (1.0f / 25.0f), 0.0f);
             }
         }
         __syncthreads();
@@ -466,12 +630,12 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
         float4* __restrict__ o0 = J.s0_new[parity ^ 1];
         float4* __restrict__ o1 = J.s1_new[parity ^ 1];
         for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-            const int ty = idx / TX, tx = idx % TX;
+            const int ty = fast_div(idx, mTX, TX), tx = idx - ty * TX;
             const int i = wk.y + ty, j = wk.z + tx;
             if (i >= g.H || j >= g.W) continue;
             const int q = (ty + 2 * S) * SX + (tx + 2 * S);
             const size_t gi = (size_t)i * g.W + j;
-            const float4 sol = make_float4(F[3 * q], F[3 * q + 1], F[3 * q + 2], 0.0f);
+            const float4 sol = F[q];
             if (J.top) {
                 o0[gi] = make_float4(sol.x, sol.y, sol.z, Ro[idx]);
                 o1[gi] = make_float4(0.0f, 0.0f, 0.0f, Yo[idx]);

@@ -47,6 +47,14 @@ def flow_field(rng, H, W, dmu, max_px, with_step=True):
     return (w * dmu[..., None]).astype(np.float32)
 
 
+def cfl_scaled(w, eta, B, dmu, max_px):
+    """Scale a flow field (rad/frame) so its largest pixel speed (Eq. 54:
+    B^T P w / dmu) is max_px."""
+    Pw = w - eta * np.einsum("hwc,hwc->hw", eta, w)[..., None]
+    sp = np.abs(np.einsum("hwkc,hwc->hwk", B, Pw)) / dmu[..., None]
+    return (w * (max_px / max(sp.max(), 1e-30))).astype(np.float32)
+
+
 def f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 

@@ -38,7 +38,10 @@ def test_propagate_matches_oracle(H, W, N, top, flags):
     fx = fy = W / 2.0 + 3.0
     cx, cy = W / 2.0 - 1.5, H / 2.0 + 0.5
     g, eta, B, dmu = gu.level_grid(H, W, fx, fy, cx, cy, 1)
-    w = gu.flow_field(rng, H, W, dmu, max_px=0.8 * N)
+    # pixel speeds up to 0.8 N (Eq. 67 holds) but at most a tenth of the grid per
+    # frame: on tiny wide-angle grids larger flows are O(1) rad/frame and the
+    # source term -w<eta,w> blows the exact solution up
+    w = gu.cfl_scaled(gu.flow_field(rng, H, W, dmu, max_px=1.0), eta, B, dmu, min(0.8 * N, 0.1 * min(H, W)))
     rho = gu.f32(0.2 + 0.15 * gu.smooth_field(rng, H, W))
     dw = None if top else gu.f32(gu.flow_field(rng, H, W, dmu, max_px=0.3 * N) * 0.5)
     Y = None if top else gu.f32(0.5 + 0.4 * gu.smooth_field(rng, H, W, n_waves=6))
@@ -57,7 +60,10 @@ def test_propagate_matches_oracle(H, W, N, top, flags):
         out1 = o1.cpu().numpy()
         assert gu.px_err(out1[..., :3], rdw, dmu) <= gu.FLOW_TOL_PX
         assert np.abs(out1[..., 3] - ry).max() <= gu.Y_TOL
-    assert cfl <= 1.0 and int(status.item()) == 0
+    # the device flags Eq. 67 exactly when the oracle's CFL number exceeds 1
+    # (cases within 1e-5 of the bound may round either way)
+    if abs(cfl - 1.0) > 1e-5:
+        assert bool(int(status.item()) & 1) == (cfl > 1.0), cfl
 
 
 def test_propagate_flags_cfl_violation():
