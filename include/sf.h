@@ -174,6 +174,30 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale,
                  const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
                  int* status, void* stream);
 
+/* sf_propagate without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory --
+ * code running inside a CUDA graph capture or a host callback, real-time
+ * loops that must not touch the allocator, hosts whose memory pools belong
+ * to another framework.  It computes exactly what sf_propagate computes,
+ * with the same arguments, but keeps the fields passed between launches and
+ * the launch descriptors in a file-scope device array of 33 MiB that every
+ * GPU using this library holds until the process exits; it calls no
+ * cudaMalloc, cudaMallocAsync or cudaFree.
+ *   - H * W must not exceed 1,048,576 pixels (e.g. 1024 x 1024); larger
+ *     grids return SF_EINVAL (use sf_propagate).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents (every
+ *     value a call reads there it has written first).  Calls whose work
+ *     overlaps on the GPU -- on different streams or different host threads
+ *     without ordering between them -- race on the array.
+ *   - The call enqueues two small descriptor kernels ahead of each
+ *     propagation launch and returns without waiting for the stream. */
+int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float wscale,
+                         const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
+                         int* status, void* stream);
+
 /* Update of one level (Sec. 4.2, 4.3, 4.5; Eqs. 30-34, 42-52) with S
  * smoothing passes.  `level` is 1-based; the level's image and inverse
  * depth are built from the level-1 inputs (H1 x W1 device arrays) by 2x2

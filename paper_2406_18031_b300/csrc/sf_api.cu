@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -728,3 +729,120 @@ int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const flo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// allocation-free propagation (sf_propagate_noalloc)
+//
+// Callers that cannot allocate device memory -- code running inside a CUDA
+// graph capture or a host callback, real-time loops that must not touch the
+// allocator, or hosts whose memory pools are owned by another framework --
+// get sf_propagate's result without cudaMalloc/cudaMallocAsync/cudaFree: the
+// intermediate fields and the launch descriptors live in one file-scope
+// device array that every GPU using this library holds until exit.
+// ---------------------------------------------------------------------------
+
+namespace {
+constexpr size_t kNoAllocMaxPixels = size_t(1) << 20;                      // H * W per call
+constexpr size_t kNoAllocDescBytes = size_t(1) << 20;                      // job + tile list
+constexpr size_t kNoAllocFieldBytes = 2 * kNoAllocMaxPixels * sizeof(float4);  // (s0, s1) between launches
+constexpr size_t kNoAllocJobBytes = 256;                                   // job slot ahead of the tiles
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDescBytes + kNoAllocFieldBytes];
+
+namespace {
+
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices];   // device address of the array, per device
+std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_scratch on the current device; looked up once
+// per device (the host-side name is only a stand-in, not a device address).
+int noalloc_scratch(unsigned char** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SF_ECUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return SF_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SF_ECUDA;
+        g_noalloc_addr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SF_OK;
+}
+
+__global__ void k_noalloc_store_job(PropJob j, PropJob* dst) { *dst = j; }
+
+__global__ void k_noalloc_fill_tiles(int4* work, int tiles_x, int ntiles, int T)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+        work[t] = make_int4(0, (t / tiles_x) * T, (t % tiles_x) * T, 0);
+}
+
+}  // namespace
+
+extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float wscale, const float* s0_in,
+                                    const float* s1_in, float* s0_out, float* s1_out, int* status, void* stream)
+{
+    if (!g || g->H < 1 || g->W < 1 || N < 1 || !s0_in || !s0_out) return SF_EINVAL;
+    if ((s1_in == nullptr) != (s1_out == nullptr)) return SF_EINVAL;
+    if (!valid_ptr_align(s0_in) || !valid_ptr_align(s0_out) || !valid_ptr_align(s1_in) || !valid_ptr_align(s1_out))
+        return SF_EINVAL;
+    const size_t n = (size_t)g->H * g->W;
+    if (n > kNoAllocMaxPixels) return SF_EINVAL;                 // larger frames: use sf_propagate
+    const int nseg = ceil_div(N, kNfMax);
+    for (int k = 0; k < nseg; ++k) {                             // every tile list must fit
+        const int T = prop_tile(N / nseg + (k < N % nseg ? 1 : 0));
+        const size_t tiles = (size_t)ceil_div(g->H, T) * ceil_div(g->W, T);
+        if (kNoAllocJobBytes + tiles * sizeof(int4) > kNoAllocDescBytes) return SF_EINVAL;
+    }
+    unsigned char* base = nullptr;
+    int r = noalloc_scratch(&base);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool c8 = s1_in != nullptr;
+    PropJob* djob = (PropJob*)base;
+    int4* dwork = (int4*)(base + kNoAllocJobBytes);
+    float4* t0 = (float4*)(base + kNoAllocDescBytes);
+    float4* t1 = t0 + kNoAllocMaxPixels;
+    const float4* in0 = (const float4*)s0_in;
+    const float4* in1 = (const float4*)s1_in;
+    for (int k = 0; k < nseg && !r; ++k) {
+        // the last launch writes the outputs; earlier ones alternate with the
+        // scratch fields so that this holds (as in sf_propagate)
+        const bool to_out = ((nseg - 1 - k) % 2) == 0;
+        float4* o0 = to_out ? (float4*)s0_out : t0;
+        float4* o1 = c8 ? (to_out ? (float4*)s1_out : t1) : nullptr;
+        PropJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.g = make_grid(*g);
+        j.in0[0] = j.in0[1] = in0;
+        j.in1[0] = j.in1[1] = in1;
+        j.out0 = o0;
+        j.out1 = o1;
+        j.nf = N / nseg + (k < N % nseg ? 1 : 0);
+        j.apply_wscale = k == 0;
+        j.dt = 1.0f / (float)N;
+        const int T = prop_tile(j.nf);
+        j.tiles_x = ceil_div(g->W, T);
+        const int ntiles = j.tiles_x * ceil_div(g->H, T);
+        // descriptors are written by the device in stream order: the previous
+        // launch has finished reading them when these kernels run
+        k_noalloc_store_job<<<1, 1, 0, st>>>(j, djob);
+        k_noalloc_fill_tiles<<<std::min(ceil_div(ntiles, 256), 1024), 256, 0, st>>>(dwork, j.tiles_x, ntiles, T);
+        r = last_error();
+        if (r) break;
+        Plan pl;
+        pl.c8 = c8;
+        pl.smem = prop_smem_bytes();
+        pl.jobs = djob;
+        pl.work = dwork;
+        pl.nwork = ntiles;
+        r = launch_propagate(pl, 0, wscale, flags, status, st);
+        in0 = o0;
+        in1 = o1;
+    }
+    return r;
+}

@@ -42,8 +42,8 @@ class CGrid(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
-           "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_update",
-           "sf_reconstruct"]
+           "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
+           "sf_update", "sf_reconstruct"]
 
 
 def lib():
@@ -71,6 +71,7 @@ def lib():
         L.sf_strerror.argtypes = [i]
         L.sf_strerror.restype = ctypes.c_char_p
         L.sf_propagate.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
+        L.sf_propagate_noalloc.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
         L.sf_update.argtypes = [P(CGrid), i, i, i, i, P(f), f, vp, vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sf_reconstruct.argtypes = [i, P(CGrid), P(vp), P(vp), f, vp, vp, i, vp, vp]
         _lib = L
@@ -219,6 +220,14 @@ def propagate(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wsca
     """Stage entry point ``sf_propagate`` on [H, W, 4] float32 CUDA tensors."""
     return _check(lib().sf_propagate(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in), _ptr(s1_in),
                                      _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)), "sf_propagate")
+
+
+def propagate_noalloc(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
+                      stream=None):
+    """``sf_propagate_noalloc``: sf_propagate without allocating (frames up to 1024 x 1024 pixels)."""
+    return _check(lib().sf_propagate_noalloc(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in),
+                                             _ptr(s1_in), _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)),
+                  "sf_propagate_noalloc")
 
 
 def update(g: CGrid, level, top, S, init, gamma, lambda_ref, image, rng, s0_new, s1_new, s0_cur=None, s1_cur=None,
