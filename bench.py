@@ -232,6 +232,14 @@ def run_ours(args):
     filt = sf.Filter(H, W, seq.levels, params)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def evict_l2(k):
+        # write a buffer larger than L2, then read another: the timed step
+        # starts with a cold L2 that holds clean lines, so it neither finds
+        # its state cached nor pays for the write-back of the flush
+        flush.fill_(float(k))
+        return flush_rd.sum()
 
     def step(k):
         kk = k % seq.frames
@@ -248,7 +256,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     time.sleep(0.3)
     for k in range(args.steps):
-        flush.fill_(float(k))                       # evict L2 between timed steps
+        evict_l2(k)                                 # cold L2 between timed steps
         starts[k].record(stream)
         step(1 + args.warmup + k)
         ends[k].record(stream)
@@ -266,7 +274,7 @@ def run_ours(args):
     # launching stream: per-kernel durations and shares
     filt.profile(True)
     for k in range(args.steps):
-        flush.fill_(float(k))
+        evict_l2(k)
         step(1 + args.warmup + args.steps + k)
     torch.cuda.synchronize()
     filt.profile(False)
@@ -300,7 +308,7 @@ def run_ours(args):
             "config": {"workload": "scene512: 512x512, 2 levels, N=[8,4], smooth=[2,4], 600 Hz, max flow 8 px/frame"
                        + ("" if args.size == 512 else f", tiled to {args.size}x{args.size} (profiling case)"),
                        "global_batch": ws, "streams_per_gpu": 1, "parallelism": f"replicas x{ws}",
-                       "l2": "flushed between timed steps (256 MiB write)"},
+                       "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)"},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},

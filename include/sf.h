@@ -147,6 +147,44 @@ void sf_destroy(sf_ctx* c);
 const char* sf_strerror(int code);
 
 /* ------------------------------------------------------------------------
+ * Batched streams.  One sf_batch holds n independent filters (camera
+ * streams) of possibly different sizes and level counts and runs a frame of
+ * all of them with one set of launches (the propagation launches, one
+ * update launch and the reconstruction cascade), so that many small streams
+ * fill the GPU; each stream computes exactly what its own sf_step would.
+ * In steady state (same dt as the previous frame, a non-default stream) the
+ * frame is replayed from a CUDA graph captured on an earlier frame.
+ * ---------------------------------------------------------------------- */
+
+typedef struct sf_batch sf_batch;
+
+/* Create n streams: stream s is H[s] x W[s] with levels[s] levels and the
+ * parameters params[s] (validated as in sf_create; all streams must use the
+ * same SF_DOMINANT_LITERAL / SF_SOURCE_SPLIT choice).  The batch owns one
+ * device input slot (image, range) and one output slot (flow 3 x H x W,
+ * inverse depth) per stream, zero-filled; see sf_batch_buffers. */
+int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params,
+                    sf_batch** out);
+
+/* Device pointers of stream s's slots (any may be NULL): the caller writes
+ * the frame's image and range there (on the step's stream or before it) and
+ * reads the flow (rad/s) and inverse depth there after the step.  The
+ * pointers stay valid until sf_batch_destroy. */
+int sf_batch_buffers(sf_batch* b, int s, float** image, float** range, float** flow, float** invdepth);
+
+/* One frame of every stream on `stream` (asynchronous; dt in seconds is the
+ * same for every stream of the batch; the first step initialises). */
+int sf_batch_step(sf_batch* b, float dt, void* stream);
+
+/* As sf_status, for the whole batch. */
+int sf_batch_status(sf_batch* b);
+
+/* Kernel launches of one steady-state sf_batch_step. */
+int sf_batch_launches_per_step(const sf_batch* b);
+
+void sf_batch_destroy(sf_batch* b);
+
+/* ------------------------------------------------------------------------
  * Stage entry points.  Each runs one stage of the frame on caller-owned
  * device buffers with the same kernels that sf_step uses, so that every
  * stage can be checked on its own.  They upload a small launch descriptor

@@ -39,11 +39,21 @@ Grid make_grid(const sf_grid& s)
     return g;
 }
 
+// the dynamic shared-memory limit of a kernel, raised once per device and size
+// (so that launches inside a graph capture never need the attribute call)
 int set_smem_attr(const void* fn, size_t bytes)
 {
     if (bytes <= 48 * 1024) return SF_OK;
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, const void*>, size_t>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SF_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : done)
+        if (e.first.first == dev && e.first.second == fn && e.second >= bytes) return SF_OK;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return SF_ECUDA;
+    done.push_back({{dev, fn}, bytes});
     return SF_OK;
 }
 
@@ -846,3 +856,367 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
     }
     return r;
 }
+
+// ---------------------------------------------------------------------------
+// batched streams (sf_batch_*): many independent filters of uneven sizes in
+// one set of launches per frame, captured in a CUDA graph
+// ---------------------------------------------------------------------------
+
+struct sf_batch_stream {
+    int H, W, L;
+    sf_params p;
+    sf_level_state lv[SF_MAX_LEVELS];
+    float* image;      // device input/output slots owned by the batch
+    float* range;
+    float* flow;
+    float* inv;
+};
+
+struct ReconPlan {
+    ReconJob* jobs = nullptr;
+    int2* work = nullptr;
+    int nwork = 0;
+};
+
+struct sf_batch {
+    std::vector<sf_batch_stream> st;
+    int parity = 0;
+    int initialised = 0;
+    float dt_prev = 0.0f;
+    int flags = 0;
+    int* status = nullptr;
+    std::vector<Plan> prop;
+    Plan upd, init;
+    std::vector<ReconPlan> recon;   // one per cascade depth
+    void* io = nullptr;             // the input/output slots of every stream
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    float graph_dt[2] = {0.0f, 0.0f};
+    int steps_plain = 0;
+};
+
+namespace {
+
+void destroy_batch(sf_batch* b)
+{
+    if (!b) return;
+    for (int q = 0; q < 2; ++q)
+        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
+    for (auto& pl : b->prop) free_plan(pl);
+    free_plan(b->upd);
+    free_plan(b->init);
+    for (auto& r : b->recon) { cudaFree(r.jobs); cudaFree(r.work); }
+    for (auto& s : b->st)
+        for (int h = 0; h < s.L; ++h) cudaFree(s.lv[h].block);
+    cudaFree(b->io);
+    cudaFree(b->status);
+    delete b;
+}
+
+int batch_plans(sf_batch* b, cudaStream_t st)
+{
+    // ---- propagation: launch k holds segment k of every (stream, level)
+    int maxseg = 0;
+    for (auto& s : b->st)
+        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, kNfMax));
+    b->prop.resize(maxseg);
+    for (int k = 0; k < maxseg; ++k) {
+        std::vector<PropJob> jobs;
+        std::vector<int4> work;
+        bool c8 = false;
+        // longest tiles first: larger nf (more passes) before smaller
+        for (int want = kNfMax; want >= 1; --want) {
+            for (auto& s : b->st) {
+                for (int h = 0; h < s.L; ++h) {
+                    sf_level_state& lv = s.lv[h];
+                    const int nseg = ceil_div(lv.N, kNfMax);
+                    if (k >= nseg) continue;
+                    const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
+                    if (nf != want) continue;
+                    const bool top = h == s.L - 1;
+                    auto out_of = [&](int seg, float4*& o0, float4*& o1) {
+                        const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
+                        o0 = to_pred ? lv.p0 : lv.t0;
+                        o1 = to_pred ? lv.p1 : lv.t1;
+                    };
+                    PropJob j;
+                    std::memset(&j, 0, sizeof(j));
+                    j.g = make_grid(lv.grid);
+                    if (k == 0) {
+                        j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+                        j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
+                        j.apply_wscale = 1;
+                    } else {
+                        float4 *o0, *o1;
+                        out_of(k - 1, o0, o1);
+                        j.in0[0] = j.in0[1] = o0;
+                        j.in1[0] = j.in1[1] = top ? nullptr : o1;
+                    }
+                    out_of(k, j.out0, j.out1);
+                    if (top) j.out1 = nullptr;
+                    j.nf = nf;
+                    j.dt = 1.0f / (float)lv.N;
+                    j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
+                    jobs.push_back(j);
+                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
+                    c8 |= !top;
+                }
+            }
+        }
+        b->prop[k].c8 = c8;
+        b->prop[k].smem = prop_smem_bytes();
+        int r = upload_plan(jobs, work, b->prop[k], st);
+        if (r) return r;
+    }
+    // ---- update and initialisation: every (stream, level), top levels first
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool init = pass == 1;
+        std::vector<UpdJob> jobs;
+        std::vector<int4> work;
+        size_t smem = 0;
+        for (int top_first = 1; top_first >= 0; --top_first) {
+            for (auto& s : b->st) {
+                for (int h = 0; h < s.L; ++h) {
+                    if ((h == s.L - 1) != (top_first == 1)) continue;
+                    sf_level_state& lv = s.lv[h];
+                    UpdJob j;
+                    std::memset(&j, 0, sizeof(j));
+                    j.g = make_grid(lv.grid);
+                    j.level = h + 1;
+                    j.top = h == s.L - 1;
+                    j.S = init ? 0 : lv.S;
+                    j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
+                    j.inv45 = 1.0f / (j.g4 + j.g5);
+                    j.inv5 = 1.0f / j.g5;
+                    for (int q = 0; q < 2; ++q) {
+                        j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q];
+                        j.s0_new[q] = lv.s0[q]; j.s1_new[q] = lv.s1[q];
+                    }
+                    j.p0 = lv.p0;
+                    j.p1 = lv.p1;
+                    j.image = s.image;
+                    j.range = s.range;
+                    j.H1 = s.H;
+                    j.W1 = s.W;
+                    j.lambda_ref = s.p.lambda_ref;
+                    j.tiles_x = ceil_div(lv.grid.W, kUpdTX);
+                    jobs.push_back(j);
+                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kUpdTX, kUpdTY);
+                    smem = std::max(smem, upd_smem(j.S));
+                }
+            }
+        }
+        Plan& pl = init ? b->init : b->upd;
+        pl.smem = smem;
+        int r = upload_plan(jobs, work, pl, st);
+        if (r) return r;
+    }
+    // ---- reconstruction cascade: depth d rebuilds level L_s - 2 - d of every stream
+    int maxL = 0;
+    for (auto& s : b->st) maxL = std::max(maxL, s.L);
+    const int depths = std::max(1, maxL - 1);
+    b->recon.resize(depths);
+    for (int d = 0; d < depths; ++d) {
+        std::vector<ReconJob> jobs;
+        std::vector<int2> work;
+        for (auto& s : b->st) {
+            const int h = s.L - 2 - d;
+            if (h < 0 && !(s.L == 1 && d == 0)) continue;
+            const int lvl = h >= 0 ? h : 0;
+            sf_level_state& lv = s.lv[lvl];
+            ReconJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.H = lv.grid.H;
+            j.W = lv.grid.W;
+            for (int q = 0; q < 2; ++q) {
+                j.s0[q] = lv.s0[q];
+                j.s1[q] = lv.s1[q];
+                if (h >= 0) j.s0c[q] = s.lv[h + 1].s0[q];
+            }
+            if (h >= 0) { j.Hc = s.lv[h + 1].grid.H; j.Wc = s.lv[h + 1].grid.W; }
+            if (lvl == 0) { j.flow_out = s.flow; j.invdepth_out = s.inv; }
+            jobs.push_back(j);
+            for (int p0 = 0; p0 < j.H * j.W; p0 += kReconChunk) work.push_back(make_int2((int)jobs.size() - 1, p0));
+        }
+        ReconPlan& rp = b->recon[d];
+        rp.nwork = (int)work.size();
+        if (cudaMalloc(&rp.jobs, jobs.size() * sizeof(ReconJob)) != cudaSuccess) return SF_ENOMEM;
+        if (cudaMalloc(&rp.work, work.size() * sizeof(int2)) != cudaSuccess) return SF_ENOMEM;
+        if (cudaMemcpyAsync(rp.jobs, jobs.data(), jobs.size() * sizeof(ReconJob), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(rp.work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SF_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return SF_ECUDA;
+    }
+    return SF_OK;
+}
+
+// the launches of one frame (no host synchronisation; capturable)
+int batch_launches(sf_batch* b, float dt, float wscale, cudaStream_t st)
+{
+    UpdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.parity = b->parity;
+    a.init = !b->initialised;
+    int r;
+    if (a.init) {
+        r = launch_update(b->init, a, st);
+    } else {
+        for (auto& pl : b->prop) {
+            r = launch_propagate(pl, b->parity, wscale, b->flags, b->status, st);
+            if (r) return r;
+        }
+        r = launch_update(b->upd, a, st);
+    }
+    if (r) return r;
+    for (auto& rp : b->recon) {
+        if (!rp.nwork) continue;
+        k_reconstruct_jobs<<<rp.nwork, kThreads, 0, st>>>(rp.jobs, rp.work, b->parity ^ 1, 1.0f / dt,
+                                                          (b->flags & SF_CHECK_FINITE) != 0, b->status);
+        r = last_error();
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params, sf_batch** out)
+{
+    if (out) *out = nullptr;
+    if (n < 1 || n > 4096 || !H || !W || !levels || !params || !out) return SF_EINVAL;
+    for (int s = 0; s < n; ++s) {
+        const sf_params* p = params + s;
+        const int L = levels[s];
+        if (L < 1 || L > SF_MAX_LEVELS || L > kMaxLevelsDev) return SF_EINVAL;
+        const int m = 1 << (L - 1);
+        if (H[s] <= 0 || W[s] <= 0 || H[s] % m || W[s] % m || H[s] / m < 8 || W[s] / m < 8) return SF_EINVAL;
+        if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->cx) || !std::isfinite(p->cy)) return SF_EINVAL;
+        if (!(p->lambda_ref > 0) || !(p->gamma[2] > 0) || !(p->gamma[4] > 0)) return SF_EINVAL;
+        for (int k = 0; k < 5; ++k)
+            if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
+        if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
+        for (int h = 0; h < L; ++h) {
+            const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
+            if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
+        }
+        if ((p->flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)) != (params[0].flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)))
+            return SF_EINVAL;   // one scheme variant per batch (one kernel instantiation)
+    }
+    sf_batch* b = new (std::nothrow) sf_batch();
+    if (!b) return SF_ENOMEM;
+    b->st.resize(n);
+    b->flags = params[0].flags;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete b; return SF_ECUDA; }
+    int r = SF_OK;
+    size_t io_floats = 0;
+    for (int s = 0; s < n; ++s) io_floats += 6 * (size_t)H[s] * W[s];   // image, range, flow (3), invdepth
+    if (cudaMalloc(&b->io, io_floats * sizeof(float)) != cudaSuccess) { b->io = nullptr; r = SF_ENOMEM; }
+    size_t off = 0;
+    for (int s = 0; s < n && !r; ++s) {
+        sf_batch_stream& bs = b->st[s];
+        bs.H = H[s]; bs.W = W[s]; bs.L = levels[s]; bs.p = params[s];
+        const size_t np = (size_t)H[s] * W[s];
+        float* base = (float*)b->io + off;
+        bs.image = base; bs.range = base + np; bs.flow = base + 2 * np; bs.inv = base + 5 * np;
+        off += 6 * np;
+        for (int h = 0; h < bs.L && !r; ++h) {
+            sf_level_state& lv = bs.lv[h];
+            const float sc = (float)(1 << h);
+            lv.grid.H = bs.H >> h; lv.grid.W = bs.W >> h;
+            lv.grid.fx = bs.p.fx / sc; lv.grid.fy = bs.p.fy / sc; lv.grid.cx = bs.p.cx / sc; lv.grid.cy = bs.p.cy / sc;
+            lv.N = bs.p.iters[h] > 0 ? bs.p.iters[h] : std::max(1, (int)std::ceil(bs.p.max_flow / sc));
+            lv.S = bs.p.smooth_iters[h];
+            for (int k = 0; k < 5; ++k) lv.gamma[k] = bs.p.gamma[k];
+            const double dmu_c = (double)sc / (double)bs.p.fx;   // reading R10
+            lv.gamma[2] = (float)(bs.p.gamma[2] * dmu_c * dmu_c);
+            const size_t nl = (size_t)lv.grid.H * lv.grid.W;
+            if (cudaMalloc(&lv.block, 8 * nl * sizeof(float4)) != cudaSuccess) { lv.block = nullptr; r = SF_ENOMEM; break; }
+            cudaMemsetAsync(lv.block, 0, 8 * nl * sizeof(float4), st);
+            float4* blk = (float4*)lv.block;
+            lv.s0[0] = blk; lv.s1[0] = blk + nl; lv.s0[1] = blk + 2 * nl; lv.s1[1] = blk + 3 * nl;
+            lv.p0 = blk + 4 * nl; lv.p1 = blk + 5 * nl; lv.t0 = blk + 6 * nl; lv.t1 = blk + 7 * nl;
+        }
+    }
+    if (!r && b->io) r = cudaMemsetAsync(b->io, 0, io_floats * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r && cudaMalloc(&b->status, sizeof(int)) != cudaSuccess) { b->status = nullptr; r = SF_ENOMEM; }
+    if (!r) r = cudaMemsetAsync(b->status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = batch_plans(b, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaStreamDestroy(st);
+    if (r) { destroy_batch(b); return r; }
+    *out = b;
+    return SF_OK;
+}
+
+int sf_batch_buffers(sf_batch* b, int s, float** image, float** range, float** flow, float** invdepth)
+{
+    if (!b || s < 0 || s >= (int)b->st.size()) return SF_EINVAL;
+    if (image) *image = b->st[s].image;
+    if (range) *range = b->st[s].range;
+    if (flow) *flow = b->st[s].flow;
+    if (invdepth) *invdepth = b->st[s].inv;
+    return SF_OK;
+}
+
+int sf_batch_step(sf_batch* b, float dt, void* stream)
+{
+    if (!b || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float wscale = b->initialised ? dt / b->dt_prev : 1.0f;   // reading R9
+    const int q = b->parity;
+    int r;
+    // steady state (same dt as the previous frame, initialised, a capturable
+    // stream, launch attributes already set by an earlier plain step): replay
+    // the frame's graph for this parity
+    const bool graphable = b->initialised && wscale == 1.0f && st != nullptr && b->steps_plain >= 2;
+    if (graphable) {
+        if (!b->graph[q] || b->graph_dt[q] != dt) {
+            if (b->graph[q]) { cudaGraphExecDestroy(b->graph[q]); b->graph[q] = nullptr; }
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SF_ECUDA;
+            r = batch_launches(b, dt, 1.0f, st);
+            const cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (r || e != cudaSuccess) { if (g) cudaGraphDestroy(g); return r ? r : SF_ECUDA; }
+            const cudaError_t ei = cudaGraphInstantiate(&b->graph[q], g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) { b->graph[q] = nullptr; return SF_ECUDA; }
+            b->graph_dt[q] = dt;
+        }
+        if (cudaGraphLaunch(b->graph[q], st) != cudaSuccess) return SF_ECUDA;
+    } else {
+        r = batch_launches(b, dt, wscale, st);
+        if (r) return r;
+        if (b->initialised) b->steps_plain++;
+    }
+    b->parity ^= 1;
+    b->initialised = 1;
+    b->dt_prev = dt;
+    return SF_OK;
+}
+
+int sf_batch_status(sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
+    int s = 0;
+    if (cudaMemcpy(&s, b->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
+    if (cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
+    if (s & kStatusNonFinite) return SF_ENONFINITE;
+    if (s & kStatusCfl) return SF_WARN_CFL;
+    return SF_OK;
+}
+
+int sf_batch_launches_per_step(const sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    int nrec = 0;
+    for (auto& rp : b->recon) nrec += rp.nwork ? 1 : 0;
+    return (int)b->prop.size() + 1 + nrec;
+}
+
+void sf_batch_destroy(sf_batch* b) { destroy_batch(b); }
+
+}  // extern "C"

@@ -334,6 +334,10 @@ struct UpdJob {
     int S;                 // smoothing passes
     float g1, g2, g3, g4, g5;
     float inv45, inv5;     // 1 / (g4 + g5) and 1 / g5 (Eq. 52 with and without a measurement)
+    const float* image;    // this job's level-1 input (batched streams); nullptr: the launch's
+    const float* range;
+    int H1, W1;
+    float lambda_ref;
     const float4* s0_cur[2];
     const float4* s1_cur[2];
     const float4* p0;
@@ -442,6 +446,13 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
     const UpdJob& J = jobs[wk.x];
     const Grid g = J.g;
     const int S = args.init ? 0 : J.S;
+    if (J.image) {   // batched streams carry their own inputs
+        args.image = J.image;
+        args.range = J.range;
+        args.H1 = J.H1;
+        args.W1 = J.W1;
+        args.lambda_ref = J.lambda_ref;
+    }
     const int SX = TX + 4 * S, SY = TY + 4 * S, DX = SX + 4, DY = SY + 4, RXd = SX + 2;
     size_t offF, offR, offY, total;
     upd_layout(TX, TY, S, &offF, &offR, &offY, &total);
@@ -696,6 +707,61 @@ __global__ void __launch_bounds__(kThreads) k_reconstruct(ReconArgs a)
     }
     if (a.check_finite && a.status) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
+    }
+}
+
+// Reconstruction and outputs of many (stream, level) jobs in one launch: a CTA
+// handles one chunk of one job's pixels.
+struct ReconJob {
+    int H, W, Hc, Wc;          // level and coarser level (Hc = 0: top level, outputs only)
+    float4* s0[2];             // new state, by the parity of the frame just written
+    const float4* s1[2];
+    const float4* s0c[2];
+    float* flow_out;           // level 1 only (may be null)
+    float* invdepth_out;
+};
+
+constexpr int kReconChunk = 4096;
+
+__global__ void __launch_bounds__(kThreads) k_reconstruct_jobs(const ReconJob* __restrict__ jobs,
+                                                              const int2* __restrict__ work, int q, float inv_dt,
+                                                              int check_finite, int* status)
+{
+    const int2 wk = work[blockIdx.x];
+    const ReconJob& J = jobs[wk.x];
+    ReconArgs a;
+    a.H = J.H; a.W = J.W; a.Hc = J.Hc; a.Wc = J.Wc;
+    a.s0 = J.s0[q]; a.s1 = J.s1[q]; a.s0c = J.Hc ? J.s0c[q] : nullptr;
+    a.flow_out = J.flow_out; a.invdepth_out = J.invdepth_out;
+    const int n = J.H * J.W, p0 = wk.y, p1 = min(n, wk.y + kReconChunk);
+    bool bad = false;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int i = p / a.W, j = p - (p / a.W) * a.W;
+        float4 s = a.s0[p];
+        if (a.s0c) {
+            const int i0 = (i - 1) >> 1, j0 = (j - 1) >> 1;
+            const float fy = (i & 1) ? 0.25f : 0.75f, fx = (j & 1) ? 0.25f : 0.75f;
+            const int ia = clampi(i0, 0, a.Hc - 1), ib = clampi(i0 + 1, 0, a.Hc - 1);
+            const int ja = clampi(j0, 0, a.Wc - 1), jb = clampi(j0 + 1, 0, a.Wc - 1);
+            const float4 c00 = a.s0c[ia * a.Wc + ja], c01 = a.s0c[ia * a.Wc + jb];
+            const float4 c10 = a.s0c[ib * a.Wc + ja], c11 = a.s0c[ib * a.Wc + jb];
+            const float4 d = a.s1[p];
+            const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
+            s.x = wy0 * (wx0 * c00.x + fx * c01.x) + fy * (wx0 * c10.x + fx * c11.x) + d.x;
+            s.y = wy0 * (wx0 * c00.y + fx * c01.y) + fy * (wx0 * c10.y + fx * c11.y) + d.y;
+            s.z = wy0 * (wx0 * c00.z + fx * c01.z) + fy * (wx0 * c10.z + fx * c11.z) + d.z;
+            a.s0[p] = s;
+        }
+        if (a.flow_out) {
+            a.flow_out[p] = s.x * inv_dt;
+            a.flow_out[n + p] = s.y * inv_dt;
+            a.flow_out[2 * n + p] = s.z * inv_dt;
+        }
+        if (a.invdepth_out) a.invdepth_out[p] = s.w;
+        if (check_finite && a.flow_out) bad |= !(isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.w));
+    }
+    if (check_finite && status) {
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
     }
 }
 

@@ -43,7 +43,8 @@ _lib = None
 
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
            "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
-           "sf_update", "sf_reconstruct"]
+           "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
+           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_destroy"]
 
 
 def lib():
@@ -71,6 +72,13 @@ def lib():
         L.sf_strerror.argtypes = [i]
         L.sf_strerror.restype = ctypes.c_char_p
         L.sf_propagate.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
+        L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
+        L.sf_batch_buffers.argtypes = [vp, i, P(vp), P(vp), P(vp), P(vp)]
+        L.sf_batch_step.argtypes = [vp, f, vp]
+        L.sf_batch_status.argtypes = [vp]
+        L.sf_batch_launches_per_step.argtypes = [vp]
+        L.sf_batch_destroy.argtypes = [vp]
+        L.sf_batch_destroy.restype = None
         L.sf_propagate_noalloc.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
         L.sf_update.argtypes = [P(CGrid), i, i, i, i, P(f), f, vp, vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sf_reconstruct.argtypes = [i, P(CGrid), P(vp), P(vp), f, vp, vp, i, vp, vp]
@@ -248,3 +256,56 @@ def reconstruct(grids, s0, s1, dt, flow_out=None, invdepth_out=None, check_finit
     p1 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s1])
     return _check(lib().sf_reconstruct(L, ga, p0, p1, float(dt), _ptr(flow_out), _ptr(invdepth_out),
                                        int(bool(check_finite)), _ptr(status), _stream(stream)), "sf_reconstruct")
+
+
+class Batch:
+    """Many independent filters (``sf_batch_*``); stream s has its own device
+    input/output slots, exposed as torch tensors viewing the batch's memory."""
+
+    def __init__(self, shapes, levels, params):
+        import torch
+        n = len(shapes)
+        Hs = (ctypes.c_int * n)(*[int(h) for h, _ in shapes])
+        Ws = (ctypes.c_int * n)(*[int(w) for _, w in shapes])
+        Ls = (ctypes.c_int * n)(*[int(x) for x in levels])
+        ps = (CParams * n)(*[p.to_c(h, w, l) for p, (h, w), l in zip(params, shapes, levels)])
+        h = ctypes.c_void_p()
+        _check(lib().sf_batch_create(n, Hs, Ws, Ls, ps, ctypes.byref(h)), "sf_batch_create")
+        self._h = h
+        self.shapes = list(shapes)
+        self.slots = []
+        for s, (H, W) in enumerate(shapes):
+            ptrs = [ctypes.c_void_p() for _ in range(4)]
+            _check(lib().sf_batch_buffers(h, s, *[ctypes.byref(x) for x in ptrs]), "sf_batch_buffers")
+            self.slots.append(tuple(_wrap(x.value, shp) for x, shp in
+                                    zip(ptrs, [(H, W), (H, W), (3, H, W), (H, W)])))
+
+    def step(self, dt, stream=None):
+        return _check(lib().sf_batch_step(self._h, float(dt), _stream(stream)), "sf_batch_step")
+
+    def status(self):
+        code = lib().sf_batch_status(self._h)
+        if code not in (OK, WARN_CFL, ENONFINITE):
+            raise SFError(code, "sf_batch_status")
+        return code
+
+    def launches_per_step(self):
+        return _check(lib().sf_batch_launches_per_step(self._h), "sf_batch_launches_per_step")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+
+def _wrap(ptr, shape):
+    """A float32 CUDA tensor viewing library-owned device memory (no copy)."""
+    import torch
+    n = int(np.prod(shape))
+
+    class _Iface:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Iface(), device="cuda")

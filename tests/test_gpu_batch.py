@@ -1,0 +1,72 @@
+"""Batched streams (sf_batch_*): every stream computes what its own sf_step
+computes, through the plain launches and the replayed CUDA graphs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_18031_b300 import scenes, sf
+from tests import gpu_util as gu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    oracle.set_threads(8)
+
+
+def _streams():
+    return [
+        scenes.plane64(frames=7, seed=11, H=64, W=64, levels=1, iters=[2]),
+        scenes.plane64(frames=7, seed=12, H=96, W=128, levels=2, iters=[3, 2], v=(2.0, -1.0, 3.0)),
+        scenes.scene512(frames=7, seed=13, H=128, W=128, max_flow=3.0, levels=3, iters=(3, 2, 1), smooth=(2, 4, 4)),
+        scenes.plane64(frames=7, seed=14, H=64, W=96, levels=2, iters=[10, 5], v=(6.0, 3.0, 1.0)),
+    ]
+
+
+def _params(seq):
+    return sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
+                     flags=sf.CHECK_CFL | sf.CHECK_FINITE)
+
+
+def test_batch_matches_single_stream_filters_and_oracle():
+    seqs = _streams()
+    dt = seqs[0].dt
+    assert all(abs(s.dt - dt) < 1e-15 for s in seqs)
+    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs], [_params(s) for s in seqs])
+    singles = [sf.Filter(*s.shape, s.levels, _params(s)) for s in seqs]
+    ref = oracle.Filter(*seqs[2].shape, seqs[2].levels,
+                        oracle.Params(seqs[2].fx, seqs[2].fy, seqs[2].cx, seqs[2].cy, iters=seqs[2].iters,
+                                      smooth=seqs[2].smooth))
+    _, _, dmu_ref = ref.geometry(0)
+    stream = torch.cuda.Stream()
+    outs = [(torch.empty((3, *s.shape), device="cuda"), torch.empty(s.shape, device="cuda")) for s in seqs]
+    for k in range(7):
+        with torch.cuda.stream(stream):
+            for s, seq in enumerate(seqs):
+                img, rng, _, _ = batch.slots[s]
+                img.copy_(torch.from_numpy(seq.image[k]).cuda())
+                rng.copy_(torch.from_numpy(seq.range[k]).cuda())
+            batch.step(dt, stream=stream)
+            for s, seq in enumerate(seqs):
+                singles[s].step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(),
+                                dt, outs[s][0], outs[s][1], stream=stream)
+        stream.synchronize()
+        for s, seq in enumerate(seqs):
+            _, _, dmu = oracle.geometry(*seq.shape, seq.fx, seq.fy, seq.cx, seq.cy)
+            bf, bi = batch.slots[s][2].cpu().numpy(), batch.slots[s][3].cpu().numpy()
+            sf_, si = outs[s][0].cpu().numpy(), outs[s][1].cpu().numpy()
+            e = np.abs(bf.astype(np.float64) - sf_) * dt / dmu[None]
+            assert e.max() <= gu.FLOW_TOL_PX, (k, s, e.max())
+            assert np.abs(bi - si).max() <= gu.RHO_TOL
+        rf, ri = ref.step(seqs[2].image[k], seqs[2].range[k], dt)
+        e = np.abs(batch.slots[2][2].cpu().numpy().astype(np.float64) - rf) * dt / dmu_ref[None]
+        assert e.max() <= gu.FLOW_TOL_PX
+    # N = 10 on stream 3 needs two propagation launches; three levels need a
+    # two-step reconstruction cascade; one update launch
+    assert batch.launches_per_step() == 2 + 1 + 2
+    assert batch.status() in (sf.OK, sf.WARN_CFL)
