@@ -182,6 +182,11 @@ int sf_batch_status(sf_batch* b);
 /* Kernel launches of one steady-state sf_batch_step. */
 int sf_batch_launches_per_step(const sf_batch* b);
 
+/* As sf_profile / sf_profile_read for a batch; while profiling, steps run as
+ * plain launches (no graph replay) so each launch can be timed. */
+int sf_batch_profile(sf_batch* b, int enable);
+int sf_batch_profile_read(sf_batch* b, float* ms, int* count, int n);
+
 void sf_batch_destroy(sf_batch* b);
 
 /* ------------------------------------------------------------------------

@@ -149,6 +149,56 @@ size_t upd_smem(int S)
 // context
 // ----------------------------------------------------------------------------
 
+// per-launch CUDA-event timing (sf_profile / sf_batch_profile)
+struct Profiler {
+    int enabled = 0;
+    std::vector<cudaEvent_t> pool;   // pairs, reused after a read
+    std::vector<int> slot;           // launch slot of each recorded pair
+    size_t used = 0;
+    ~Profiler()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+    int read(float* ms, int* count, int n)
+    {
+        for (int k = 0; k < n; ++k) { ms[k] = 0.0f; count[k] = 0; }
+        for (size_t p = 0; p < used; ++p) {
+            if (cudaEventSynchronize(pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, pool[2 * p], pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
+            if (slot[p] < n) { ms[slot[p]] += t; count[slot[p]] += 1; }
+        }
+        used = 0;
+        return SF_OK;
+    }
+};
+
+// event pair around one launch of slot `slot` (no-op unless profiling)
+struct ProfScope {
+    Profiler& pr;
+    cudaStream_t st;
+    size_t pair;
+    ProfScope(Profiler& p, int slot_, cudaStream_t st_) : pr(p), st(st_), pair((size_t)-1)
+    {
+        if (!pr.enabled) return;
+        if (2 * pr.used + 2 > pr.pool.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            pr.pool.push_back(a);
+            pr.pool.push_back(b);
+        }
+        pair = pr.used++;
+        if (pr.slot.size() < pr.used) pr.slot.resize(pr.used);
+        pr.slot[pair] = slot_;
+        cudaEventRecord(pr.pool[2 * pair], st);
+    }
+    ~ProfScope()
+    {
+        if (pair != (size_t)-1) cudaEventRecord(pr.pool[2 * pair + 1], st);
+    }
+};
+
 struct sf_level_state {
     sf_grid grid;
     int N, S;
@@ -173,11 +223,7 @@ struct sf_ctx {
     std::vector<Plan> prop;      // one per propagation launch of a frame
     Plan upd;
     Plan init;
-    // per-launch profiling (sf_profile)
-    int profiling = 0;
-    std::vector<cudaEvent_t> ev_pool;   // pairs, reused after sf_profile_read
-    std::vector<int> ev_slot;           // slot of each recorded pair
-    size_t ev_used = 0;
+    Profiler prof;                      // per-launch timing (sf_profile)
     // staging for sf_step_host
     float* stage_image = nullptr;
     float* stage_range = nullptr;
@@ -190,7 +236,6 @@ namespace {
 void destroy_ctx(sf_ctx* c)
 {
     if (!c) return;
-    for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto& pl : c->prop) free_plan(pl);
     free_plan(c->upd);
     free_plan(c->init);
@@ -300,32 +345,6 @@ int build_plans(sf_ctx* c, cudaStream_t st)
     return SF_OK;
 }
 
-// event pair around launch slot `slot` (no-op unless profiling)
-struct ProfScope {
-    sf_ctx* c;
-    cudaStream_t st;
-    size_t pair;
-    ProfScope(sf_ctx* c_, int slot, cudaStream_t st_) : c(c_), st(st_), pair((size_t)-1)
-    {
-        if (!c->profiling) return;
-        if (2 * c->ev_used + 2 > c->ev_pool.size()) {
-            cudaEvent_t a, b;
-            if (cudaEventCreate(&a) != cudaSuccess) return;
-            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
-            c->ev_pool.push_back(a);
-            c->ev_pool.push_back(b);
-        }
-        pair = c->ev_used++;
-        if (c->ev_slot.size() < c->ev_used) c->ev_slot.resize(c->ev_used);
-        c->ev_slot[pair] = slot;
-        cudaEventRecord(c->ev_pool[2 * pair], st);
-    }
-    ~ProfScope()
-    {
-        if (pair != (size_t)-1) cudaEventRecord(c->ev_pool[2 * pair + 1], st);
-    }
-};
-
 // reconstruction cascade and outputs of a frame whose new state has parity q
 int run_reconstruct(sf_ctx* c, int q, float dt, float* flow_out, float* inv_out, cudaStream_t st)
 {
@@ -354,7 +373,7 @@ int run_reconstruct(sf_ctx* c, int q, float dt, float* flow_out, float* inv_out,
             a.check_finite = (c->p.flags & SF_CHECK_FINITE) != 0;
             a.status = c->status;
         }
-        ProfScope ps(c, slot++, st);
+        ProfScope ps(c->prof, slot++, st);
         int r = launch_reconstruct(a, st);
         if (r) return r;
     }
@@ -467,11 +486,11 @@ int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* 
         a.init = 0;
         const float wscale = dt / c->dt_prev;   // reading R9
         for (size_t k = 0; k < c->prop.size(); ++k) {
-            ProfScope ps(c, (int)k, st);
+            ProfScope ps(c->prof, (int)k, st);
             r = launch_propagate(c->prop[k], c->parity, wscale, c->p.flags, c->status, st);
             if (r) return r;
         }
-        ProfScope ps(c, (int)c->prop.size(), st);
+        ProfScope ps(c->prof, (int)c->prop.size(), st);
         r = launch_update(c->upd, a, st);
     }
     if (r) return r;
@@ -547,24 +566,16 @@ int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* st
 int sf_profile(sf_ctx* c, int enable)
 {
     if (!c) return SF_EINVAL;
-    c->profiling = enable != 0;
+    c->prof.enabled = enable != 0;
     return SF_OK;
 }
 
 int sf_profile_read(sf_ctx* c, float* ms, int* count, int n)
 {
     if (!c || (n > 0 && (!ms || !count))) return SF_EINVAL;
-    const int slots = (int)c->prop.size() + 1 + std::max(1, c->L - 1);
-    for (int k = 0; k < n; ++k) { ms[k] = 0.0f; count[k] = 0; }
-    for (size_t p = 0; p < c->ev_used; ++p) {
-        if (cudaEventSynchronize(c->ev_pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
-        float t = 0.0f;
-        if (cudaEventElapsedTime(&t, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]) != cudaSuccess) return SF_ECUDA;
-        const int s = c->ev_slot[p];
-        if (s < n) { ms[s] += t; count[s] += 1; }
-    }
-    c->ev_used = 0;
-    return slots;
+    const int r = c->prof.read(ms, count, n);
+    if (r) return r;
+    return (int)c->prop.size() + 1 + std::max(1, c->L - 1);
 }
 
 int sf_kernels_per_step(const sf_ctx* c)
@@ -892,6 +903,7 @@ struct sf_batch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     float graph_dt[2] = {0.0f, 0.0f};
     int steps_plain = 0;
+    Profiler prof;                  // per-launch timing (sf_batch_profile); disables graph replay
 };
 
 namespace {
@@ -1058,18 +1070,23 @@ int batch_launches(sf_batch* b, float dt, float wscale, cudaStream_t st)
     a.parity = b->parity;
     a.init = !b->initialised;
     int r;
+    int slot = 0;
     if (a.init) {
         r = launch_update(b->init, a, st);
+        slot = (int)b->prop.size() + 1;
     } else {
         for (auto& pl : b->prop) {
+            ProfScope ps(b->prof, slot++, st);
             r = launch_propagate(pl, b->parity, wscale, b->flags, b->status, st);
             if (r) return r;
         }
+        ProfScope ps(b->prof, slot++, st);
         r = launch_update(b->upd, a, st);
     }
     if (r) return r;
     for (auto& rp : b->recon) {
         if (!rp.nwork) continue;
+        ProfScope ps(b->prof, slot++, st);
         k_reconstruct_jobs<<<rp.nwork, kThreads, 0, st>>>(rp.jobs, rp.work, b->parity ^ 1, 1.0f / dt,
                                                           (b->flags & SF_CHECK_FINITE) != 0, b->status);
         r = last_error();
@@ -1171,7 +1188,8 @@ int sf_batch_step(sf_batch* b, float dt, void* stream)
     // steady state (same dt as the previous frame, initialised, a capturable
     // stream, launch attributes already set by an earlier plain step): replay
     // the frame's graph for this parity
-    const bool graphable = b->initialised && wscale == 1.0f && st != nullptr && b->steps_plain >= 2;
+    const bool graphable = b->initialised && wscale == 1.0f && st != nullptr && b->steps_plain >= 2 &&
+                           !b->prof.enabled;
     if (graphable) {
         if (!b->graph[q] || b->graph_dt[q] != dt) {
             if (b->graph[q]) { cudaGraphExecDestroy(b->graph[q]); b->graph[q] = nullptr; }
@@ -1215,6 +1233,21 @@ int sf_batch_launches_per_step(const sf_batch* b)
     int nrec = 0;
     for (auto& rp : b->recon) nrec += rp.nwork ? 1 : 0;
     return (int)b->prop.size() + 1 + nrec;
+}
+
+int sf_batch_profile(sf_batch* b, int enable)
+{
+    if (!b) return SF_EINVAL;
+    b->prof.enabled = enable != 0;
+    return SF_OK;
+}
+
+int sf_batch_profile_read(sf_batch* b, float* ms, int* count, int n)
+{
+    if (!b || (n > 0 && (!ms || !count))) return SF_EINVAL;
+    const int r = b->prof.read(ms, count, n);
+    if (r) return r;
+    return sf_batch_launches_per_step(b);
 }
 
 void sf_batch_destroy(sf_batch* b) { destroy_batch(b); }

@@ -364,28 +364,67 @@ def drive(frames=500, seed=1002, H=384, W=1248, rate=100.0, levels=3, iters=(32,
                     levels, list(iters), list(smooth), v, om, meta=dict(speed=speed))
 
 
-def batch(frames=4, seed=1003, sizes=((256, 16), (512, 32), (1024, 16)), max_flow=4.0):
-    """Independent plane64-style streams of mixed sizes (list of Sequences).
+class _Waves2D:
+    """Cheap plane texture: a few random 2-D sinusoids, range [0, 1]."""
 
-    Each stream gets its own plane depth and camera velocity, chosen so the
-    flow at level 1 reaches about ``max_flow`` px/frame.  256x256 streams use
-    two pyramid levels, larger ones three.
+    def __init__(self, rng, n, k_range):
+        d = rng.normal(size=(n, 2))
+        self.k = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(*k_range, size=(n, 1))
+        self.ph = rng.uniform(0, 2 * np.pi, size=n)
+        self.a = rng.uniform(0.3, 1.0, size=n)
+        self.a /= self.a.sum()
+
+    def __call__(self, st):
+        out = np.zeros(st.shape[:-1], np.float32)
+        for k, ph, a in zip(self.k, self.ph, self.a):
+            out += np.float32(a) * np.sin((st @ k + ph).astype(np.float32))
+        return np.clip(0.5 + 0.4 * out, 0.0, 1.0)
+
+
+def plane_stream(frames, seed, H, W, depth, v, rate, levels, iters, smooth):
+    """A fronto-parallel textured plane under camera translation (config-1
+    style) with a sinusoidal texture that renders fast at any size."""
+    rng = np.random.default_rng(seed)
+    f = W / 2.0
+    dt = 1.0 / rate
+    px_m = depth / f
+    tex = _Waves2D(rng, 8, (2 * np.pi / (40 * px_m), 2 * np.pi / (6 * px_m)))
+    eta = camera_rays(H, W, f, f, W / 2.0, H / 2.0)
+    vv = np.asarray(v, dtype=np.float64)
+    imgs, rngs = [], []
+    for k in range(frames):
+        c = vv * (k * dt)
+        lam = (depth - c[2]) / eta[..., 2]
+        X = c[None, None, :2] + lam[..., None] * eta[..., :2]
+        imgs.append(tex(X)); rngs.append(lam)
+    return Sequence("plane_stream", np.array(imgs, np.float32), np.array(rngs, np.float32), dt, f, f, W / 2.0,
+                    H / 2.0, levels, list(iters), list(smooth), np.tile(vv, (frames, 1)), np.zeros((frames, 3)),
+                    meta=dict(depth=depth))
+
+
+def batch(frames=2, seed=1003, sizes=((256, 16), (512, 32), (1024, 16)), max_flow=4.0, rate=600.0):
+    """Independent config-1-style streams of mixed sizes (list of Sequences).
+
+    Each stream is a textured plane with its own depth and camera velocity,
+    chosen so the flow at level 1 reaches about ``max_flow`` px/frame; 256x256
+    streams use two pyramid levels, larger ones three, with
+    N_h = ceil(max_flow / 2^(h-1)) and smoothing [2, 4, 4].
     """
     rng = np.random.default_rng(seed)
     out = []
     for size, count in sizes:
         levels = 2 if size <= 256 else 3
+        iters = [int(np.ceil(max_flow / 2 ** h)) for h in range(levels)]
+        smooth = [2] + [4] * (levels - 1)
         for _ in range(count):
             depth = rng.uniform(3.0, 8.0)
-            direction = rng.normal(size=3); direction[2] = abs(direction[2])
+            direction = rng.normal(size=3)
+            direction[2] = abs(direction[2])
             direction /= np.linalg.norm(direction)
-            rate = 600.0
-            # lateral image flow ~ f * |v_xy| / depth / rate px per frame
-            vmag = max_flow * depth * rate / (size / 2.0) / max(np.linalg.norm(direction[:2]), 0.3)
-            iters = [int(np.ceil(max_flow / 2 ** h)) for h in range(levels)]
-            out.append(plane64(frames=frames, seed=int(rng.integers(1 << 30)), H=size, W=size, depth=depth,
-                               v=tuple(direction * vmag), rate=rate, n_blobs=max(200, size * size // 200),
-                               iters=iters, levels=levels))
+            # lateral image flow ~ f |v_xy| / depth / rate (px/frame), f = size / 2
+            vmag = 0.8 * max_flow * depth * rate / (size / 2.0) / max(np.linalg.norm(direction[:2]), 0.3)
+            out.append(plane_stream(frames, int(rng.integers(1 << 30)), size, size, depth, direction * vmag, rate,
+                                    levels, iters, smooth))
     return out
 
 

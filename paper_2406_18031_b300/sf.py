@@ -44,7 +44,8 @@ _lib = None
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
            "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
-           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_destroy"]
+           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_profile", "sf_batch_profile_read",
+           "sf_batch_destroy"]
 
 
 def lib():
@@ -77,6 +78,8 @@ def lib():
         L.sf_batch_step.argtypes = [vp, f, vp]
         L.sf_batch_status.argtypes = [vp]
         L.sf_batch_launches_per_step.argtypes = [vp]
+        L.sf_batch_profile.argtypes = [vp, i]
+        L.sf_batch_profile_read.argtypes = [vp, P(f), P(i), i]
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_destroy.restype = None
         L.sf_propagate_noalloc.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
@@ -291,6 +294,15 @@ class Batch:
 
     def launches_per_step(self):
         return _check(lib().sf_batch_launches_per_step(self._h), "sf_batch_launches_per_step")
+
+    def profile(self, enable: bool):
+        _check(lib().sf_batch_profile(self._h, int(bool(enable))), "sf_batch_profile")
+
+    def profile_read(self):
+        n = 16
+        ms = (ctypes.c_float * n)(); cnt = (ctypes.c_int * n)()
+        slots = _check(lib().sf_batch_profile_read(self._h, ms, cnt, n), "sf_batch_profile_read")
+        return [(ms[k], cnt[k]) for k in range(min(slots, n))]
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
