@@ -41,6 +41,47 @@ def dist_env():
     return ws, rank, local
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu
+# captures of these very workloads (profiles/traffic_k_propagate.md), valid
+# only for the kernel sources they were taken with.
+TRAFFIC = {
+    "kernel_sources_sha256_16": "7e7fc510c02cb9e6",
+    "scene512_k_propagate_bytes": 9_479_936 + 1_024,
+    "batch_k_propagate_bytes": 1_069_888_000 + 1_017_789_696,
+}
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sf_kernels.cuh", "sf_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_18031_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key):
+    return TRAFFIC[key] if kernel_sources_hash() == TRAFFIC["kernel_sources_sha256_16"] else None
+
+
+def job_time_ms(local_ms, ws, device):
+    """Max over ranks of the ranks' timed milliseconds (the job ends when its
+    slowest rank does); a plain float with one rank."""
+    if ws <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, max_ms):
+    """Units processed by all ranks per second (weak scaling: every rank runs
+    its own stream of the same workload)."""
+    return ws * units_per_rank / (max_ms / 1e3)
+
+
 def algorithmic_bytes_per_frame(H, W, levels):
     """Bytes a perfectly fused frame must move: the level-1 inputs (image +
     range, 8 B/px), the state of every level read once and written once
@@ -51,6 +92,24 @@ def algorithmic_bytes_per_frame(H, W, levels):
         n = (H >> h) * (W >> h)
         per = 20 if h == levels - 1 else 32
         total += 2 * per * n
+    return total
+
+
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def propagate_flops_per_launch(H, W, levels, iters, nf_max=8):
+    """Algorithmic FP32 operations of the first propagation launch: per pixel
+    and sub-iteration 94 below the top level (8 channels) and 58 at the top
+    (4 channels): per pass <eta,w> 5, speed 3, dt*s 1, 5 per channel with a
+    source term, 3 for Y."""
+    total = 0
+    for h in range(levels):
+        n = (H >> h) * (W >> h)
+        N = iters[h]
+        nseg = -(-N // nf_max)
+        nf = N // nseg + (1 if N % nseg else 0)
+        total += n * nf * (58 if h == levels - 1 else 94)
     return total
 
 
@@ -265,11 +324,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = job_time_ms(sum(step_ms), ws, dev)
     # second timed pass, same steps, with the library's per-launch events on the
     # launching stream: per-kernel durations and shares
     filt.profile(True)
@@ -282,7 +337,7 @@ def run_ours(args):
     status = filt.status()
 
     if rank == 0:
-        value = ws * args.steps / (total_ms / 1e3)
+        value = whole_job_rate(args.steps, ws, total_ms)
         peaks, peak_kind = measured_peaks()
         kstep = filt.kernels_per_step()
         # dominant kernel: the first propagation launch of each frame (all levels)
@@ -293,6 +348,7 @@ def run_ours(args):
                   for n, (ms, c) in zip(names, slots)}
         prop_ms = slots[0][0] / max(slots[0][1], 1)
         bpl = propagate_bytes_per_launch(H, W, seq.levels)
+        prop_flops = propagate_flops_per_launch(H, W, seq.levels, seq.iters)
         achieved = bpl / (prop_ms / 1e3) / 1e9
         frame_bytes = algorithmic_bytes_per_frame(H, W, seq.levels)
         if args.quick:
@@ -318,7 +374,12 @@ def run_ours(args):
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
             "roofline": {"kernel": "k_propagate (first launch of the frame, all levels)", "bound": "hbm",
                          "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": measured_traffic("scene512_k_propagate_bytes") if args.size == 512 else None,
+                         "traffic_note": "ncu dram read+write of one launch at this workload; the 9.4 MB "
+                                         "prediction write stays in L2 (state smaller than L2)",
+                         "fp32_tflops": prop_flops / (prop_ms / 1e3) / 1e12,
+                         "fp32_frac_of_peak": prop_flops / (prop_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                          "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": prop_ms,
                          "algorithmic_bytes_per_launch": bpl},
             "kernels": shares,
@@ -404,7 +465,8 @@ def measure_batch(steps, warmup, dev):
                     for n, (ms, c) in zip(names, slots)},
         "roofline": {"kernel": "k_propagate (first launch, all streams and levels)", "bound": "hbm",
                      "achieved": prop_bytes / (prop_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": prop_bytes / (prop_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                     "frac": prop_bytes / (prop_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "traffic": measured_traffic("batch_k_propagate_bytes"),
                      "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": prop_ms,
                      "algorithmic_bytes_per_launch": prop_bytes},
         "graph": "steady-state steps replay a captured CUDA graph (the profiled pass runs plain launches)",
