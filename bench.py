@@ -341,8 +341,8 @@ def run_ours(args):
         peaks, peak_kind = measured_peaks()
         kstep = filt.kernels_per_step()
         # dominant kernel: the first propagation launch of each frame (all levels)
-        names = [f"k_propagate#{k}" for k in range(len(slots) - 1 - max(1, seq.levels - 1))] + ["k_update"] + \
-                [f"k_reconstruct#{k}" for k in range(max(1, seq.levels - 1))]
+        names = [f"k_propagate#{k}" for k in range(len(slots) - 1 - seq.levels)] + ["k_solve"] + \
+                [f"k_smooth_recon#level{seq.levels - k}" for k in range(seq.levels)]
         tot = sum(ms for ms, _ in slots) or 1.0
         shares = {n: {"ms_per_launch": ms / max(c, 1), "launches": c, "share": ms / tot}
                   for n, (ms, c) in zip(names, slots)}
@@ -445,9 +445,10 @@ def measure_batch(steps, warmup, dev):
     step_s = total_ms / steps / 1e3
     px = sum(q.shape[0] * q.shape[1] for q in seqs)
     frame_bytes = sum(algorithmic_bytes_per_frame(q.shape[0], q.shape[1], q.levels) for q in seqs)
-    nprop = len(slots) - 1 - max(1, max(q.levels for q in seqs) - 1)
-    names = [f"k_propagate#{k}" for k in range(nprop)] + ["k_update"] + \
-            [f"k_reconstruct_jobs#{k}" for k in range(len(slots) - 1 - nprop)]
+    maxL = max(q.levels for q in seqs)
+    nprop = len(slots) - 1 - maxL
+    names = [f"k_propagate#{k}" for k in range(nprop)] + ["k_solve"] + \
+            [f"k_smooth_recon#depth{k}" for k in range(maxL)]
     tot = sum(ms for ms, _ in slots) or 1.0
     prop_bytes = sum(propagate_bytes_per_launch(q.shape[0], q.shape[1], q.levels) for q in seqs)
     prop_ms = slots[0][0] / max(slots[0][1], 1)

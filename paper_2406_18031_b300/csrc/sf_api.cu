@@ -1,7 +1,15 @@
-// sf_api.cu -- host side of libsf: contexts, launch plans and the C ABI of
-// include/sf.h.  All device work is issued on the caller's stream; nothing
-// here synchronises except sf_status, sf_step_host and the checkpoint calls'
-// own documented waits.
+// sf_api.cu -- host side of libsf: filter engines, launch plans and the C ABI
+// of include/sf.h.  All device work is issued on the caller's stream; nothing
+// here synchronises except sf_status / sf_batch_status, sf_step_host and the
+// stage entry points' descriptor uploads.
+//
+// An engine is a set of independent camera streams, each with its pyramid
+// levels.  Its frame is a fixed sequence of launches whose descriptors are
+// built once: the propagation launches (every level of every stream), one
+// solve launch (every level), then the smoothing + reconstruction cascade
+// (one launch per pyramid depth, top levels first).  sf_ctx is an engine of
+// one stream fed through per-frame pointers; sf_batch is an engine of many
+// streams with library-owned input/output slots, replayed from CUDA graphs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,9 +28,8 @@ using namespace sfdev;
 namespace {
 
 // the largest number of sub-iterations fused in one propagation launch (its
-// square output tile is 64 - 2 nf pixels wide) and the update tile
+// square output tile is 64 - 2 nf pixels wide)
 constexpr int kNfMax = 8;
-constexpr int kUpdTX = 32, kUpdTY = 32;
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
@@ -57,26 +64,24 @@ int set_smem_attr(const void* fn, size_t bytes)
     return SF_OK;
 }
 
-int last_error()
-{
-    return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA;
-}
+int last_error() { return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA; }
 
-// A launch of k_propagate or k_update: device copies of its jobs and work list.
+// A launch: device copies of its jobs and of its work list (one item per CTA).
 struct Plan {
-    void* jobs = nullptr;     // device PropJob[] or UpdJob[]
-    int4* work = nullptr;     // device work items (job, tile row, tile col, 0)
+    void* jobs = nullptr;
+    int4* work = nullptr;
     int nwork = 0;
     size_t smem = 0;
-    bool c8 = false;          // propagate: any 8-channel job (all jobs share one instantiation)
+    bool c8 = false;     // propagation: some job transports 8 channels
 };
 
 template <class Job>
 int upload_plan(const std::vector<Job>& jobs, const std::vector<int4>& work, Plan& p, cudaStream_t st)
 {
     p.nwork = (int)work.size();
-    if (cudaMalloc(&p.jobs, jobs.size() * sizeof(Job)) != cudaSuccess) return SF_ENOMEM;
-    if (cudaMalloc(&p.work, work.size() * sizeof(int4)) != cudaSuccess) return SF_ENOMEM;
+    if (jobs.empty()) return SF_OK;
+    if (cudaMalloc(&p.jobs, jobs.size() * sizeof(Job)) != cudaSuccess) { p.jobs = nullptr; return SF_ENOMEM; }
+    if (cudaMalloc(&p.work, work.size() * sizeof(int4)) != cudaSuccess) { p.work = nullptr; return SF_ENOMEM; }
     if (cudaMemcpyAsync(p.jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SF_ECUDA;
     if (cudaMemcpyAsync(p.work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -97,6 +102,10 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
         for (int tx = 0; tx < W; tx += TX) work.push_back(make_int4(job, ty, tx, 0));
 }
 
+// offset of the work list behind a job in one stage-call upload: int4 loads
+// need 16-byte alignment whatever the size of the job struct
+inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
+
 template <bool C8, bool LIT>
 int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
 {
@@ -116,11 +125,20 @@ int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* st
                : launch_propagate_t<false, false>(p, parity, wscale, flags, status, st);
 }
 
-int launch_update(const Plan& p, const UpdArgs& a, cudaStream_t st)
+int launch_solve(const Plan& p, const UpdArgs& a, cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
-    if (set_smem_attr((const void*)k_update, p.smem)) return SF_ECUDA;
-    k_update<<<p.nwork, kUpdThreads, p.smem, st>>>((const UpdJob*)p.jobs, p.work, a, kUpdTX, kUpdTY);
+    k_solve<<<p.nwork, kSolveThreads, 0, st>>>((const SolveJob*)p.jobs, p.work, a);
+    return last_error();
+}
+
+int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* status, float* flow, float* inv,
+                  cudaStream_t st)
+{
+    if (p.nwork == 0) return SF_OK;
+    if (set_smem_attr((const void*)k_smooth_recon, p.smem)) return SF_ECUDA;
+    k_smooth_recon<<<p.nwork, kSmoothThreads, p.smem, st>>>((const SmoothJob*)p.jobs, p.work, q, inv_dt, check_finite,
+                                                             status, flow, inv);
     return last_error();
 }
 
@@ -132,24 +150,35 @@ int launch_reconstruct(const ReconArgs& a, cudaStream_t st)
     return last_error();
 }
 
-// offset of the work list behind a job in one stage-call upload: int4 loads
-// need 16-byte alignment whatever the size of the job struct
-inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-size_t upd_smem(int S)
+// parameter checks shared by sf_create and sf_batch_create (no device calls)
+int check_params(int H, int W, int L, const sf_params* p)
 {
-    size_t a, b, c, total;
-    upd_layout(kUpdTX, kUpdTY, S, &a, &b, &c, &total);
-    return total;
+    if (!p || L < 1 || L > SF_MAX_LEVELS || L > kMaxLevelsDev) return SF_EINVAL;
+    const int m = 1 << (L - 1);
+    if (H <= 0 || W <= 0 || H % m || W % m || H / m < 8 || W / m < 8) return SF_EINVAL;
+    if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->cx) ||
+        !std::isfinite(p->cy))
+        return SF_EINVAL;
+    if (!(p->lambda_ref > 0) || !std::isfinite(p->lambda_ref) || !(p->gamma[2] > 0) || !(p->gamma[4] > 0))
+        return SF_EINVAL;
+    for (int k = 0; k < 5; ++k)
+        if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
+    if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
+    for (int h = 0; h < L; ++h) {
+        const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
+        if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
+    }
+    return SF_OK;
 }
 
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// context
+// per-launch timing
 // ----------------------------------------------------------------------------
 
-// per-launch CUDA-event timing (sf_profile / sf_batch_profile)
 struct Profiler {
     int enabled = 0;
     std::vector<cudaEvent_t> pool;   // pairs, reused after a read
@@ -199,31 +228,299 @@ struct ProfScope {
     }
 };
 
+// ----------------------------------------------------------------------------
+// engines
+// ----------------------------------------------------------------------------
+
 struct sf_level_state {
     sf_grid grid;
     int N, S;
-    float gamma[5];       // gamma[2] scaled for this level
+    float gamma[5];       // gamma[2] scaled for this level (reading R10)
     float4* s0[2];        // state, double buffered by frame parity
     float4* s1[2];
     float4* p0;           // prediction k+
     float4* p1;
-    float4* t0;           // intermediate fields between propagation launches
-    float4* t1;
-    void* block;          // single allocation holding the eight planes
+    float4* t0;           // between propagation launches; then the solution
+    float4* t1;           // between propagation launches; then Y-hat (as floats)
+    void* block;          // one allocation holding the eight planes
 };
 
-struct sf_ctx {
+struct EngineStream {
     int H, W, L;
     sf_params p;
-    int parity;
-    int initialised;
-    float dt_prev;
-    int* status;                 // device status word
     sf_level_state lv[SF_MAX_LEVELS];
-    std::vector<Plan> prop;      // one per propagation launch of a frame
-    Plan upd;
-    Plan init;
-    Profiler prof;                      // per-launch timing (sf_profile)
+    float* image;         // input/output slots (batches); null: the frame's pointers
+    float* range;
+    float* flow;
+    float* inv;
+};
+
+struct Engine {
+    std::vector<EngineStream> st;
+    int flags = 0;
+    int parity = 0;
+    int initialised = 0;
+    float dt_prev = 0.0f;
+    int* status = nullptr;
+    std::vector<Plan> prop;     // propagation launches
+    Plan solve;                 // every level of every stream
+    std::vector<Plan> smooth;   // cascade: depth d handles level L - 1 - d of every stream
+    void* io = nullptr;         // slots of a batch
+    Profiler prof;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    float graph_dt[2] = {0.0f, 0.0f};
+    int steps_plain = 0;
+
+    int launches_per_step() const
+    {
+        int n = (int)prop.size() + 1;
+        for (auto& p : smooth) n += p.nwork ? 1 : 0;
+        return n;
+    }
+};
+
+namespace {
+
+void engine_free(Engine& E)
+{
+    for (int q = 0; q < 2; ++q)
+        if (E.graph[q]) cudaGraphExecDestroy(E.graph[q]);
+    for (auto& pl : E.prop) free_plan(pl);
+    free_plan(E.solve);
+    for (auto& pl : E.smooth) free_plan(pl);
+    for (auto& s : E.st)
+        for (int h = 0; h < s.L; ++h) cudaFree(s.lv[h].block);
+    cudaFree(E.io);
+    cudaFree(E.status);
+}
+
+int engine_levels(EngineStream& s, cudaStream_t st)
+{
+    for (int h = 0; h < s.L; ++h) {
+        sf_level_state& lv = s.lv[h];
+        const float sc = (float)(1 << h);
+        lv.grid.H = s.H >> h;
+        lv.grid.W = s.W >> h;
+        lv.grid.fx = s.p.fx / sc; lv.grid.fy = s.p.fy / sc; lv.grid.cx = s.p.cx / sc; lv.grid.cy = s.p.cy / sc;
+        lv.N = s.p.iters[h] > 0 ? s.p.iters[h] : std::max(1, (int)std::ceil(s.p.max_flow / sc));
+        lv.S = s.p.smooth_iters[h];
+        for (int k = 0; k < 5; ++k) lv.gamma[k] = s.p.gamma[k];
+        const double dmu_c = (double)sc / (double)s.p.fx;   // reading R10
+        lv.gamma[2] = (float)(s.p.gamma[2] * dmu_c * dmu_c);
+        const size_t n = (size_t)lv.grid.H * lv.grid.W;
+        lv.block = nullptr;
+        if (cudaMalloc(&lv.block, 8 * n * sizeof(float4)) != cudaSuccess) { lv.block = nullptr; return SF_ENOMEM; }
+        if (cudaMemsetAsync(lv.block, 0, 8 * n * sizeof(float4), st) != cudaSuccess) return SF_ECUDA;
+        float4* b = (float4*)lv.block;
+        lv.s0[0] = b; lv.s1[0] = b + n; lv.s0[1] = b + 2 * n; lv.s1[1] = b + 3 * n;
+        lv.p0 = b + 4 * n; lv.p1 = b + 5 * n; lv.t0 = b + 6 * n; lv.t1 = b + 7 * n;
+    }
+    return SF_OK;
+}
+
+int engine_plans(Engine& E, cudaStream_t st)
+{
+    // ---- propagation: level h of stream s runs ceil(N / nfmax) launches;
+    // launch k holds segment k of every (stream, level) that has one.  The last
+    // segment writes the prediction planes, earlier ones alternate with t0/t1.
+    int maxseg = 0;
+    for (auto& s : E.st)
+        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, kNfMax));
+    E.prop.resize(maxseg);
+    for (int k = 0; k < maxseg; ++k) {
+        std::vector<PropJob> jobs;
+        std::vector<int4> work;
+        bool c8 = false;
+        for (int want = kNfMax; want >= 1; --want) {   // longest tiles (most passes) first
+            for (auto& s : E.st) {
+                for (int h = 0; h < s.L; ++h) {
+                    sf_level_state& lv = s.lv[h];
+                    const int nseg = ceil_div(lv.N, kNfMax);
+                    if (k >= nseg) continue;
+                    const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
+                    if (nf != want) continue;
+                    const bool top = h == s.L - 1;
+                    auto out_of = [&](int seg, float4*& o0, float4*& o1) {
+                        const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
+                        o0 = to_pred ? lv.p0 : lv.t0;
+                        o1 = to_pred ? lv.p1 : lv.t1;
+                    };
+                    PropJob j;
+                    std::memset(&j, 0, sizeof(j));
+                    j.g = make_grid(lv.grid);
+                    if (k == 0) {
+                        j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+                        j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
+                        j.apply_wscale = 1;
+                    } else {
+                        float4 *o0, *o1;
+                        out_of(k - 1, o0, o1);
+                        j.in0[0] = j.in0[1] = o0;
+                        j.in1[0] = j.in1[1] = top ? nullptr : o1;
+                    }
+                    out_of(k, j.out0, j.out1);
+                    if (top) j.out1 = nullptr;
+                    j.nf = nf;
+                    j.dt = 1.0f / (float)lv.N;
+                    j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
+                    jobs.push_back(j);
+                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
+                    c8 |= !top;
+                }
+            }
+        }
+        E.prop[k].c8 = c8;
+        E.prop[k].smem = prop_smem_bytes();
+        int r = upload_plan(jobs, work, E.prop[k], st);
+        if (r) return r;
+    }
+    // ---- solve: every level of every stream, one 32 x 32 tile per CTA
+    {
+        std::vector<SolveJob> jobs;
+        std::vector<int4> work;
+        for (auto& s : E.st) {
+            for (int h = s.L - 1; h >= 0; --h) {
+                sf_level_state& lv = s.lv[h];
+                SolveJob j;
+                std::memset(&j, 0, sizeof(j));
+                j.g = make_grid(lv.grid);
+                j.level = h + 1;
+                j.top = h == s.L - 1;
+                j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
+                j.inv45 = 1.0f / (j.g4 + j.g5);
+                j.inv5 = 1.0f / j.g5;
+                for (int q = 0; q < 2; ++q) { j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q]; }
+                j.p0 = lv.p0;
+                j.p1 = lv.p1;
+                j.x_out = lv.t0;
+                j.y_out = (float*)lv.t1;
+                j.image = s.image;
+                j.range = s.range;
+                j.H1 = s.H;
+                j.W1 = s.W;
+                j.lambda_ref = s.p.lambda_ref;
+                j.tiles_x = ceil_div(lv.grid.W, kSolveT);
+                jobs.push_back(j);
+                add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kSolveT, kSolveT);
+            }
+        }
+        int r = upload_plan(jobs, work, E.solve, st);
+        if (r) return r;
+    }
+    // ---- smoothing + reconstruction cascade
+    int maxL = 0;
+    for (auto& s : E.st) maxL = std::max(maxL, s.L);
+    E.smooth.resize(maxL);
+    for (int d = 0; d < maxL; ++d) {
+        std::vector<SmoothJob> jobs;
+        std::vector<int4> work;
+        size_t smem = 0;
+        for (auto& s : E.st) {
+            const int h = s.L - 1 - d;
+            if (h < 0) continue;
+            sf_level_state& lv = s.lv[h];
+            SmoothJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.H = lv.grid.H;
+            j.W = lv.grid.W;
+            j.S = lv.S;
+            j.top = h == s.L - 1;
+            j.x_in = lv.t0;
+            j.y_in = (const float*)lv.t1;
+            for (int q = 0; q < 2; ++q) {
+                j.s0_new[q] = lv.s0[q];
+                j.s1_new[q] = lv.s1[q];
+                j.s0c[q] = j.top ? nullptr : s.lv[h + 1].s0[q];
+            }
+            if (!j.top) { j.Hc = s.lv[h + 1].grid.H; j.Wc = s.lv[h + 1].grid.W; }
+            if (h == 0) {
+                j.flow_out = s.flow;
+                j.invdepth_out = s.inv;
+                j.frame_outputs = s.image == nullptr;   // single-stream filter: per-frame output pointers
+            }
+            j.tiles_x = ceil_div(lv.grid.W, kSmoothT);
+            jobs.push_back(j);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kSmoothT, kSmoothT);
+            smem = std::max(smem, smooth_smem_bytes(j.S));
+        }
+        E.smooth[d].smem = smem;
+        int r = upload_plan(jobs, work, E.smooth[d], st);
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+// create the streams' levels, the status word and the plans
+int engine_init(Engine& E)
+{
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SF_ECUDA;
+    int r = SF_OK;
+    for (auto& s : E.st) {
+        r = engine_levels(s, st);
+        if (r) break;
+    }
+    if (!r && cudaMalloc(&E.status, sizeof(int)) != cudaSuccess) { E.status = nullptr; r = SF_ENOMEM; }
+    if (!r) r = cudaMemsetAsync(E.status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = engine_plans(E, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaStreamDestroy(st);
+    return r;
+}
+
+// the launches of one frame (no host synchronisation; capturable)
+int engine_launches(Engine& E, const float* image, const float* range, float dt, float wscale, float* flow,
+                    float* inv, cudaStream_t st)
+{
+    UpdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.image = image;
+    a.range = range;
+    a.H1 = E.st[0].H;
+    a.W1 = E.st[0].W;
+    a.lambda_ref = E.st[0].p.lambda_ref;
+    a.parity = E.parity;
+    a.init = !E.initialised;
+    int slot = 0, r;
+    if (!a.init) {
+        for (auto& pl : E.prop) {
+            ProfScope ps(E.prof, slot++, st);
+            r = launch_propagate(pl, E.parity, wscale, E.flags, E.status, st);
+            if (r) return r;
+        }
+    } else {
+        slot = (int)E.prop.size();
+    }
+    {
+        ProfScope ps(E.prof, slot++, st);
+        r = launch_solve(E.solve, a, st);
+        if (r) return r;
+    }
+    const int check = (E.flags & SF_CHECK_FINITE) != 0;
+    for (auto& pl : E.smooth) {
+        if (!pl.nwork) continue;
+        ProfScope ps(E.prof, slot++, st);
+        r = launch_smooth(pl, E.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
+        if (r) return r;
+    }
+    return SF_OK;
+}
+
+int engine_status(Engine& E)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
+    int s = 0;
+    if (cudaMemcpy(&s, E.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
+    if (cudaMemset(E.status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
+    if (s & kStatusNonFinite) return SF_ENONFINITE;
+    if (s & kStatusCfl) return SF_WARN_CFL;
+    return SF_OK;
+}
+
+}  // namespace
+
+struct sf_ctx {
+    Engine E;
     // staging for sf_step_host
     float* stage_image = nullptr;
     float* stage_range = nullptr;
@@ -231,16 +528,16 @@ struct sf_ctx {
     float* stage_inv = nullptr;
 };
 
+struct sf_batch {
+    Engine E;
+};
+
 namespace {
 
 void destroy_ctx(sf_ctx* c)
 {
     if (!c) return;
-    for (auto& pl : c->prop) free_plan(pl);
-    free_plan(c->upd);
-    free_plan(c->init);
-    for (int h = 0; h < c->L; ++h) cudaFree(c->lv[h].block);
-    cudaFree(c->status);
+    engine_free(c->E);
     cudaFree(c->stage_image);
     cudaFree(c->stage_range);
     cudaFree(c->stage_flow);
@@ -248,144 +545,17 @@ void destroy_ctx(sf_ctx* c)
     delete c;
 }
 
-int build_plans(sf_ctx* c, cudaStream_t st)
+void destroy_batch(sf_batch* b)
 {
-    const int L = c->L;
-    // ---- propagation: level h runs ceil(N_h / nfmax) launches; launch k holds
-    // segment k of every level that has one.  The last segment writes the
-    // prediction planes, earlier ones alternate so that this holds.
-    int nseg[SF_MAX_LEVELS], maxseg = 0;
-    for (int h = 0; h < L; ++h) {
-        nseg[h] = ceil_div(c->lv[h].N, kNfMax);
-        maxseg = std::max(maxseg, nseg[h]);
-    }
-    c->prop.resize(maxseg);
-    for (int k = 0; k < maxseg; ++k) {
-        std::vector<PropJob> jobs;
-        std::vector<int4> work;
-        size_t smem = 0;
-        bool c8 = false;
-        // lower levels first: they carry the most work per tile
-        for (int h = 0; h < L; ++h) {
-            if (k >= nseg[h]) continue;
-            sf_level_state& lv = c->lv[h];
-            const bool top = (h == L - 1);
-            const int base = lv.N / nseg[h], extra = lv.N % nseg[h];
-            const int nf = base + (k < extra ? 1 : 0);
-            PropJob j;
-            std::memset(&j, 0, sizeof(j));
-            j.g = make_grid(lv.grid);
-            auto out_of = [&](int seg, float4*& o0, float4*& o1) {
-                const bool to_pred = ((nseg[h] - 1 - seg) % 2) == 0;
-                o0 = to_pred ? lv.p0 : lv.t0;
-                o1 = to_pred ? lv.p1 : lv.t1;
-            };
-            if (k == 0) {
-                j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
-                j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
-                j.apply_wscale = 1;
-            } else {
-                float4 *o0, *o1;
-                out_of(k - 1, o0, o1);
-                j.in0[0] = j.in0[1] = o0;
-                j.in1[0] = j.in1[1] = top ? nullptr : o1;
-            }
-            out_of(k, j.out0, j.out1);
-            if (top) j.out1 = nullptr;
-            j.nf = nf;
-            j.dt = 1.0f / (float)lv.N;
-            j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
-            jobs.push_back(j);
-            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
-            c8 |= !top;
-        }
-        // one instantiation per launch: a mixed launch runs the top level through
-        // the 8-channel path (it skips dw and Y when in1 is null)
-        smem = prop_smem_bytes();
-        c->prop[k].c8 = c8;
-        c->prop[k].smem = smem;
-        int r = upload_plan(jobs, work, c->prop[k], st);
-        if (r) return r;
-    }
-    // ---- update (and the first-frame initialisation): every level in one launch
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool init = pass == 1;
-        std::vector<UpdJob> jobs;
-        std::vector<int4> work;
-        size_t smem = 0;
-        for (int hh = 0; hh < L; ++hh) {
-            const int h = L - 1 - hh;   // longest tiles first: the top level has the widest halo
-            sf_level_state& lv = c->lv[h];
-            UpdJob j;
-            std::memset(&j, 0, sizeof(j));
-            j.g = make_grid(lv.grid);
-            j.level = h + 1;
-            j.top = (h == L - 1);
-            j.S = init ? 0 : lv.S;
-            j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
-            j.inv45 = 1.0f / (j.g4 + j.g5);
-            j.inv5 = 1.0f / j.g5;
-            for (int q = 0; q < 2; ++q) {
-                j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q];
-                j.s0_new[q] = lv.s0[q]; j.s1_new[q] = lv.s1[q];
-            }
-            j.p0 = lv.p0;
-            j.p1 = lv.p1;
-            j.diag = nullptr;
-            j.tiles_x = ceil_div(lv.grid.W, kUpdTX);
-            jobs.push_back(j);
-            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kUpdTX, kUpdTY);
-            smem = std::max(smem, upd_smem(j.S));
-        }
-        Plan& pl = init ? c->init : c->upd;
-        pl.smem = smem;
-        int r = upload_plan(jobs, work, pl, st);
-        if (r) return r;
-    }
-    return SF_OK;
+    if (!b) return;
+    engine_free(b->E);
+    delete b;
 }
-
-// reconstruction cascade and outputs of a frame whose new state has parity q
-int run_reconstruct(sf_ctx* c, int q, float dt, float* flow_out, float* inv_out, cudaStream_t st)
-{
-    int slot = (int)c->prop.size() + 1;
-    const int L = c->L;
-    for (int h = L - 2; h >= -1; --h) {
-        // h >= 0: reconstruct level h from level h+1; h == -1 with L == 1: outputs only
-        if (h == -1 && L > 1) break;
-        const int lvl = h >= 0 ? h : 0;
-        sf_level_state& lv = c->lv[lvl];
-        ReconArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.H = lv.grid.H;
-        a.W = lv.grid.W;
-        a.s0 = lv.s0[q];
-        a.s1 = lv.s1[q];
-        if (h >= 0) {
-            a.Hc = c->lv[h + 1].grid.H;
-            a.Wc = c->lv[h + 1].grid.W;
-            a.s0c = c->lv[h + 1].s0[q];
-        }
-        if (lvl == 0) {
-            a.flow_out = flow_out;
-            a.invdepth_out = inv_out;
-            a.inv_dt = 1.0f / dt;
-            a.check_finite = (c->p.flags & SF_CHECK_FINITE) != 0;
-            a.status = c->status;
-        }
-        ProfScope ps(c->prof, slot++, st);
-        int r = launch_reconstruct(a, st);
-        if (r) return r;
-    }
-    return SF_OK;
-}
-
-bool valid_ptr_align(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// C ABI
+// C ABI: single-stream filter
 // ----------------------------------------------------------------------------
 
 extern "C" {
@@ -415,49 +585,17 @@ int sf_params_default(sf_params* p, int H, int W, int levels)
 int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
 {
     if (out) *out = nullptr;
-    if (!p || !out || levels < 1 || levels > SF_MAX_LEVELS || levels > kMaxLevelsDev) return SF_EINVAL;
-    const int m = 1 << (levels - 1);
-    if (H <= 0 || W <= 0 || H % m || W % m || H / m < 8 || W / m < 8) return SF_EINVAL;
-    if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->cx) || !std::isfinite(p->cy)) return SF_EINVAL;
-    if (!(p->lambda_ref > 0) || !(p->gamma[2] > 0) || !(p->gamma[4] > 0)) return SF_EINVAL;
-    for (int k = 0; k < 5; ++k)
-        if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
-    if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
-    for (int h = 0; h < levels; ++h) {
-        const float s = (float)(1 << h);
-        const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / s));
-        if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
-    }
+    if (!out) return SF_EINVAL;
+    int r = check_params(H, W, levels, p);
+    if (r) return r;
     sf_ctx* c = new (std::nothrow) sf_ctx();
     if (!c) return SF_ENOMEM;
-    c->H = H; c->W = W; c->L = levels; c->p = *p;
-    c->parity = 0; c->initialised = 0; c->dt_prev = 0.0f;
-    int r = SF_OK;
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return SF_ECUDA; }
-    for (int h = 0; h < levels && !r; ++h) {
-        sf_level_state& lv = c->lv[h];
-        const float s = (float)(1 << h);
-        lv.grid.H = H >> h;
-        lv.grid.W = W >> h;
-        lv.grid.fx = p->fx / s; lv.grid.fy = p->fy / s; lv.grid.cx = p->cx / s; lv.grid.cy = p->cy / s;
-        lv.N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / s));
-        lv.S = p->smooth_iters[h];
-        for (int k = 0; k < 5; ++k) lv.gamma[k] = p->gamma[k];
-        const double dmu_c = (double)s / (double)p->fx;   // reading R10
-        lv.gamma[2] = (float)(p->gamma[2] * dmu_c * dmu_c);
-        const size_t n = (size_t)lv.grid.H * lv.grid.W;
-        if (cudaMalloc(&lv.block, 8 * n * sizeof(float4)) != cudaSuccess) { lv.block = nullptr; r = SF_ENOMEM; break; }
-        cudaMemsetAsync(lv.block, 0, 8 * n * sizeof(float4), st);
-        float4* b = (float4*)lv.block;
-        lv.s0[0] = b; lv.s1[0] = b + n; lv.s0[1] = b + 2 * n; lv.s1[1] = b + 3 * n;
-        lv.p0 = b + 4 * n; lv.p1 = b + 5 * n; lv.t0 = b + 6 * n; lv.t1 = b + 7 * n;
-    }
-    if (!r && cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) { c->status = nullptr; r = SF_ENOMEM; }
-    if (!r) r = cudaMemsetAsync(c->status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    if (!r) r = build_plans(c, st);
-    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    cudaStreamDestroy(st);
+    c->E.st.resize(1);
+    EngineStream& s = c->E.st[0];
+    std::memset(&s, 0, sizeof(s));
+    s.H = H; s.W = W; s.L = levels; s.p = *p;
+    c->E.flags = p->flags;
+    r = engine_init(c->E);
     if (r) { destroy_ctx(c); return r; }
     *out = c;
     return SF_OK;
@@ -466,7 +604,7 @@ int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
 int sf_reset(sf_ctx* c)
 {
     if (!c) return SF_EINVAL;
-    c->initialised = 0;
+    c->E.initialised = 0;
     return SF_OK;
 }
 
@@ -474,31 +612,13 @@ int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* 
             void* stream)
 {
     if (!c || !image || !range || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    UpdArgs a;
-    a.image = image; a.range = range; a.H1 = c->H; a.W1 = c->W; a.lambda_ref = c->p.lambda_ref;
-    a.parity = c->parity;
-    int r;
-    if (!c->initialised) {
-        a.init = 1;
-        r = launch_update(c->init, a, st);
-    } else {
-        a.init = 0;
-        const float wscale = dt / c->dt_prev;   // reading R9
-        for (size_t k = 0; k < c->prop.size(); ++k) {
-            ProfScope ps(c->prof, (int)k, st);
-            r = launch_propagate(c->prop[k], c->parity, wscale, c->p.flags, c->status, st);
-            if (r) return r;
-        }
-        ProfScope ps(c->prof, (int)c->prop.size(), st);
-        r = launch_update(c->upd, a, st);
-    }
+    Engine& E = c->E;
+    const float wscale = E.initialised ? dt / E.dt_prev : 1.0f;   // reading R9
+    const int r = engine_launches(E, image, range, dt, wscale, flow_out, invdepth_out, (cudaStream_t)stream);
     if (r) return r;
-    r = run_reconstruct(c, c->parity ^ 1, dt, flow_out, invdepth_out, st);
-    if (r) return r;
-    c->parity ^= 1;
-    c->initialised = 1;
-    c->dt_prev = dt;
+    E.parity ^= 1;
+    E.initialised = 1;
+    E.dt_prev = dt;
     return SF_OK;
 }
 
@@ -507,7 +627,7 @@ int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, fl
 {
     if (!c || !image || !range) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t n = (size_t)c->H * c->W;
+    const size_t n = (size_t)c->E.st[0].H * c->E.st[0].W;
     if (!c->stage_image) {
         if (cudaMalloc(&c->stage_image, n * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&c->stage_range, n * sizeof(float)) != cudaSuccess ||
@@ -518,12 +638,14 @@ int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, fl
     if (cudaMemcpyAsync(c->stage_image, image, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(c->stage_range, range, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SF_ECUDA;
-    int r = sf_step(c, c->stage_image, c->stage_range, dt, flow_out ? c->stage_flow : nullptr, invdepth_out ? c->stage_inv : nullptr,
-                    stream);
+    int r = sf_step(c, c->stage_image, c->stage_range, dt, flow_out ? c->stage_flow : nullptr,
+                    invdepth_out ? c->stage_inv : nullptr, stream);
     if (r) return r;
-    if (flow_out && cudaMemcpyAsync(flow_out, c->stage_flow, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (flow_out && cudaMemcpyAsync(flow_out, c->stage_flow, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess)
         return SF_ECUDA;
-    if (invdepth_out && cudaMemcpyAsync(invdepth_out, c->stage_inv, n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (invdepth_out &&
+        cudaMemcpyAsync(invdepth_out, c->stage_inv, n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SF_ECUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
 }
@@ -531,57 +653,51 @@ int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, fl
 int sf_status(sf_ctx* c)
 {
     if (!c) return SF_EINVAL;
-    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
-    int s = 0;
-    if (cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
-    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
-    if (s & kStatusNonFinite) return SF_ENONFINITE;
-    if (s & kStatusCfl) return SF_WARN_CFL;
-    return SF_OK;
+    return engine_status(c->E);
 }
 
 int sf_get_state(sf_ctx* c, int level, float* dst, float* dt_prev, void* stream)
 {
-    if (!c || level < 0 || level >= c->L || !dst) return SF_EINVAL;
-    sf_level_state& lv = c->lv[level];
+    if (!c || level < 0 || level >= c->E.st[0].L || !dst) return SF_EINVAL;
+    sf_level_state& lv = c->E.st[0].lv[level];
     const int n = lv.grid.H * lv.grid.W;
-    k_pack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(lv.s0[c->parity], lv.s1[c->parity],
-                                                                              dst, n);
-    if (dt_prev) *dt_prev = c->dt_prev;
+    k_pack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(lv.s0[c->E.parity],
+                                                                              lv.s1[c->E.parity], dst, n);
+    if (dt_prev) *dt_prev = c->E.dt_prev;
     return last_error();
 }
 
 int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* stream)
 {
-    if (!c || level < 0 || level >= c->L || !src || !(dt_prev > 0.0f)) return SF_EINVAL;
-    sf_level_state& lv = c->lv[level];
+    if (!c || level < 0 || level >= c->E.st[0].L || !src || !(dt_prev > 0.0f)) return SF_EINVAL;
+    sf_level_state& lv = c->E.st[0].lv[level];
     const int n = lv.grid.H * lv.grid.W;
-    k_unpack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(src, lv.s0[c->parity],
-                                                                                lv.s1[c->parity], n);
-    c->dt_prev = dt_prev;
-    c->initialised = 1;
+    k_unpack<<<std::min(ceil_div(n, 256), 1184), 256, 0, (cudaStream_t)stream>>>(src, lv.s0[c->E.parity],
+                                                                                lv.s1[c->E.parity], n);
+    c->E.dt_prev = dt_prev;
+    c->E.initialised = 1;
     return last_error();
 }
 
 int sf_profile(sf_ctx* c, int enable)
 {
     if (!c) return SF_EINVAL;
-    c->prof.enabled = enable != 0;
+    c->E.prof.enabled = enable != 0;
     return SF_OK;
 }
 
 int sf_profile_read(sf_ctx* c, float* ms, int* count, int n)
 {
     if (!c || (n > 0 && (!ms || !count))) return SF_EINVAL;
-    const int r = c->prof.read(ms, count, n);
+    const int r = c->E.prof.read(ms, count, n);
     if (r) return r;
-    return (int)c->prop.size() + 1 + std::max(1, c->L - 1);
+    return c->E.launches_per_step();
 }
 
 int sf_kernels_per_step(const sf_ctx* c)
 {
     if (!c) return SF_EINVAL;
-    return (int)c->prop.size() + 1 + std::max(1, c->L - 1);
+    return c->E.launches_per_step();
 }
 
 void sf_destroy(sf_ctx* c) { destroy_ctx(c); }
@@ -601,7 +717,128 @@ const char* sf_strerror(int code)
 }
 
 // ---------------------------------------------------------------------------
-// stage entry points
+// C ABI: batched streams
+// ---------------------------------------------------------------------------
+
+int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params, sf_batch** out)
+{
+    if (out) *out = nullptr;
+    if (n < 1 || n > 4096 || !H || !W || !levels || !params || !out) return SF_EINVAL;
+    for (int s = 0; s < n; ++s) {
+        const int r = check_params(H[s], W[s], levels[s], params + s);
+        if (r) return r;
+        if ((params[s].flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)) !=
+            (params[0].flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)))
+            return SF_EINVAL;   // one scheme variant per batch (one kernel instantiation)
+    }
+    sf_batch* b = new (std::nothrow) sf_batch();
+    if (!b) return SF_ENOMEM;
+    Engine& E = b->E;
+    E.st.resize(n);
+    E.flags = params[0].flags;
+    size_t io_floats = 0;
+    for (int s = 0; s < n; ++s) io_floats += 6 * (size_t)H[s] * W[s];   // image, range, flow (3), inverse depth
+    int r = SF_OK;
+    if (cudaMalloc(&E.io, io_floats * sizeof(float)) != cudaSuccess) { E.io = nullptr; r = SF_ENOMEM; }
+    if (!r && cudaMemset(E.io, 0, io_floats * sizeof(float)) != cudaSuccess) r = SF_ECUDA;
+    size_t off = 0;
+    for (int s = 0; s < n && !r; ++s) {
+        EngineStream& es = E.st[s];
+        std::memset(&es, 0, sizeof(es));
+        es.H = H[s]; es.W = W[s]; es.L = levels[s]; es.p = params[s];
+        const size_t np = (size_t)H[s] * W[s];
+        float* base = (float*)E.io + off;
+        es.image = base; es.range = base + np; es.flow = base + 2 * np; es.inv = base + 5 * np;
+        off += 6 * np;
+    }
+    if (!r) r = engine_init(E);
+    if (r) { destroy_batch(b); return r; }
+    *out = b;
+    return SF_OK;
+}
+
+int sf_batch_buffers(sf_batch* b, int s, float** image, float** range, float** flow, float** invdepth)
+{
+    if (!b || s < 0 || s >= (int)b->E.st.size()) return SF_EINVAL;
+    const EngineStream& es = b->E.st[s];
+    if (image) *image = es.image;
+    if (range) *range = es.range;
+    if (flow) *flow = es.flow;
+    if (invdepth) *invdepth = es.inv;
+    return SF_OK;
+}
+
+int sf_batch_step(sf_batch* b, float dt, void* stream)
+{
+    if (!b || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
+    Engine& E = b->E;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float wscale = E.initialised ? dt / E.dt_prev : 1.0f;   // reading R9
+    const int q = E.parity;
+    int r;
+    // steady state (same dt as the previous frame, initialised, a capturable
+    // stream, launch attributes already set by earlier plain steps, not
+    // profiling): replay the frame's graph for this parity
+    const bool graphable = E.initialised && wscale == 1.0f && st != nullptr && E.steps_plain >= 2 && !E.prof.enabled;
+    if (graphable) {
+        if (!E.graph[q] || E.graph_dt[q] != dt) {
+            if (E.graph[q]) { cudaGraphExecDestroy(E.graph[q]); E.graph[q] = nullptr; }
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SF_ECUDA;
+            r = engine_launches(E, nullptr, nullptr, dt, 1.0f, nullptr, nullptr, st);
+            const cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (r || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return r ? r : SF_ECUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&E.graph[q], g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) { E.graph[q] = nullptr; return SF_ECUDA; }
+            E.graph_dt[q] = dt;
+        }
+        if (cudaGraphLaunch(E.graph[q], st) != cudaSuccess) return SF_ECUDA;
+    } else {
+        r = engine_launches(E, nullptr, nullptr, dt, wscale, nullptr, nullptr, st);
+        if (r) return r;
+        if (E.initialised) E.steps_plain++;
+    }
+    E.parity ^= 1;
+    E.initialised = 1;
+    E.dt_prev = dt;
+    return SF_OK;
+}
+
+int sf_batch_status(sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    return engine_status(b->E);
+}
+
+int sf_batch_launches_per_step(const sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    return b->E.launches_per_step();
+}
+
+int sf_batch_profile(sf_batch* b, int enable)
+{
+    if (!b) return SF_EINVAL;
+    b->E.prof.enabled = enable != 0;
+    return SF_OK;
+}
+
+int sf_batch_profile_read(sf_batch* b, float* ms, int* count, int n)
+{
+    if (!b || (n > 0 && (!ms || !count))) return SF_EINVAL;
+    const int r = b->E.prof.read(ms, count, n);
+    if (r) return r;
+    return b->E.launches_per_step();
+}
+
+void sf_batch_destroy(sf_batch* b) { destroy_batch(b); }
+
+// ---------------------------------------------------------------------------
+// C ABI: stage entry points
 // ---------------------------------------------------------------------------
 
 int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* s0_in, const float* s1_in,
@@ -609,8 +846,7 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
 {
     if (!g || g->H < 1 || g->W < 1 || N < 1 || !s0_in || !s0_out) return SF_EINVAL;
     if ((s1_in == nullptr) != (s1_out == nullptr)) return SF_EINVAL;
-    if (!valid_ptr_align(s0_in) || !valid_ptr_align(s0_out) || !valid_ptr_align(s1_in) || !valid_ptr_align(s1_out))
-        return SF_EINVAL;
+    if (!aligned16(s0_in) || !aligned16(s0_out) || !aligned16(s1_in) || !aligned16(s1_out)) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool c8 = s1_in != nullptr;
     const int nseg = ceil_div(N, kNfMax);
@@ -669,50 +905,69 @@ int sf_update(const sf_grid* g, int level, int top, int S, int init, const float
               const float* p0, const float* p1, float* s0_new, float* s1_new, float* diag, void* stream)
 {
     if (!g || !gamma || !image || !range || !s0_new || !s1_new || level < 1 || level > kMaxLevelsDev || S < 0 ||
-        S > 16)
+        S > 16 || g->H < 1 || g->W < 1)
         return SF_EINVAL;
     if ((g->H << (level - 1)) > H1 || (g->W << (level - 1)) > W1) return SF_EINVAL;
     if (!init && (!p0 || (top ? (!s0_cur || !s1_cur) : !p1))) return SF_EINVAL;
+    if (!(gamma[4] > 0.0f) || !(gamma[3] >= 0.0f)) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    UpdJob j;
+    const size_t n = (size_t)g->H * g->W;
+    SolveJob j;
     std::memset(&j, 0, sizeof(j));
     j.g = make_grid(*g);
     j.level = level;
     j.top = top != 0;
-    j.S = S;
     j.g1 = gamma[0]; j.g2 = gamma[1]; j.g3 = gamma[2]; j.g4 = gamma[3]; j.g5 = gamma[4];
-    if (!(j.g5 > 0.0f) || !(j.g4 >= 0.0f)) return SF_EINVAL;
     j.inv45 = 1.0f / (j.g4 + j.g5);
     j.inv5 = 1.0f / j.g5;
     j.s0_cur[0] = j.s0_cur[1] = (const float4*)s0_cur;
     j.s1_cur[0] = j.s1_cur[1] = (const float4*)s1_cur;
     j.p0 = (const float4*)p0;
     j.p1 = (const float4*)p1;
-    j.s0_new[0] = j.s0_new[1] = (float4*)s0_new;
-    j.s1_new[0] = j.s1_new[1] = (float4*)s1_new;
     j.diag = diag;
-    j.tiles_x = ceil_div(g->W, kUpdTX);
-    std::vector<int4> work;
-    add_tiles(work, 0, g->H, g->W, kUpdTX, kUpdTY);
-    const size_t woff = work_offset(sizeof(UpdJob));
-    const size_t bytes = woff + work.size() * sizeof(int4);
-    void* mem = nullptr;
-    if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) return SF_ENOMEM;
-    std::vector<unsigned char> host(bytes);
-    std::memcpy(host.data(), &j, sizeof(UpdJob));
-    std::memcpy(host.data() + woff, work.data(), work.size() * sizeof(int4));
-    int r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    Plan pl;
-    pl.jobs = mem;
-    pl.work = (int4*)((unsigned char*)mem + woff);
-    pl.nwork = (int)work.size();
-    pl.smem = upd_smem(init ? 0 : S);
+    j.tiles_x = ceil_div(g->W, kSolveT);
+    SmoothJob m;
+    std::memset(&m, 0, sizeof(m));
+    m.H = g->H;
+    m.W = g->W;
+    m.S = S;
+    m.top = top != 0;
+    m.s0_new[0] = m.s0_new[1] = (float4*)s0_new;
+    m.s1_new[0] = m.s1_new[1] = (float4*)s1_new;
+    m.tiles_x = ceil_div(g->W, kSmoothT);
+    std::vector<int4> wsolve, wsmooth;
+    add_tiles(wsolve, 0, g->H, g->W, kSolveT, kSolveT);
+    add_tiles(wsmooth, 0, g->H, g->W, kSmoothT, kSmoothT);
+    // one stream-ordered allocation: the solution and Y-hat planes, then the
+    // two launch descriptors
+    const size_t fields = n * sizeof(float4) + ((n * sizeof(float) + 255) & ~(size_t)255);
+    const size_t o_js = fields, o_ws = o_js + work_offset(sizeof(SolveJob));
+    const size_t o_jm = o_ws + work_offset(wsolve.size() * sizeof(int4)), o_wm = o_jm + work_offset(sizeof(SmoothJob));
+    const size_t bytes = o_wm + wsmooth.size() * sizeof(int4);
+    unsigned char* mem = nullptr;
+    if (cudaMallocAsync((void**)&mem, bytes, st) != cudaSuccess) return SF_ENOMEM;
+    j.x_out = (float4*)mem;
+    j.y_out = (float*)(mem + n * sizeof(float4));
+    m.x_in = j.x_out;
+    m.y_in = j.y_out;
+    std::vector<unsigned char> host(bytes - fields);
+    std::memcpy(host.data() + (o_js - fields), &j, sizeof(SolveJob));
+    std::memcpy(host.data() + (o_ws - fields), wsolve.data(), wsolve.size() * sizeof(int4));
+    std::memcpy(host.data() + (o_jm - fields), &m, sizeof(SmoothJob));
+    std::memcpy(host.data() + (o_wm - fields), wsmooth.data(), wsmooth.size() * sizeof(int4));
+    int r = cudaMemcpyAsync(mem + fields, host.data(), host.size(), cudaMemcpyHostToDevice, st) == cudaSuccess
+                ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;  // host buffer lifetime
     UpdArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.image = image; a.range = range; a.H1 = H1; a.W1 = W1; a.lambda_ref = lambda_ref;
-    a.parity = 0;   // new planes are read at parity ^ 1; both slots point to the same buffer
+    a.parity = 0;   // s*_cur[0]; the smoothing writes slot q = 0 (both slots are the caller's planes)
     a.init = init != 0;
-    if (!r) r = launch_update(pl, a, st);
+    Plan ps, pm;
+    ps.jobs = mem + o_js; ps.work = (int4*)(mem + o_ws); ps.nwork = (int)wsolve.size();
+    pm.jobs = mem + o_jm; pm.work = (int4*)(mem + o_wm); pm.nwork = (int)wsmooth.size(); pm.smem = smooth_smem_bytes(S);
+    if (!r) r = launch_solve(ps, a, st);
+    if (!r) r = launch_smooth(pm, 0, 1.0f, 0, nullptr, nullptr, nullptr, st);
     cudaFreeAsync(mem, st);
     return r;
 }
@@ -809,8 +1064,7 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
 {
     if (!g || g->H < 1 || g->W < 1 || N < 1 || !s0_in || !s0_out) return SF_EINVAL;
     if ((s1_in == nullptr) != (s1_out == nullptr)) return SF_EINVAL;
-    if (!valid_ptr_align(s0_in) || !valid_ptr_align(s0_out) || !valid_ptr_align(s1_in) || !valid_ptr_align(s1_out))
-        return SF_EINVAL;
+    if (!aligned16(s0_in) || !aligned16(s0_out) || !aligned16(s1_in) || !aligned16(s1_out)) return SF_EINVAL;
     const size_t n = (size_t)g->H * g->W;
     if (n > kNoAllocMaxPixels) return SF_EINVAL;                 // larger frames: use sf_propagate
     const int nseg = ceil_div(N, kNfMax);
@@ -867,389 +1121,3 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
     }
     return r;
 }
-
-// ---------------------------------------------------------------------------
-// batched streams (sf_batch_*): many independent filters of uneven sizes in
-// one set of launches per frame, captured in a CUDA graph
-// ---------------------------------------------------------------------------
-
-struct sf_batch_stream {
-    int H, W, L;
-    sf_params p;
-    sf_level_state lv[SF_MAX_LEVELS];
-    float* image;      // device input/output slots owned by the batch
-    float* range;
-    float* flow;
-    float* inv;
-};
-
-struct ReconPlan {
-    ReconJob* jobs = nullptr;
-    int2* work = nullptr;
-    int nwork = 0;
-};
-
-struct sf_batch {
-    std::vector<sf_batch_stream> st;
-    int parity = 0;
-    int initialised = 0;
-    float dt_prev = 0.0f;
-    int flags = 0;
-    int* status = nullptr;
-    std::vector<Plan> prop;
-    Plan upd, init;
-    std::vector<ReconPlan> recon;   // one per cascade depth
-    void* io = nullptr;             // the input/output slots of every stream
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    float graph_dt[2] = {0.0f, 0.0f};
-    int steps_plain = 0;
-    Profiler prof;                  // per-launch timing (sf_batch_profile); disables graph replay
-};
-
-namespace {
-
-void destroy_batch(sf_batch* b)
-{
-    if (!b) return;
-    for (int q = 0; q < 2; ++q)
-        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
-    for (auto& pl : b->prop) free_plan(pl);
-    free_plan(b->upd);
-    free_plan(b->init);
-    for (auto& r : b->recon) { cudaFree(r.jobs); cudaFree(r.work); }
-    for (auto& s : b->st)
-        for (int h = 0; h < s.L; ++h) cudaFree(s.lv[h].block);
-    cudaFree(b->io);
-    cudaFree(b->status);
-    delete b;
-}
-
-int batch_plans(sf_batch* b, cudaStream_t st)
-{
-    // ---- propagation: launch k holds segment k of every (stream, level)
-    int maxseg = 0;
-    for (auto& s : b->st)
-        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, kNfMax));
-    b->prop.resize(maxseg);
-    for (int k = 0; k < maxseg; ++k) {
-        std::vector<PropJob> jobs;
-        std::vector<int4> work;
-        bool c8 = false;
-        // longest tiles first: larger nf (more passes) before smaller
-        for (int want = kNfMax; want >= 1; --want) {
-            for (auto& s : b->st) {
-                for (int h = 0; h < s.L; ++h) {
-                    sf_level_state& lv = s.lv[h];
-                    const int nseg = ceil_div(lv.N, kNfMax);
-                    if (k >= nseg) continue;
-                    const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
-                    if (nf != want) continue;
-                    const bool top = h == s.L - 1;
-                    auto out_of = [&](int seg, float4*& o0, float4*& o1) {
-                        const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
-                        o0 = to_pred ? lv.p0 : lv.t0;
-                        o1 = to_pred ? lv.p1 : lv.t1;
-                    };
-                    PropJob j;
-                    std::memset(&j, 0, sizeof(j));
-                    j.g = make_grid(lv.grid);
-                    if (k == 0) {
-                        j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
-                        j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
-                        j.apply_wscale = 1;
-                    } else {
-                        float4 *o0, *o1;
-                        out_of(k - 1, o0, o1);
-                        j.in0[0] = j.in0[1] = o0;
-                        j.in1[0] = j.in1[1] = top ? nullptr : o1;
-                    }
-                    out_of(k, j.out0, j.out1);
-                    if (top) j.out1 = nullptr;
-                    j.nf = nf;
-                    j.dt = 1.0f / (float)lv.N;
-                    j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
-                    jobs.push_back(j);
-                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
-                    c8 |= !top;
-                }
-            }
-        }
-        b->prop[k].c8 = c8;
-        b->prop[k].smem = prop_smem_bytes();
-        int r = upload_plan(jobs, work, b->prop[k], st);
-        if (r) return r;
-    }
-    // ---- update and initialisation: every (stream, level), top levels first
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool init = pass == 1;
-        std::vector<UpdJob> jobs;
-        std::vector<int4> work;
-        size_t smem = 0;
-        for (int top_first = 1; top_first >= 0; --top_first) {
-            for (auto& s : b->st) {
-                for (int h = 0; h < s.L; ++h) {
-                    if ((h == s.L - 1) != (top_first == 1)) continue;
-                    sf_level_state& lv = s.lv[h];
-                    UpdJob j;
-                    std::memset(&j, 0, sizeof(j));
-                    j.g = make_grid(lv.grid);
-                    j.level = h + 1;
-                    j.top = h == s.L - 1;
-                    j.S = init ? 0 : lv.S;
-                    j.g1 = lv.gamma[0]; j.g2 = lv.gamma[1]; j.g3 = lv.gamma[2]; j.g4 = lv.gamma[3]; j.g5 = lv.gamma[4];
-                    j.inv45 = 1.0f / (j.g4 + j.g5);
-                    j.inv5 = 1.0f / j.g5;
-                    for (int q = 0; q < 2; ++q) {
-                        j.s0_cur[q] = lv.s0[q]; j.s1_cur[q] = lv.s1[q];
-                        j.s0_new[q] = lv.s0[q]; j.s1_new[q] = lv.s1[q];
-                    }
-                    j.p0 = lv.p0;
-                    j.p1 = lv.p1;
-                    j.image = s.image;
-                    j.range = s.range;
-                    j.H1 = s.H;
-                    j.W1 = s.W;
-                    j.lambda_ref = s.p.lambda_ref;
-                    j.tiles_x = ceil_div(lv.grid.W, kUpdTX);
-                    jobs.push_back(j);
-                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kUpdTX, kUpdTY);
-                    smem = std::max(smem, upd_smem(j.S));
-                }
-            }
-        }
-        Plan& pl = init ? b->init : b->upd;
-        pl.smem = smem;
-        int r = upload_plan(jobs, work, pl, st);
-        if (r) return r;
-    }
-    // ---- reconstruction cascade: depth d rebuilds level L_s - 2 - d of every stream
-    int maxL = 0;
-    for (auto& s : b->st) maxL = std::max(maxL, s.L);
-    const int depths = std::max(1, maxL - 1);
-    b->recon.resize(depths);
-    for (int d = 0; d < depths; ++d) {
-        std::vector<ReconJob> jobs;
-        std::vector<int2> work;
-        for (auto& s : b->st) {
-            const int h = s.L - 2 - d;
-            if (h < 0 && !(s.L == 1 && d == 0)) continue;
-            const int lvl = h >= 0 ? h : 0;
-            sf_level_state& lv = s.lv[lvl];
-            ReconJob j;
-            std::memset(&j, 0, sizeof(j));
-            j.H = lv.grid.H;
-            j.W = lv.grid.W;
-            for (int q = 0; q < 2; ++q) {
-                j.s0[q] = lv.s0[q];
-                j.s1[q] = lv.s1[q];
-                if (h >= 0) j.s0c[q] = s.lv[h + 1].s0[q];
-            }
-            if (h >= 0) { j.Hc = s.lv[h + 1].grid.H; j.Wc = s.lv[h + 1].grid.W; }
-            if (lvl == 0) { j.flow_out = s.flow; j.invdepth_out = s.inv; }
-            jobs.push_back(j);
-            for (int p0 = 0; p0 < j.H * j.W; p0 += kReconChunk) work.push_back(make_int2((int)jobs.size() - 1, p0));
-        }
-        ReconPlan& rp = b->recon[d];
-        rp.nwork = (int)work.size();
-        if (cudaMalloc(&rp.jobs, jobs.size() * sizeof(ReconJob)) != cudaSuccess) return SF_ENOMEM;
-        if (cudaMalloc(&rp.work, work.size() * sizeof(int2)) != cudaSuccess) return SF_ENOMEM;
-        if (cudaMemcpyAsync(rp.jobs, jobs.data(), jobs.size() * sizeof(ReconJob), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(rp.work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return SF_ECUDA;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return SF_ECUDA;
-    }
-    return SF_OK;
-}
-
-// the launches of one frame (no host synchronisation; capturable)
-int batch_launches(sf_batch* b, float dt, float wscale, cudaStream_t st)
-{
-    UpdArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.parity = b->parity;
-    a.init = !b->initialised;
-    int r;
-    int slot = 0;
-    if (a.init) {
-        r = launch_update(b->init, a, st);
-        slot = (int)b->prop.size() + 1;
-    } else {
-        for (auto& pl : b->prop) {
-            ProfScope ps(b->prof, slot++, st);
-            r = launch_propagate(pl, b->parity, wscale, b->flags, b->status, st);
-            if (r) return r;
-        }
-        ProfScope ps(b->prof, slot++, st);
-        r = launch_update(b->upd, a, st);
-    }
-    if (r) return r;
-    for (auto& rp : b->recon) {
-        if (!rp.nwork) continue;
-        ProfScope ps(b->prof, slot++, st);
-        k_reconstruct_jobs<<<rp.nwork, kThreads, 0, st>>>(rp.jobs, rp.work, b->parity ^ 1, 1.0f / dt,
-                                                          (b->flags & SF_CHECK_FINITE) != 0, b->status);
-        r = last_error();
-        if (r) return r;
-    }
-    return SF_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params, sf_batch** out)
-{
-    if (out) *out = nullptr;
-    if (n < 1 || n > 4096 || !H || !W || !levels || !params || !out) return SF_EINVAL;
-    for (int s = 0; s < n; ++s) {
-        const sf_params* p = params + s;
-        const int L = levels[s];
-        if (L < 1 || L > SF_MAX_LEVELS || L > kMaxLevelsDev) return SF_EINVAL;
-        const int m = 1 << (L - 1);
-        if (H[s] <= 0 || W[s] <= 0 || H[s] % m || W[s] % m || H[s] / m < 8 || W[s] / m < 8) return SF_EINVAL;
-        if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->cx) || !std::isfinite(p->cy)) return SF_EINVAL;
-        if (!(p->lambda_ref > 0) || !(p->gamma[2] > 0) || !(p->gamma[4] > 0)) return SF_EINVAL;
-        for (int k = 0; k < 5; ++k)
-            if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
-        if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
-        for (int h = 0; h < L; ++h) {
-            const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
-            if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
-        }
-        if ((p->flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)) != (params[0].flags & (SF_DOMINANT_LITERAL | SF_SOURCE_SPLIT)))
-            return SF_EINVAL;   // one scheme variant per batch (one kernel instantiation)
-    }
-    sf_batch* b = new (std::nothrow) sf_batch();
-    if (!b) return SF_ENOMEM;
-    b->st.resize(n);
-    b->flags = params[0].flags;
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { delete b; return SF_ECUDA; }
-    int r = SF_OK;
-    size_t io_floats = 0;
-    for (int s = 0; s < n; ++s) io_floats += 6 * (size_t)H[s] * W[s];   // image, range, flow (3), invdepth
-    if (cudaMalloc(&b->io, io_floats * sizeof(float)) != cudaSuccess) { b->io = nullptr; r = SF_ENOMEM; }
-    size_t off = 0;
-    for (int s = 0; s < n && !r; ++s) {
-        sf_batch_stream& bs = b->st[s];
-        bs.H = H[s]; bs.W = W[s]; bs.L = levels[s]; bs.p = params[s];
-        const size_t np = (size_t)H[s] * W[s];
-        float* base = (float*)b->io + off;
-        bs.image = base; bs.range = base + np; bs.flow = base + 2 * np; bs.inv = base + 5 * np;
-        off += 6 * np;
-        for (int h = 0; h < bs.L && !r; ++h) {
-            sf_level_state& lv = bs.lv[h];
-            const float sc = (float)(1 << h);
-            lv.grid.H = bs.H >> h; lv.grid.W = bs.W >> h;
-            lv.grid.fx = bs.p.fx / sc; lv.grid.fy = bs.p.fy / sc; lv.grid.cx = bs.p.cx / sc; lv.grid.cy = bs.p.cy / sc;
-            lv.N = bs.p.iters[h] > 0 ? bs.p.iters[h] : std::max(1, (int)std::ceil(bs.p.max_flow / sc));
-            lv.S = bs.p.smooth_iters[h];
-            for (int k = 0; k < 5; ++k) lv.gamma[k] = bs.p.gamma[k];
-            const double dmu_c = (double)sc / (double)bs.p.fx;   // reading R10
-            lv.gamma[2] = (float)(bs.p.gamma[2] * dmu_c * dmu_c);
-            const size_t nl = (size_t)lv.grid.H * lv.grid.W;
-            if (cudaMalloc(&lv.block, 8 * nl * sizeof(float4)) != cudaSuccess) { lv.block = nullptr; r = SF_ENOMEM; break; }
-            cudaMemsetAsync(lv.block, 0, 8 * nl * sizeof(float4), st);
-            float4* blk = (float4*)lv.block;
-            lv.s0[0] = blk; lv.s1[0] = blk + nl; lv.s0[1] = blk + 2 * nl; lv.s1[1] = blk + 3 * nl;
-            lv.p0 = blk + 4 * nl; lv.p1 = blk + 5 * nl; lv.t0 = blk + 6 * nl; lv.t1 = blk + 7 * nl;
-        }
-    }
-    if (!r && b->io) r = cudaMemsetAsync(b->io, 0, io_floats * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    if (!r && cudaMalloc(&b->status, sizeof(int)) != cudaSuccess) { b->status = nullptr; r = SF_ENOMEM; }
-    if (!r) r = cudaMemsetAsync(b->status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    if (!r) r = batch_plans(b, st);
-    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    cudaStreamDestroy(st);
-    if (r) { destroy_batch(b); return r; }
-    *out = b;
-    return SF_OK;
-}
-
-int sf_batch_buffers(sf_batch* b, int s, float** image, float** range, float** flow, float** invdepth)
-{
-    if (!b || s < 0 || s >= (int)b->st.size()) return SF_EINVAL;
-    if (image) *image = b->st[s].image;
-    if (range) *range = b->st[s].range;
-    if (flow) *flow = b->st[s].flow;
-    if (invdepth) *invdepth = b->st[s].inv;
-    return SF_OK;
-}
-
-int sf_batch_step(sf_batch* b, float dt, void* stream)
-{
-    if (!b || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    const float wscale = b->initialised ? dt / b->dt_prev : 1.0f;   // reading R9
-    const int q = b->parity;
-    int r;
-    // steady state (same dt as the previous frame, initialised, a capturable
-    // stream, launch attributes already set by an earlier plain step): replay
-    // the frame's graph for this parity
-    const bool graphable = b->initialised && wscale == 1.0f && st != nullptr && b->steps_plain >= 2 &&
-                           !b->prof.enabled;
-    if (graphable) {
-        if (!b->graph[q] || b->graph_dt[q] != dt) {
-            if (b->graph[q]) { cudaGraphExecDestroy(b->graph[q]); b->graph[q] = nullptr; }
-            cudaGraph_t g = nullptr;
-            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SF_ECUDA;
-            r = batch_launches(b, dt, 1.0f, st);
-            const cudaError_t e = cudaStreamEndCapture(st, &g);
-            if (r || e != cudaSuccess) { if (g) cudaGraphDestroy(g); return r ? r : SF_ECUDA; }
-            const cudaError_t ei = cudaGraphInstantiate(&b->graph[q], g, 0);
-            cudaGraphDestroy(g);
-            if (ei != cudaSuccess) { b->graph[q] = nullptr; return SF_ECUDA; }
-            b->graph_dt[q] = dt;
-        }
-        if (cudaGraphLaunch(b->graph[q], st) != cudaSuccess) return SF_ECUDA;
-    } else {
-        r = batch_launches(b, dt, wscale, st);
-        if (r) return r;
-        if (b->initialised) b->steps_plain++;
-    }
-    b->parity ^= 1;
-    b->initialised = 1;
-    b->dt_prev = dt;
-    return SF_OK;
-}
-
-int sf_batch_status(sf_batch* b)
-{
-    if (!b) return SF_EINVAL;
-    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
-    int s = 0;
-    if (cudaMemcpy(&s, b->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
-    if (cudaMemset(b->status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
-    if (s & kStatusNonFinite) return SF_ENONFINITE;
-    if (s & kStatusCfl) return SF_WARN_CFL;
-    return SF_OK;
-}
-
-int sf_batch_launches_per_step(const sf_batch* b)
-{
-    if (!b) return SF_EINVAL;
-    int nrec = 0;
-    for (auto& rp : b->recon) nrec += rp.nwork ? 1 : 0;
-    return (int)b->prop.size() + 1 + nrec;
-}
-
-int sf_batch_profile(sf_batch* b, int enable)
-{
-    if (!b) return SF_EINVAL;
-    b->prof.enabled = enable != 0;
-    return SF_OK;
-}
-
-int sf_batch_profile_read(sf_batch* b, float* ms, int* count, int n)
-{
-    if (!b || (n > 0 && (!ms || !count))) return SF_EINVAL;
-    const int r = b->prof.read(ms, count, n);
-    if (r) return r;
-    return sf_batch_launches_per_step(b);
-}
-
-void sf_batch_destroy(sf_batch* b) { destroy_batch(b); }
-
-}  // extern "C"

@@ -1,19 +1,21 @@
 // sf_kernels.cuh -- the CUDA kernels of libsf (sm_103a).
 //
 //   k_propagate   prediction of Sec. 4.6 with temporal blocking: a CTA loads
-//                 a tile plus an nf-pixel halo of the state into shared
-//                 memory once and runs nf sub-iterations (2 nf axis passes)
-//                 there, ping-ponging two buffers while the valid window
-//                 shrinks by one pixel per pass; only the tile goes back to
-//                 HBM.  One launch serves every level of the pyramid (a work
-//                 list of (job, tile) items).
-//   k_update      image model (Eqs. 30-31) by separable 5-tap filters, the
+//                 a 64 x 64 region (an output tile plus an nf-pixel halo) of
+//                 the state into registers once and runs nf sub-iterations
+//                 (2 nf axis passes) there, exchanging neighbours by warp
+//                 shuffles and shared-memory edge rows; only the tile goes
+//                 back to HBM.  One launch serves every level of every stream
+//                 (a work list of (job, tile) items).
+//   k_solve       image model (Eqs. 30-31) by separable 5-tap filters, the
 //                 inverse-depth model (Eqs. 32-34), the 3x3 least-squares
-//                 update (Eqs. 42-50) in closed form, the blend (Eq. 52) and
-//                 S passes of 5x5 smoothing, fused in shared memory; the
-//                 level's pyramid data (2x2 means) is built on the fly from
-//                 the level-1 input.
-//   k_reconstruct Eq. 26 for one level, plus the level-1 outputs.
+//                 update (Eqs. 42-50) in closed form and the blend (Eq. 52),
+//                 once per pixel; the level's pyramid data (2x2 means) is
+//                 built on the fly from the level-1 input.
+//   k_smooth_recon S passes of 5x5 smoothing (Sec. 4.5) in shared memory,
+//                 the reconstruction of Eq. 26 and the level-1 outputs.
+//   k_reconstruct Eq. 26 for one level, plus the level-1 outputs (stage
+//                 entry point sf_reconstruct).
 //   k_pack/k_unpack  interleaved float4 state <-> planar checkpoint layout.
 #pragma once
 
@@ -318,35 +320,10 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     }
 }
 
-// n / d for 0 <= n < 2^16 and 1 <= d < 2^16 with a precomputed multiplier
-// m = ceil(2^32 / d) (exact in that range); d == 1 has no 32-bit multiplier.
-__device__ __forceinline__ unsigned div_magic(int d) { return d > 1 ? 0xFFFFFFFFu / (unsigned)d + 1u : 0u; }
-__device__ __forceinline__ int fast_div(int n, unsigned m, int d) { return d > 1 ? (int)__umulhi((unsigned)n, m) : n; }
 
 // --------------------------------------------------------------------------
 // update
 // --------------------------------------------------------------------------
-
-struct UpdJob {
-    Grid g;
-    int level;             // 1-based pyramid level (selects the 2x2-mean depth)
-    int top;
-    int S;                 // smoothing passes
-    float g1, g2, g3, g4, g5;
-    float inv45, inv5;     // 1 / (g4 + g5) and 1 / g5 (Eq. 52 with and without a measurement)
-    const float* image;    // this job's level-1 input (batched streams); nullptr: the launch's
-    const float* range;
-    int H1, W1;
-    float lambda_ref;
-    const float4* s0_cur[2];
-    const float4* s1_cur[2];
-    const float4* p0;
-    const float4* p1;
-    float4* s0_new[2];
-    float4* s1_new[2];
-    float* diag;
-    int tiles_x;
-};
 
 struct UpdArgs {
     const float* image;    // level-1 input, H1 x W1
@@ -402,21 +379,6 @@ __device__ __forceinline__ void level_data(int level, const UpdArgs& a, int i, i
     }
 }
 
-__host__ __device__ inline void upd_layout(int TX, int TY, int S, size_t* off_F, size_t* off_R, size_t* off_Y,
-                                           size_t* total)
-{
-    const int SX = TX + 4 * S, SY = TY + 4 * S;        // solve region
-    const int DX = SX + 4, DY = SY + 4;                // image region (model halo 2)
-    const size_t data = (size_t)DX * DY + (size_t)(SX + 2) * (SY + 2) + 2 * (size_t)DY * SX;  // floats
-    const size_t tmp = 4 * (size_t)SX * SY;            // smoothing temporary (float4), aliases the data region
-    const size_t first = ((data > tmp ? data : tmp) + 3) & ~(size_t)3;
-    *off_F = first;                                    // solution, float4 per pixel
-    *off_R = first + 4 * (size_t)SX * SY;
-    *off_Y = *off_R + (size_t)TX * TY;
-    *total = (*off_Y + (size_t)TX * TY) * sizeof(float);
-}
-
-constexpr int kUpdThreads = 512;
 
 // eta, dd = a/|m'| and 1 - eta_x^2 at pixel (i, j) without divisions
 __device__ __forceinline__ Geo update_geometry(const Grid& g, int i, int j)
@@ -438,69 +400,131 @@ __device__ __forceinline__ Geo update_geometry(const Grid& g, int i, int j)
     return o;
 }
 
-__global__ void __launch_bounds__(kUpdThreads)
-k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs args, int TX, int TY)
-{
-    extern __shared__ float smf[];
-    const int4 wk = work[blockIdx.x];
-    const UpdJob& J = jobs[wk.x];
-    const Grid g = J.g;
-    const int S = args.init ? 0 : J.S;
-    if (J.image) {   // batched streams carry their own inputs
-        args.image = J.image;
-        args.range = J.range;
-        args.H1 = J.H1;
-        args.W1 = J.W1;
-        args.lambda_ref = J.lambda_ref;
-    }
-    const int SX = TX + 4 * S, SY = TY + 4 * S, DX = SX + 4, DY = SY + 4, RXd = SX + 2;
-    size_t offF, offR, offY, total;
-    upd_layout(TX, TY, S, &offF, &offR, &offY, &total);
-    float* Yd = smf;                                  // [DY][DX] level image, replicated border
-    float* Rd = Yd + DX * DY;                         // [SY+2][SX+2] level inverse depth
-    float* H0 = Rd + RXd * (SY + 2);                  // [DY][SX] sum g Y
-    float* H1 = H0 + DY * SX;                         // [DY][SX] sum g d Y
-    float4* F = reinterpret_cast<float4*>(smf + offF);   // [SY][SX] solution (.w unused)
-    float4* T = reinterpret_cast<float4*>(smf);          // smoothing temporary (aliases the above)
-    float* Ro = smf + offR;                           // [TY][TX] new inverse depth
-    float* Yo = smf + offY;                           // [TY][TX] new Y-hat
+// --------------------------------------------------------------------------
+// solve (models + 3x3 update + blend, once per pixel) and smooth+reconstruct
+// --------------------------------------------------------------------------
 
-    const int sx0 = wk.z - 2 * S, sy0 = wk.y - 2 * S;  // solve-region origin (image coords)
-    // 1. level data with replicated border
-    const unsigned mDX = div_magic(DX), mSX = div_magic(SX), mTX = div_magic(TX);
-    for (int idx = threadIdx.x; idx < DX * DY; idx += blockDim.x) {
-        const int dy = fast_div(idx, mDX, DX), dx = idx - dy * DX;
-        const int i = clampi(sy0 - 2 + dy, 0, g.H - 1), j = clampi(sx0 - 2 + dx, 0, g.W - 1);
-        float y, r;
-        level_data(J.level, args, i, j, y, r);
-        Yd[idx] = y;
-        if (dy >= 1 && dy < SY + 3 && dx >= 1 && dx < SX + 3) Rd[(dy - 1) * RXd + (dx - 1)] = r;
+struct SolveJob {
+    Grid g;
+    int level, top;
+    float g1, g2, g3, g4, g5, inv45, inv5;
+    const float4* s0_cur[2];
+    const float4* s1_cur[2];
+    const float4* p0;
+    const float4* p1;
+    float4* x_out;         // (solution, new inverse depth)
+    float* y_out;          // new Y-hat
+    float* diag;
+    const float* image;    // this job's level-1 input (batched streams); nullptr: the launch's
+    const float* range;
+    int H1, W1;
+    float lambda_ref;
+    int tiles_x;
+};
+
+constexpr int kSolveT = 32;          // output tile edge
+constexpr int kSolveThreads = 256;
+
+// Level data of the (T + 4)^2 region around a solve tile into shared memory;
+// on levels 1 and 2 every load of the thread is issued before the first store.
+template <int L>
+__device__ __forceinline__ void solve_region(const UpdArgs& a, const Grid& g, int y0, int x0, float* Yd, float* Rd)
+{
+    constexpr int T = kSolveT, DX = T + 4, RXd = T + 2, N = DX * DX;
+    constexpr int K = (N + kSolveThreads - 1) / kSolveThreads;
+    if constexpr (L > 2) {
+        // 16 or 64 level-1 pixels per value: the loads of one value are enough in flight
+        for (int idx = threadIdx.x; idx < N; idx += kSolveThreads) {
+            const int dy = idx / DX, dx = idx - dy * DX;
+            float y, r;
+            LevelData<L>::get(a, clampi(y0 - 2 + dy, 0, g.H - 1), clampi(x0 - 2 + dx, 0, g.W - 1), y, r);
+            Yd[idx] = y;
+            if (dy >= 1 && dy < T + 3 && dx >= 1 && dx < T + 3) Rd[(dy - 1) * RXd + (dx - 1)] = r;
+        }
+    } else {
+        float yv[K], rv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int idx = threadIdx.x + k * kSolveThreads;
+            yv[k] = 0.0f;
+            rv[k] = 0.0f;
+            if (idx < N) {
+                const int dy = idx / DX, dx = idx - dy * DX;
+                LevelData<L>::get(a, clampi(y0 - 2 + dy, 0, g.H - 1), clampi(x0 - 2 + dx, 0, g.W - 1), yv[k], rv[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int idx = threadIdx.x + k * kSolveThreads;
+            if (idx < N) {
+                const int dy = idx / DX, dx = idx - dy * DX;
+                Yd[idx] = yv[k];
+                if (dy >= 1 && dy < T + 3 && dx >= 1 && dx < T + 3) Rd[(dy - 1) * RXd + (dx - 1)] = rv[k];
+            }
+        }
+    }
+}
+
+// Image model (Eqs. 30-31, separable 5-tap g and g*d filters), inverse-depth
+// model (Eqs. 32-34), the closed-form minimiser of Eq. 42 and the blend of
+// Eq. 52 for every pixel of a 32 x 32 tile.  The 3x3 normal equations of
+// Eq. 46, A = g1 r r^T + g2 q q^T + g3 I with r = P gradY and q = P gradR +
+// dmu^2 rho-hat eta, are solved in Woodbury form around the prior:
+// x = prior - R K e, R = [r q], e the two residuals at the prior and
+// K = (g3 I + Gamma R^T R)^-1 Gamma, whose 2x2 determinant
+// g3^2 + g3 (g1 |r|^2 + g2 |q|^2) + g1 g2 |r x q|^2 has no cancellation.
+__global__ void __launch_bounds__(kSolveThreads)
+k_solve(const SolveJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs args)
+{
+    constexpr int T = kSolveT, DX = T + 4, RXd = T + 2;
+    __shared__ float Yd[DX * DX];          // level image, replicated border
+    __shared__ float Rd[RXd * RXd];        // level inverse depth (0: no measurement)
+    __shared__ float H0[DX * T];           // sum g Y   (rows of the image region, columns of the tile)
+    __shared__ float H1[DX * T];           // sum g d Y
+    const int4 wk = work[blockIdx.x];
+    const SolveJob& J = jobs[wk.x];
+    const Grid g = J.g;
+    if (J.image) {
+        args.image = J.image; args.range = J.range; args.H1 = J.H1; args.W1 = J.W1; args.lambda_ref = J.lambda_ref;
+    }
+    const int x0 = wk.z, y0 = wk.y;
+    switch (J.level) {
+    case 1: solve_region<1>(args, g, y0, x0, Yd, Rd); break;
+    case 2: solve_region<2>(args, g, y0, x0, Yd, Rd); break;
+    case 3: solve_region<3>(args, g, y0, x0, Yd, Rd); break;
+    default: solve_region<4>(args, g, y0, x0, Yd, Rd); break;
     }
     __syncthreads();
-    // 2. horizontal 5-tap passes (g = [1 4 6 4 1]/16, and g*d)
-    for (int idx = threadIdx.x; idx < DY * SX; idx += blockDim.x) {
-        const int dy = fast_div(idx, mSX, SX), sx = idx - dy * SX;
-        const float* row = Yd + dy * DX + sx;  // taps at offsets -2..2 of column sx+2
+    for (int idx = threadIdx.x; idx < DX * T; idx += blockDim.x) {
+        const int dy = idx / T, sx = idx % T;
+        const float* row = Yd + dy * DX + sx;
         const float m2 = row[0], m1 = row[1], c = row[2], p1 = row[3], p2 = row[4];
         H0[idx] = (m2 + p2) * 0.0625f + (m1 + p1) * 0.25f + c * 0.375f;
-        H1[idx] = (p2 - m2) * 0.125f + (p1 - m1) * 0.25f;  // sum g(d) d Y
+        H1[idx] = (p2 - m2) * 0.125f + (p1 - m1) * 0.25f;
     }
     __syncthreads();
-    // 3. models, solve, blend for every in-image pixel of the solve region
     const int parity = args.parity;
-    for (int idx = threadIdx.x; idx < SX * SY; idx += blockDim.x) {
-        const int sy = fast_div(idx, mSX, SX), sx = idx - sy * SX;
-        const int i = sy0 + sy, j = sx0 + sx;
-        if (i < 0 || i >= g.H || j < 0 || j >= g.W) continue;
-        const float* c0 = H0 + sy * SX + sx;  // rows sy..sy+4 of the image region = offsets -2..2
-        const float* c1 = H1 + sy * SX + sx;
-        const float Yhat = (c0[0] + c0[4 * SX]) * 0.0625f + (c0[SX] + c0[3 * SX]) * 0.25f + c0[2 * SX] * 0.375f;
-        const float d1 = (c1[0] + c1[4 * SX]) * 0.0625f + (c1[SX] + c1[3 * SX]) * 0.25f + c1[2 * SX] * 0.375f;
-        const float d2 = (c0[4 * SX] - c0[0]) * 0.125f + (c0[3 * SX] - c0[SX]) * 0.25f;
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+        const int sy = idx / T, sx = idx % T;
+        const int i = y0 + sy, j = x0 + sx;
+        if (i >= g.H || j >= g.W) continue;
+        const size_t gi = (size_t)i * g.W + j;
+        // state reads first: their latency overlaps the model arithmetic
+        float4 P0 = make_float4(0.f, 0.f, 0.f, 0.f), Q = P0, C0 = P0, C1 = P0;
+        if (!args.init) {
+            P0 = J.p0[gi];
+            if (J.top) { C0 = J.s0_cur[parity][gi]; C1 = J.s1_cur[parity][gi]; }
+            else Q = J.p1[gi];
+        }
+        const float* c0 = H0 + sy * T + sx;
+        const float* c1 = H1 + sy * T + sx;
+        const float Yhat = (c0[0] + c0[4 * T]) * 0.0625f + (c0[T] + c0[3 * T]) * 0.25f + c0[2 * T] * 0.375f;
+        const float d1 = (c1[0] + c1[4 * T]) * 0.0625f + (c1[T] + c1[3 * T]) * 0.25f + c1[2 * T] * 0.375f;
+        const float d2 = (c0[4 * T] - c0[0]) * 0.125f + (c0[3 * T] - c0[T]) * 0.25f;
         const float* rr = Rd + (sy + 1) * RXd + (sx + 1);
         const float rc = rr[0];
         const bool valid = rc > 0.0f;
-        float e1 = 0.0f, e2 = 0.0f;  // min-abs depth differences (Eqs. 32-33)
+        float e1 = 0.0f, e2 = 0.0f;
         if (valid) {
             {
                 const float rp = rr[1], rm = rr[-1];
@@ -517,144 +541,242 @@ k_update(const UpdJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs
         }
         const Geo geo = update_geometry(g, i, j);
         const float exy = geo.ex * geo.ey, exz = geo.ex * geo.ez;
-        // lifts dmu B d (Eqs. 31, 34, reading R4)
         const float gx = geo.dd * (geo.omx2 * d1);
         const float gy = geo.dd * fmaf(-exy, d1, geo.ez * d2);
         const float gz = geo.dd * fmaf(-exz, d1, -geo.ey * d2);
         const float ax_ = geo.dd * (geo.omx2 * e1);
         const float ay_ = geo.dd * fmaf(-exy, e1, geo.ez * e2);
         const float az_ = geo.dd * fmaf(-exz, e1, -geo.ey * e2);
-        const size_t gi = (size_t)i * g.W + j;
-        float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f, rho_new;
+        float x0v = 0.0f, x1v = 0.0f, x2v = 0.0f, rho_new;
         if (args.init) {
-            rho_new = valid ? rc : 0.0f;  // reading R18
+            rho_new = valid ? rc : 0.0f;   // reading R18
         } else {
-            float px, py, pz, Yref, rref, rpred;
-            const float4 P0 = J.p0[gi];
-            if (J.top) {
-                const float4 C0 = J.s0_cur[parity][gi];
-                const float4 C1 = J.s1_cur[parity][gi];
-                px = P0.x; py = P0.y; pz = P0.z;
-                Yref = C1.w;       // Y-hat^k     (Eq. 43, R11)
-                rref = C0.w;       // rho^k       (Eq. 44, R11)
-            } else {
-                const float4 P1 = J.p1[gi];
-                px = P1.x; py = P1.y; pz = P1.z;
-                Yref = P1.w;       // Y-hat^{k+}  (Eq. 48)
-                rref = P0.w;       // rho^{k+}    (Eq. 49)
-            }
-            rpred = P0.w;
+            float px, py, pz, Yref, rref;
+            if (J.top) { px = P0.x; py = P0.y; pz = P0.z; Yref = C1.w; rref = C0.w; }   // Eqs. 43-45, R11
+            else { px = Q.x; py = Q.y; pz = Q.z; Yref = Q.w; rref = P0.w; }            // Eqs. 48-50
             const float dmu2 = geo.dd * geo.dd * geo.omx2;
-            // rows of E_Y and E_rho in the unknown: r = P gradY = gradY (tangent),
-            // q = P gradR + dmu^2 rho-hat eta
-            const float rX = gx, rY = gy, rZ = gz;
             const float k = dmu2 * rc;
             const float qX = fmaf(k, geo.ex, ax_), qY = fmaf(k, geo.ey, ay_), qZ = fmaf(k, geo.ez, az_);
             const float cY = dmu2 * (Yhat - Yref);
             const float cR = dmu2 * (rc - rref);
             const float G1 = J.g1, G2 = valid ? J.g2 : 0.0f, G3 = J.g3;
-            // residuals at the prior, then the closed-form minimiser of Eq. 42:
-            // x = prior - R K e, K = (g3 I + Gamma R^T R)^-1 Gamma (Woodbury form
-            // of the normal equations A x = b of Eq. 46)
-            const float eY = fmaf(rX, px, fmaf(rY, py, fmaf(rZ, pz, cY)));
+            const float eY = fmaf(gx, px, fmaf(gy, py, fmaf(gz, pz, cY)));
             const float eR = fmaf(qX, px, fmaf(qY, py, fmaf(qZ, pz, cR)));
-            const float rr2 = fmaf(rX, rX, fmaf(rY, rY, rZ * rZ));
+            const float rr2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
             const float qq2 = fmaf(qX, qX, fmaf(qY, qY, qZ * qZ));
-            const float rq = fmaf(rX, qX, fmaf(rY, qY, rZ * qZ));
-            const float cx_ = fmaf(rY, qZ, -rZ * qY), cy_ = fmaf(rZ, qX, -rX * qZ), cz_ = fmaf(rX, qY, -rY * qX);
+            const float rq = fmaf(gx, qX, fmaf(gy, qY, gz * qZ));
+            const float cx_ = fmaf(gy, qZ, -gz * qY), cy_ = fmaf(gz, qX, -gx * qZ), cz_ = fmaf(gx, qY, -gy * qX);
             const float cross2 = fmaf(cx_, cx_, fmaf(cy_, cy_, cz_ * cz_));
             const float det = fmaf(G3, G3, fmaf(G3, fmaf(G1, rr2, G2 * qq2), G1 * G2 * cross2));
             const float inv = 1.0f / det;
             const float k11 = G1 * fmaf(G2, qq2, G3) * inv;
             const float k22 = G2 * fmaf(G1, rr2, G3) * inv;
             const float k12 = -G1 * G2 * rq * inv;
-            const float c1 = fmaf(k11, eY, k12 * eR);
-            const float c2 = fmaf(k12, eY, k22 * eR);
-            x0 = px - fmaf(c1, rX, c2 * qX);
-            x1 = py - fmaf(c1, rY, c2 * qY);
-            x2 = pz - fmaf(c1, rZ, c2 * qZ);
-            // Eq. 52; without a measurement gamma4 = 0
-            rho_new = valid ? fmaf(J.g4, rc, J.g5 * rpred) * J.inv45 : (J.g5 * rpred) * J.inv5;
+            const float cc1 = fmaf(k11, eY, k12 * eR);
+            const float cc2 = fmaf(k12, eY, k22 * eR);
+            x0v = px - fmaf(cc1, gx, cc2 * qX);
+            x1v = py - fmaf(cc1, gy, cc2 * qY);
+            x2v = pz - fmaf(cc1, gz, cc2 * qZ);
+            rho_new = valid ? fmaf(J.g4, rc, J.g5 * P0.w) * J.inv45 : (J.g5 * P0.w) * J.inv5;   // Eq. 52
         }
-        F[idx] = make_float4(x0, x1, x2, 0.0f);
-        const int ty = sy - 2 * S, tx = sx - 2 * S;
-        if (ty >= 0 && ty < TY && tx >= 0 && tx < TX) {
-            Ro[ty * TX + tx] = rho_new;
-            Yo[ty * TX + tx] = Yhat;
-            if (J.diag) {
-                float* d = J.diag + gi * 12;
-                d[0] = Yhat; d[1] = gx; d[2] = gy; d[3] = gz;
-                d[4] = rc; d[5] = ax_; d[6] = ay_; d[7] = az_;
-                d[8] = x0; d[9] = x1; d[10] = x2; d[11] = 0.0f;
+        J.x_out[gi] = make_float4(x0v, x1v, x2v, rho_new);
+        J.y_out[gi] = Yhat;
+        if (J.diag) {
+            float* d = J.diag + gi * 12;
+            d[0] = Yhat; d[1] = gx; d[2] = gy; d[3] = gz;
+            d[4] = rc; d[5] = ax_; d[6] = ay_; d[7] = az_;
+            d[8] = x0v; d[9] = x1v; d[10] = x2v; d[11] = 0.0f;
+        }
+    }
+}
+
+struct SmoothJob {
+    int H, W;
+    int S, top;
+    const float4* x_in;    // (solution, new inverse depth)
+    const float* y_in;     // new Y-hat
+    float4* s0_new[2];     // indexed by the parity of the frame being written
+    float4* s1_new[2];
+    const float4* s0c[2];  // coarser level's new state (reconstruction), or null
+    int Hc, Wc;
+    float* flow_out;       // level 1 only
+    float* invdepth_out;
+    int frame_outputs;     // level 1 of a single-stream filter: the launch's output pointers
+    int tiles_x;
+};
+
+constexpr int kSmoothT = 32;          // output tile edge (one warp-width row)
+constexpr int kSmoothThreads = 256;
+constexpr int kSmoothOut = kSmoothT * kSmoothT / kSmoothThreads;   // output pixels per thread
+constexpr int kSmoothC = kSmoothT / 2 + 2;                        // coarse tile edge for the reconstruction
+static_assert(kSmoothT == 32 && kSmoothT * kSmoothT % kSmoothThreads == 0, "tile = warp-wide rows");
+
+// shared memory: the coarse tile (float4), the new inverse depth of the tile,
+// and the three flow planes of the region, each row padded to an odd pitch
+__host__ __device__ inline size_t smooth_smem_bytes(int S)
+{
+    const size_t SX = kSmoothT + 4 * S;
+    return kSmoothC * kSmoothC * sizeof(float4) + (kSmoothT * kSmoothT + 3 * SX * (SX + 1)) * sizeof(float);
+}
+
+// S passes of the 5-tap mean with replicated ends over p[lo..hi] (stride
+// `st`), in place.  A pass keeps its 5-wide window in registers and reads
+// four values ahead, all still unwritten.
+__device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, int S)
+{
+    for (int s = 0; s < S; ++s) {
+        float w0 = p[lo * st], w1 = w0, w2 = w0;
+        float w3 = p[min(lo + 1, hi) * st], w4 = p[min(lo + 2, hi) * st];
+        float sum = (w0 + w1) + (w2 + w3) + w4;
+        for (int e = lo; e <= hi; e += 5) {
+            float n[5];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) n[u] = p[min(e + 3 + u, hi) * st];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+                if (e + u <= hi) p[(e + u) * st] = sum * 0.2f;
+                sum += n[u] - w0;
+                w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = n[u];
+            }
+        }
+    }
+}
+
+// S passes of the 5x5 mean with replicated border (Sec. 4.5) on the solution,
+// then the level's new state: top: (w, rho) and (0, Y-hat); lower: the
+// reconstruction w_h = up(w_{h+1}) + dw_h (Eq. 26, reading R14) and (dw, Y-hat);
+// level 1 also writes flow = w / dt and the inverse depth.
+//
+// The 5x5 mean with a replicated border is a row pass followed by a column
+// pass, and row and column passes commute, so S passes are S row passes on
+// every row of the (32 + 4S)^2 region followed by S column passes on the 32
+// tile columns.  A line is one thread's work: no barrier between passes.
+// At the image border the line ends are the image's; inside the image the
+// region's halo of 2S pixels absorbs the effect of the cut.
+__global__ void __launch_bounds__(kSmoothThreads)
+k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work, int q, float inv_dt,
+               int check_finite, int* __restrict__ status, float* frame_flow, float* frame_inv)
+{
+    extern __shared__ float4 sm4[];
+    const int4 wk = work[blockIdx.x];
+    const SmoothJob& J = jobs[wk.x];
+    constexpr int T = kSmoothT, CE = kSmoothC;
+    const int S = J.S, SX = T + 4 * S, SP = SX + 1, PL = SX * SP;
+    float4* Cc = sm4;                                         // coarse tile (reconstruction)
+    float* Wt = reinterpret_cast<float*>(sm4 + CE * CE);      // new inverse depth of the tile
+    float* Pl = Wt + T * T;                                   // flow planes x, y, z of the region
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kSmoothThreads / 32;
+    const int sx0 = wk.z - 2 * S, sy0 = wk.y - 2 * S;         // region origin in the level
+    const int wx0 = max(0, -sx0), wx1 = min(SX, J.W - sx0);   // in-image window of the region
+    const int wy0 = max(0, -sy0), wy1 = min(SX, J.H - sy0);
+
+    // Y-hat of this thread's output pixels (independent of the smoothing)
+    float yv[kSmoothOut];
+#pragma unroll
+    for (int k = 0; k < kSmoothOut; ++k) {
+        const int i = wk.y + warp + NW * k, j = wk.z + lane;
+        yv[k] = (i < J.H && j < J.W) ? __ldg(J.y_in + (size_t)i * J.W + j) : 0.0f;
+    }
+    // coarse tile: rows and columns floor((i - 1) / 2) .. + CE - 1, clamped
+    const float4* __restrict__ coarse = J.s0c[q];
+    const int ci0 = (wk.y - 1) >> 1, cj0 = (wk.z - 1) >> 1;
+    if (!J.top && coarse) {
+        for (int idx = tid; idx < CE * CE; idx += kSmoothThreads) {
+            const int cy = idx / CE, cx = idx - cy * CE;
+            Cc[idx] = coarse[clampi(ci0 + cy, 0, J.Hc - 1) * J.Wc + clampi(cj0 + cx, 0, J.Wc - 1)];
+        }
+    }
+    // the region: two rows per warp in flight, up to three 32-column slots
+    for (int r0 = wy0 + warp; r0 < wy1; r0 += 2 * NW) {
+        float4 v[2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r = r0 + u * NW;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int c = wx0 + lane + 32 * m;
+                if (r < wy1 && c < wx1) v[u][m] = J.x_in[(size_t)(sy0 + r) * J.W + (sx0 + c)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r = r0 + u * NW;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int c = wx0 + lane + 32 * m;
+                if (r < wy1 && c < wx1) {
+                    const int o = r * SP + c;
+                    Pl[o] = v[u][m].x;
+                    Pl[PL + o] = v[u][m].y;
+                    Pl[2 * PL + o] = v[u][m].z;
+                    const int ty = r - 2 * S, tx = c - 2 * S;
+                    if (ty >= 0 && ty < T && tx >= 0 && tx < T) Wt[ty * T + tx] = v[u][m].w;
+                }
             }
         }
     }
     __syncthreads();
-    // 4. S passes of the 5x5 mean with replicated border (Sec. 4.5), separable,
-    //    over a window that shrinks by 2 pixels per pass away from the image edge
-    int wx0 = max(0, -sx0), wx1 = min(SX, g.W - sx0);
-    int wy0 = max(0, -sy0), wy1 = min(SY, g.H - sy0);
-    const int ix0 = wx0, ix1 = wx1 - 1, iy0 = wy0, iy1 = wy1 - 1;   // image extent in region coords
-    const bool el = sx0 + wx0 == 0, er = sx0 + wx1 == g.W, et = sy0 + wy0 == 0, eb = sy0 + wy1 == g.H;
-    for (int s = 0; s < S; ++s) {
-        wx0 += el ? 0 : 2;
-        wx1 -= er ? 0 : 2;
-        // horizontal sums over rows of the current y window
-        {
-            const int ww = wx1 - wx0, n = ww * (wy1 - wy0);
-            const unsigned mw = div_magic(ww);
-            for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-                const int qq = fast_div(idx, mw, ww);
-                const int sy = wy0 + qq, sx = wx0 + (idx - qq * ww);
-                const float4* row = F + sy * SX;
-                float4 acc = row[clampi(sx - 2, ix0, ix1)];
-#pragma unroll
-                for (int d = -1; d <= 2; ++d) {
-                    const float4 v = row[clampi(sx + d, ix0, ix1)];
-                    acc.x += v.x; acc.y += v.y; acc.z += v.z;
-                }
-                T[sy * SX + sx] = acc;
-            }
+    if (S > 0) {
+        // row passes: every in-image row of the region, one (row, channel) per thread
+        const int nrow = wy1 - wy0;
+        for (int t = tid; t < 3 * nrow; t += kSmoothThreads) {
+            const int ch = t / nrow, r = wy0 + (t - ch * nrow);
+            box5_passes(Pl + ch * PL + r * SP, 1, wx0, wx1 - 1, S);
         }
         __syncthreads();
-        wy0 += et ? 0 : 2;
-        wy1 -= eb ? 0 : 2;
-        {
-            const int ww = wx1 - wx0, n = ww * (wy1 - wy0);
-            const unsigned mw = div_magic(ww);
-            for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-                const int qq = fast_div(idx, mw, ww);
-                const int sy = wy0 + qq, sx = wx0 + (idx - qq * ww);
-                float4 acc = T[clampi(sy - 2, iy0, iy1) * SX + sx];
-#pragma unroll
-                for (int d = -1; d <= 2; ++d) {
-                    const float4 v = T[clampi(sy + d, iy0, iy1) * SX + sx];
-                    acc.x += v.x; acc.y += v.y; acc.z += v.z;
-                }
-                F[sy * SX + sx] = make_float4(acc.x * (1.0f / 25.0f), acc.y * (1.0f / 25.0f), acc.z * (1.0f / 25.0f), 0.0f);
-            }
+        // column passes on the tile's columns, one (column, channel) per thread
+        for (int t = tid; t < 3 * T; t += kSmoothThreads) {
+            const int ch = t / T, c = 2 * S + (t - ch * T);
+            if (c < wx1) box5_passes(Pl + ch * PL + c, SP, wy0, wy1 - 1, S);
         }
         __syncthreads();
     }
-    // 5. write the tile
-    {
-        float4* __restrict__ o0 = J.s0_new[parity ^ 1];
-        float4* __restrict__ o1 = J.s1_new[parity ^ 1];
-        for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-            const int ty = fast_div(idx, mTX, TX), tx = idx - ty * TX;
-            const int i = wk.y + ty, j = wk.z + tx;
-            if (i >= g.H || j >= g.W) continue;
-            const int q = (ty + 2 * S) * SX + (tx + 2 * S);
-            const size_t gi = (size_t)i * g.W + j;
-            const float4 sol = F[q];
-            if (J.top) {
-                o0[gi] = make_float4(sol.x, sol.y, sol.z, Ro[idx]);
-                o1[gi] = make_float4(0.0f, 0.0f, 0.0f, Yo[idx]);
-            } else {
-                o0[gi] = make_float4(0.0f, 0.0f, 0.0f, Ro[idx]);
-                o1[gi] = make_float4(sol.x, sol.y, sol.z, Yo[idx]);
+
+    // the tile: new state, reconstruction, outputs
+    bool bad = false;
+    const int n = J.H * J.W;
+    float* const flow_out = J.frame_outputs ? frame_flow : J.flow_out;
+    float* const inv_out = J.frame_outputs ? frame_inv : J.invdepth_out;
+#pragma unroll
+    for (int k = 0; k < kSmoothOut; ++k) {
+        const int ty = warp + NW * k, tx = lane;
+        const int i = wk.y + ty, j = wk.z + tx;
+        if (i >= J.H || j >= J.W) continue;
+        const int o = (ty + 2 * S) * SP + (tx + 2 * S);
+        const float4 x = make_float4(Pl[o], Pl[PL + o], Pl[2 * PL + o], Wt[ty * T + tx]);
+        const size_t gi = (size_t)i * J.W + j;
+        float4 w = make_float4(0.f, 0.f, 0.f, x.w);
+        if (J.top) {
+            w = x;
+            J.s0_new[q][gi] = x;
+            J.s1_new[q][gi] = make_float4(0.f, 0.f, 0.f, yv[k]);
+        } else {
+            if (coarse) {
+                // bilinear x2 at pixel centres (reading R14): coarse coordinate i/2 - 1/4
+                const int i0 = (i - 1) >> 1, j0 = (j - 1) >> 1;
+                const float fy = (i & 1) ? 0.25f : 0.75f, fx = (j & 1) ? 0.25f : 0.75f;
+                const float4* c = Cc + (i0 - ci0) * CE + (j0 - cj0);
+                const float4 c00 = c[0], c01 = c[1], c10 = c[CE], c11 = c[CE + 1];
+                const float wy0_ = 1.0f - fy, wx0_ = 1.0f - fx;
+                w.x = wy0_ * (wx0_ * c00.x + fx * c01.x) + fy * (wx0_ * c10.x + fx * c11.x) + x.x;
+                w.y = wy0_ * (wx0_ * c00.y + fx * c01.y) + fy * (wx0_ * c10.y + fx * c11.y) + x.y;
+                w.z = wy0_ * (wx0_ * c00.z + fx * c01.z) + fy * (wx0_ * c10.z + fx * c11.z) + x.z;
             }
+            J.s0_new[q][gi] = w;
+            J.s1_new[q][gi] = make_float4(x.x, x.y, x.z, yv[k]);
         }
+        if (flow_out) {
+            flow_out[gi] = w.x * inv_dt;
+            flow_out[n + gi] = w.y * inv_dt;
+            flow_out[2 * n + gi] = w.z * inv_dt;
+        }
+        if (inv_out) inv_out[gi] = w.w;
+        if (check_finite && (J.frame_outputs || J.flow_out || J.invdepth_out))
+            bad |= !(isfinite(w.x) && isfinite(w.y) && isfinite(w.z) && isfinite(w.w));
+    }
+    if (check_finite && status) {
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
     }
 }
 
@@ -707,61 +829,6 @@ __global__ void __launch_bounds__(kThreads) k_reconstruct(ReconArgs a)
     }
     if (a.check_finite && a.status) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
-    }
-}
-
-// Reconstruction and outputs of many (stream, level) jobs in one launch: a CTA
-// handles one chunk of one job's pixels.
-struct ReconJob {
-    int H, W, Hc, Wc;          // level and coarser level (Hc = 0: top level, outputs only)
-    float4* s0[2];             // new state, by the parity of the frame just written
-    const float4* s1[2];
-    const float4* s0c[2];
-    float* flow_out;           // level 1 only (may be null)
-    float* invdepth_out;
-};
-
-constexpr int kReconChunk = 4096;
-
-__global__ void __launch_bounds__(kThreads) k_reconstruct_jobs(const ReconJob* __restrict__ jobs,
-                                                              const int2* __restrict__ work, int q, float inv_dt,
-                                                              int check_finite, int* status)
-{
-    const int2 wk = work[blockIdx.x];
-    const ReconJob& J = jobs[wk.x];
-    ReconArgs a;
-    a.H = J.H; a.W = J.W; a.Hc = J.Hc; a.Wc = J.Wc;
-    a.s0 = J.s0[q]; a.s1 = J.s1[q]; a.s0c = J.Hc ? J.s0c[q] : nullptr;
-    a.flow_out = J.flow_out; a.invdepth_out = J.invdepth_out;
-    const int n = J.H * J.W, p0 = wk.y, p1 = min(n, wk.y + kReconChunk);
-    bool bad = false;
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int i = p / a.W, j = p - (p / a.W) * a.W;
-        float4 s = a.s0[p];
-        if (a.s0c) {
-            const int i0 = (i - 1) >> 1, j0 = (j - 1) >> 1;
-            const float fy = (i & 1) ? 0.25f : 0.75f, fx = (j & 1) ? 0.25f : 0.75f;
-            const int ia = clampi(i0, 0, a.Hc - 1), ib = clampi(i0 + 1, 0, a.Hc - 1);
-            const int ja = clampi(j0, 0, a.Wc - 1), jb = clampi(j0 + 1, 0, a.Wc - 1);
-            const float4 c00 = a.s0c[ia * a.Wc + ja], c01 = a.s0c[ia * a.Wc + jb];
-            const float4 c10 = a.s0c[ib * a.Wc + ja], c11 = a.s0c[ib * a.Wc + jb];
-            const float4 d = a.s1[p];
-            const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
-            s.x = wy0 * (wx0 * c00.x + fx * c01.x) + fy * (wx0 * c10.x + fx * c11.x) + d.x;
-            s.y = wy0 * (wx0 * c00.y + fx * c01.y) + fy * (wx0 * c10.y + fx * c11.y) + d.y;
-            s.z = wy0 * (wx0 * c00.z + fx * c01.z) + fy * (wx0 * c10.z + fx * c11.z) + d.z;
-            a.s0[p] = s;
-        }
-        if (a.flow_out) {
-            a.flow_out[p] = s.x * inv_dt;
-            a.flow_out[n + p] = s.y * inv_dt;
-            a.flow_out[2 * n + p] = s.z * inv_dt;
-        }
-        if (a.invdepth_out) a.invdepth_out[p] = s.w;
-        if (check_finite && a.flow_out) bad |= !(isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.w));
-    }
-    if (check_finite && status) {
-        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
     }
 }
 

@@ -66,7 +66,7 @@ def test_batch_matches_single_stream_filters_and_oracle():
         rf, ri = ref.step(seqs[2].image[k], seqs[2].range[k], dt)
         e = np.abs(batch.slots[2][2].cpu().numpy().astype(np.float64) - rf) * dt / dmu_ref[None]
         assert e.max() <= gu.FLOW_TOL_PX
-    # N = 10 on stream 3 needs two propagation launches; three levels need a
-    # two-step reconstruction cascade; one update launch
-    assert batch.launches_per_step() == 2 + 1 + 2
+    # N = 10 on stream 3 needs two propagation launches, then one solve launch
+    # and a smoothing + reconstruction cascade of three levels
+    assert batch.launches_per_step() == 2 + 1 + 3
     assert batch.status() in (sf.OK, sf.WARN_CFL)
