@@ -381,34 +381,59 @@ class _Waves2D:
         return np.clip(0.5 + 0.4 * out, 0.0, 1.0)
 
 
-def plane_stream(frames, seed, H, W, depth, v, rate, levels, iters, smooth):
+def plane_stream(frames, seed, H, W, depth, v, rate, levels, iters, smooth, period=None):
     """A fronto-parallel textured plane under camera translation (config-1
-    style) with a sinusoidal texture that renders fast at any size."""
+    style) with a sinusoidal texture.
+
+    Without ``period`` the camera moves at constant velocity v.  With it the
+    camera oscillates, c(t) = v T / (2 pi) sin(2 pi t / T) with T = period
+    frames, so its velocity is v cos(2 pi t / T), never faster than v, and
+    frame k + period equals frame k: the sequence cycles without a jump.
+
+    The plane's world point seen by pixel (i, j) is separable in the pixel
+    coordinates, so each sinusoid of the texture is rendered as
+    sin(a_j + b_i) = sin a_j cos b_i + cos a_j sin b_i from per-column and
+    per-row values (one [H, 16] x [16, W] product per frame)."""
     rng = np.random.default_rng(seed)
     f = W / 2.0
     dt = 1.0 / rate
     px_m = depth / f
     tex = _Waves2D(rng, 8, (2 * np.pi / (40 * px_m), 2 * np.pi / (6 * px_m)))
-    eta = camera_rays(H, W, f, f, W / 2.0, H / 2.0)
+    xj = (np.arange(W) + 0.5 - W / 2.0) / f          # ray direction (x_j, y_i, 1) of pixel (i, j)
+    yi = (np.arange(H) + 0.5 - H / 2.0) / f
+    norm = np.sqrt(1.0 + xj[None, :] ** 2 + yi[:, None] ** 2)
     vv = np.asarray(v, dtype=np.float64)
-    imgs, rngs = [], []
+    imgs, rngs, vel = [], [], []
     for k in range(frames):
-        c = vv * (k * dt)
-        lam = (depth - c[2]) / eta[..., 2]
-        X = c[None, None, :2] + lam[..., None] * eta[..., :2]
-        imgs.append(tex(X)); rngs.append(lam)
+        if period:
+            ph = 2.0 * np.pi * k / period
+            c = vv * (period * dt / (2.0 * np.pi)) * np.sin(ph)
+            vel.append(vv * np.cos(ph))
+        else:
+            c = vv * (k * dt)
+            vel.append(vv)
+        z = depth - c[2]                             # distance to the plane along the optical axis
+        X = c[0] + z * xj                            # world x of the point seen by column j
+        Y = c[1] + z * yi                            # world y of the point seen by row i
+        aj = tex.k[:, 0:1] * X[None, :] + tex.ph[:, None]                  # [waves, W]
+        bi = tex.k[:, 1:2] * Y[None, :]                                     # [waves, H]
+        rows = np.concatenate([np.cos(bi), np.sin(bi)]).T                   # [H, 2 waves]
+        cols = np.concatenate([tex.a[:, None] * np.sin(aj), tex.a[:, None] * np.cos(aj)])
+        imgs.append(np.clip(0.5 + 0.4 * (rows @ cols), 0.0, 1.0)); rngs.append(z * norm)
     return Sequence("plane_stream", np.array(imgs, np.float32), np.array(rngs, np.float32), dt, f, f, W / 2.0,
-                    H / 2.0, levels, list(iters), list(smooth), np.tile(vv, (frames, 1)), np.zeros((frames, 3)),
-                    meta=dict(depth=depth))
+                    H / 2.0, levels, list(iters), list(smooth), np.array(vel), np.zeros((frames, 3)),
+                    meta=dict(depth=depth, period=period))
 
 
-def batch(frames=2, seed=1003, sizes=((256, 16), (512, 32), (1024, 16)), max_flow=4.0, rate=600.0):
+def batch(frames=2, seed=1003, sizes=((256, 16), (512, 32), (1024, 16)), max_flow=4.0, rate=600.0, period=None):
     """Independent config-1-style streams of mixed sizes (list of Sequences).
 
     Each stream is a textured plane with its own depth and camera velocity,
-    chosen so the flow at level 1 reaches about ``max_flow`` px/frame; 256x256
+    chosen so the largest per-axis flow at level 1 is just below ``max_flow``
+    px/frame (so N_1 = max_flow sub-iterations satisfy the CFL bound); 256x256
     streams use two pyramid levels, larger ones three, with
-    N_h = ceil(max_flow / 2^(h-1)) and smoothing [2, 4, 4].
+    N_h = ceil(max_flow / 2^(h-1)) and smoothing [2, 4, 4].  ``period``: the
+    cameras oscillate with that many frames per cycle (see plane_stream).
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -421,10 +446,13 @@ def batch(frames=2, seed=1003, sizes=((256, 16), (512, 32), (1024, 16)), max_flo
             direction = rng.normal(size=3)
             direction[2] = abs(direction[2])
             direction /= np.linalg.norm(direction)
-            # lateral image flow ~ f |v_xy| / depth / rate (px/frame), f = size / 2
-            vmag = 0.8 * max_flow * depth * rate / (size / 2.0) / max(np.linalg.norm(direction[:2]), 0.3)
+            # image flow of a fronto-parallel plane, per axis: (x v_z - f v_xy) / depth / rate
+            # (px/frame, f = size / 2, |x| <= f), at most f (|v_xy| + sqrt(2) v_z) / depth / rate
+            # over the image: the largest per-axis flow stays below max_flow (CFL-safe at N_1)
+            vmag = 0.95 * max_flow * depth * rate / (size / 2.0) / (np.linalg.norm(direction[:2]) +
+                                                                     np.sqrt(2.0) * direction[2])
             out.append(plane_stream(frames, int(rng.integers(1 << 30)), size, size, depth, direction * vmag, rate,
-                                    levels, iters, smooth))
+                                    levels, iters, smooth, period))
     return out
 
 
