@@ -287,8 +287,10 @@ def run_ours(args):
     ranges = torch.from_numpy(seq.range).to(dev)
     flow = torch.empty((3, H, W), device=dev)
     inv = torch.empty((H, W), device=dev)
-    params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth)
+    params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
+                       flags=sf.CHECK_CFL | sf.AUTOTUNE)
     filt = sf.Filter(H, W, seq.levels, params)
+    nf_max = filt.nf_max()       # the autotuner's choice of sub-iterations per propagation launch
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -348,7 +350,7 @@ def run_ours(args):
                   for n, (ms, c) in zip(names, slots)}
         prop_ms = slots[0][0] / max(slots[0][1], 1)
         bpl = propagate_bytes_per_launch(H, W, seq.levels)
-        prop_flops = propagate_flops_per_launch(H, W, seq.levels, seq.iters)
+        prop_flops = propagate_flops_per_launch(H, W, seq.levels, seq.iters, nf_max)
         achieved = bpl / (prop_ms / 1e3) / 1e9
         frame_bytes = algorithmic_bytes_per_frame(H, W, seq.levels)
         if args.quick:
@@ -368,7 +370,8 @@ def run_ours(args):
             "config": {"workload": "scene512: 512x512, 2 levels, N=[8,4], smooth=[2,4], 600 Hz, max flow 8 px/frame"
                        + ("" if args.size == 512 else f", tiled to {args.size}x{args.size} (profiling case)"),
                        "global_batch": ws, "streams_per_gpu": 1, "parallelism": f"replicas x{ws}",
-                       "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)"},
+                       "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)",
+                       "nf_max": nf_max, "autotune": True},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
@@ -412,7 +415,8 @@ def measure_batch(steps, warmup, dev):
     from paper_2406_18031_b300 import scenes, sf
     seqs = scenes.batch(frames=BATCH_FRAMES, sizes=BATCH_SIZES, period=BATCH_FRAMES)
     dt = seqs[0].dt
-    params = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
+    params = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth,
+                        flags=sf.CHECK_CFL | sf.AUTOTUNE) for q in seqs]
     batch = sf.Batch([q.shape for q in seqs], [q.levels for q in seqs], params)
     frames = [[(torch.from_numpy(q.image[f]).to(dev), torch.from_numpy(q.range[f]).to(dev))
                for f in range(BATCH_FRAMES)] for q in seqs]
@@ -459,7 +463,7 @@ def measure_batch(steps, warmup, dev):
         "workload": "64 streams: 16x256^2 (2 levels), 32x512^2 and 16x1024^2 (3 levels), peak flow < 4 px/frame, "
                     "cameras oscillating with a 16-frame period, "
                     "N=[4,2(,1)], smooth=[2,4(,4)], plane scenes, 600 Hz",
-        "streams": len(seqs), "mpx_per_step": px / 1e6,
+        "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(), "autotune": True,
         "frames_per_s_per_stream": 1.0 / step_s, "ms_per_step": step_s * 1e3,
         "stream_frames_per_s": len(seqs) / step_s, "mpx_per_s": px / step_s / 1e6,
         "hbm_gbs_algorithmic": frame_bytes / step_s / 1e9,

@@ -58,6 +58,10 @@ extern "C" {
                                  Eq. 53) instead of dt in both printed passes */
 #define SF_CHECK_CFL 4        /* record SF_WARN_CFL when Eq. 67 is violated   */
 #define SF_CHECK_FINITE 8     /* record SF_ENONFINITE for NaN/Inf output flow */
+#define SF_AUTOTUNE 16        /* at creation, time the propagation launches of one
+                                 frame for each nf_max in {8, 6, 4, 3, 2} that
+                                 splits the N_h differently and keep the fastest
+                                 (overrides sf_params.nf_max; see sf_nf_max)   */
 
 typedef struct sf_params {
     float fx, fy, cx, cy;          /* level-1 pinhole intrinsics, pixels              */
@@ -69,6 +73,12 @@ typedef struct sf_params {
                                       prior weight of level h is gamma[2] * (2^(h-1)/fx)^2 */
     float lambda_ref;              /* reference range of Eq. 8, metres (1.0)          */
     int flags;                     /* SF_* flags above                                */
+    int nf_max;                    /* sub-iterations fused in one propagation launch,
+                                      1..8; 0 selects 8.  Level h then runs
+                                      ceil(N_h / nf_max) launches of about equal
+                                      length (a launch of nf sub-iterations
+                                      recomputes an nf-pixel halo around each
+                                      (64 - 2 nf)^2 output tile)                   */
 } sf_params;
 
 typedef struct sf_ctx sf_ctx;      /* opaque; owns all device state of one stream     */
@@ -126,9 +136,15 @@ int sf_get_state(sf_ctx* c, int level, float* dst, float* dt_prev, void* stream)
 int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* stream);
 
 /* Number of kernel launches one sf_step enqueues after the first frame (the
- * propagation launches, the update launch and the reconstruction
- * launches); a negative code for a NULL context. */
+ * propagation launches, the solve launch and one smoothing/reconstruction
+ * launch per pyramid level); a negative code for a NULL context. */
 int sf_kernels_per_step(const sf_ctx* c);
+
+/* The nf_max the context runs with (sf_params.nf_max, or the autotuner's
+ * choice under SF_AUTOTUNE); a negative code for a NULL context.  The paper
+ * has no such setting: it is how the N sub-iterations of Sec. 4.6 are cut
+ * into launches. */
+int sf_nf_max(const sf_ctx* c);
 
 /* Per-launch device timing.  sf_profile(c, 1) makes every following sf_step
  * record a CUDA event pair around each of its kernel launches, on the
@@ -160,7 +176,8 @@ typedef struct sf_batch sf_batch;
 
 /* Create n streams: stream s is H[s] x W[s] with levels[s] levels and the
  * parameters params[s] (validated as in sf_create; all streams must use the
- * same SF_DOMINANT_LITERAL / SF_SOURCE_SPLIT choice).  The batch owns one
+ * same SF_DOMINANT_LITERAL / SF_SOURCE_SPLIT choice; nf_max and SF_AUTOTUNE
+ * are taken from params[0]).  The batch owns one
  * device input slot (image, range) and one output slot (flow 3 x H x W,
  * inverse depth) per stream, zero-filled; see sf_batch_buffers. */
 int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params,
@@ -181,6 +198,10 @@ int sf_batch_status(sf_batch* b);
 
 /* Kernel launches of one steady-state sf_batch_step. */
 int sf_batch_launches_per_step(const sf_batch* b);
+
+/* As sf_nf_max, for the whole batch (every stream uses params[0].nf_max and
+ * params[0].flags' SF_AUTOTUNE). */
+int sf_batch_nf_max(const sf_batch* b);
 
 /* As sf_profile / sf_profile_read for a batch; while profiling, steps run as
  * plain launches (no graph replay) so each launch can be timed. */

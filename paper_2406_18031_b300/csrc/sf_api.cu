@@ -28,8 +28,8 @@ using namespace sfdev;
 namespace {
 
 // the largest number of sub-iterations fused in one propagation launch (its
-// square output tile is 64 - 2 nf pixels wide)
-constexpr int kNfMax = 8;
+// square output tile is 64 - 2 nf pixels wide); an engine may use fewer
+constexpr int kNfLimit = 8;
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
@@ -166,6 +166,7 @@ int check_params(int H, int W, int L, const sf_params* p)
     for (int k = 0; k < 5; ++k)
         if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
     if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
+    if (p->nf_max < 0 || p->nf_max > kNfLimit) return SF_EINVAL;
     for (int h = 0; h < L; ++h) {
         const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
         if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
@@ -258,6 +259,7 @@ struct EngineStream {
 struct Engine {
     std::vector<EngineStream> st;
     int flags = 0;
+    int nf_max = kNfLimit;      // sub-iterations fused per propagation launch (tuned or set)
     int parity = 0;
     int initialised = 0;
     float dt_prev = 0.0f;
@@ -318,24 +320,27 @@ int engine_levels(EngineStream& s, cudaStream_t st)
     return SF_OK;
 }
 
-int engine_plans(Engine& E, cudaStream_t st)
+int engine_prop_plans(Engine& E, cudaStream_t st)
 {
+    for (auto& pl : E.prop) free_plan(pl);
+    E.prop.clear();
+    const int nfmax = E.nf_max;
     // ---- propagation: level h of stream s runs ceil(N / nfmax) launches;
     // launch k holds segment k of every (stream, level) that has one.  The last
     // segment writes the prediction planes, earlier ones alternate with t0/t1.
     int maxseg = 0;
     for (auto& s : E.st)
-        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, kNfMax));
+        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, nfmax));
     E.prop.resize(maxseg);
     for (int k = 0; k < maxseg; ++k) {
         std::vector<PropJob> jobs;
         std::vector<int4> work;
         bool c8 = false;
-        for (int want = kNfMax; want >= 1; --want) {   // longest tiles (most passes) first
+        for (int want = nfmax; want >= 1; --want) {   // longest tiles (most passes) first
             for (auto& s : E.st) {
                 for (int h = 0; h < s.L; ++h) {
                     sf_level_state& lv = s.lv[h];
-                    const int nseg = ceil_div(lv.N, kNfMax);
+                    const int nseg = ceil_div(lv.N, nfmax);
                     if (k >= nseg) continue;
                     const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
                     if (nf != want) continue;
@@ -374,6 +379,11 @@ int engine_plans(Engine& E, cudaStream_t st)
         int r = upload_plan(jobs, work, E.prop[k], st);
         if (r) return r;
     }
+    return SF_OK;
+}
+
+int engine_update_plans(Engine& E, cudaStream_t st)
+{
     // ---- solve: every level of every stream, one 32 x 32 tile per CTA
     {
         std::vector<SolveJob> jobs;
@@ -450,6 +460,48 @@ int engine_plans(Engine& E, cudaStream_t st)
     return SF_OK;
 }
 
+// The autotuner: time one frame's propagation launches for every nf_max in
+// {8, 6, 4, 3, 2} that splits the levels' N_h into a different set of launches
+// (12 frames after 2 warm-up frames, CUDA events on the engine's stream) and
+// keep the fastest.  It runs on the engine's zero state: the kernel has no
+// data-dependent branches, so the timing is that of any state, and the
+// propagation of zeros writes zeros, so the engine is left as created.
+int engine_tune(Engine& E, cudaStream_t st)
+{
+    const int cand[] = {8, 6, 4, 3, 2};
+    std::vector<std::vector<int>> seen;
+    int best = E.nf_max, r = SF_OK;
+    float best_ms = -1.0f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = SF_ECUDA;
+    const int flags = E.flags & ~(SF_CHECK_CFL | SF_CHECK_FINITE);
+    for (int nf : cand) {
+        if (r) break;
+        std::vector<int> sig;
+        for (auto& s : E.st)
+            for (int h = 0; h < s.L; ++h) sig.push_back(ceil_div(s.lv[h].N, nf));
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
+        E.nf_max = nf;
+        r = engine_prop_plans(E, st);
+        for (int it = 0; it < 14 && !r; ++it) {
+            if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
+            for (auto& pl : E.prop)
+                if (!r) r = launch_propagate(pl, 0, 1.0f, flags, nullptr, st);
+        }
+        if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
+        if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
+        float ms = 0.0f;
+        if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
+        if (!r && (best_ms < 0.0f || ms < best_ms)) { best_ms = ms; best = nf; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (r) return r;
+    E.nf_max = best;
+    return engine_prop_plans(E, st);
+}
+
 // create the streams' levels, the status word and the plans
 int engine_init(Engine& E)
 {
@@ -462,7 +514,9 @@ int engine_init(Engine& E)
     }
     if (!r && cudaMalloc(&E.status, sizeof(int)) != cudaSuccess) { E.status = nullptr; r = SF_ENOMEM; }
     if (!r) r = cudaMemsetAsync(E.status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
-    if (!r) r = engine_plans(E, st);
+    if (!r) r = engine_prop_plans(E, st);
+    if (!r) r = engine_update_plans(E, st);
+    if (!r && (E.flags & SF_AUTOTUNE)) r = engine_tune(E, st);
     if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
     cudaStreamDestroy(st);
     return r;
@@ -595,6 +649,7 @@ int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
     std::memset(&s, 0, sizeof(s));
     s.H = H; s.W = W; s.L = levels; s.p = *p;
     c->E.flags = p->flags;
+    c->E.nf_max = p->nf_max ? p->nf_max : kNfLimit;
     r = engine_init(c->E);
     if (r) { destroy_ctx(c); return r; }
     *out = c;
@@ -700,6 +755,12 @@ int sf_kernels_per_step(const sf_ctx* c)
     return c->E.launches_per_step();
 }
 
+int sf_nf_max(const sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    return c->E.nf_max;
+}
+
 void sf_destroy(sf_ctx* c) { destroy_ctx(c); }
 
 const char* sf_strerror(int code)
@@ -736,6 +797,7 @@ int sf_batch_create(int n, const int* H, const int* W, const int* levels, const 
     Engine& E = b->E;
     E.st.resize(n);
     E.flags = params[0].flags;
+    E.nf_max = params[0].nf_max ? params[0].nf_max : kNfLimit;
     size_t io_floats = 0;
     for (int s = 0; s < n; ++s) io_floats += 6 * (size_t)H[s] * W[s];   // image, range, flow (3), inverse depth
     int r = SF_OK;
@@ -820,6 +882,12 @@ int sf_batch_launches_per_step(const sf_batch* b)
     return b->E.launches_per_step();
 }
 
+int sf_batch_nf_max(const sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    return b->E.nf_max;
+}
+
 int sf_batch_profile(sf_batch* b, int enable)
 {
     if (!b) return SF_EINVAL;
@@ -849,7 +917,7 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
     if (!aligned16(s0_in) || !aligned16(s0_out) || !aligned16(s1_in) || !aligned16(s1_out)) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool c8 = s1_in != nullptr;
-    const int nseg = ceil_div(N, kNfMax);
+    const int nseg = ceil_div(N, kNfLimit);
     const size_t n = (size_t)g->H * g->W;
     float4* scratch = nullptr;
     if (nseg > 1) {
@@ -1067,7 +1135,7 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
     if (!aligned16(s0_in) || !aligned16(s0_out) || !aligned16(s1_in) || !aligned16(s1_out)) return SF_EINVAL;
     const size_t n = (size_t)g->H * g->W;
     if (n > kNoAllocMaxPixels) return SF_EINVAL;                 // larger frames: use sf_propagate
-    const int nseg = ceil_div(N, kNfMax);
+    const int nseg = ceil_div(N, kNfLimit);
     for (int k = 0; k < nseg; ++k) {                             // every tile list must fit
         const int T = prop_tile(N / nseg + (k < N % nseg ? 1 : 0));
         const size_t tiles = (size_t)ceil_div(g->H, T) * ceil_div(g->W, T);

@@ -18,7 +18,7 @@ LIB_PATH = _PKG / "libsf.so"
 
 MAX_LEVELS = 4
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, WARN_CFL = 0, -1, -2, -3, -4, -5, 1
-DOMINANT_LITERAL, SOURCE_SPLIT, CHECK_CFL, CHECK_FINITE = 1, 2, 4, 8
+DOMINANT_LITERAL, SOURCE_SPLIT, CHECK_CFL, CHECK_FINITE, AUTOTUNE = 1, 2, 4, 8, 16
 
 
 class SFError(RuntimeError):
@@ -31,7 +31,7 @@ class CParams(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("iters", ctypes.c_int * MAX_LEVELS), ("max_flow", ctypes.c_float),
                 ("smooth_iters", ctypes.c_int * MAX_LEVELS), ("gamma", ctypes.c_float * 5),
-                ("lambda_ref", ctypes.c_float), ("flags", ctypes.c_int)]
+                ("lambda_ref", ctypes.c_float), ("flags", ctypes.c_int), ("nf_max", ctypes.c_int)]
 
 
 class CGrid(ctypes.Structure):
@@ -42,9 +42,10 @@ class CGrid(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
-           "sf_set_state", "sf_kernels_per_step", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
+           "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
-           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_profile", "sf_batch_profile_read",
+           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_profile",
+           "sf_batch_profile_read",
            "sf_batch_destroy"]
 
 
@@ -66,6 +67,7 @@ def lib():
         L.sf_get_state.argtypes = [vp, i, vp, P(f), vp]
         L.sf_set_state.argtypes = [vp, i, vp, f, vp]
         L.sf_kernels_per_step.argtypes = [vp]
+        L.sf_nf_max.argtypes = [vp]
         L.sf_profile.argtypes = [vp, i]
         L.sf_profile_read.argtypes = [vp, P(f), P(i), i]
         L.sf_destroy.argtypes = [vp]
@@ -78,6 +80,7 @@ def lib():
         L.sf_batch_step.argtypes = [vp, f, vp]
         L.sf_batch_status.argtypes = [vp]
         L.sf_batch_launches_per_step.argtypes = [vp]
+        L.sf_batch_nf_max.argtypes = [vp]
         L.sf_batch_profile.argtypes = [vp, i]
         L.sf_batch_profile_read.argtypes = [vp, P(f), P(i), i]
         L.sf_batch_destroy.argtypes = [vp]
@@ -129,11 +132,12 @@ class Params:
     gamma: tuple | None = None
     lambda_ref: float | None = None
     flags: int | None = None
+    nf_max: int | None = None
 
     def to_c(self, H, W, levels) -> CParams:
         c = CParams()
         _check(lib().sf_params_default(ctypes.byref(c), H, W, levels), "sf_params_default")
-        for name in ("fx", "fy", "cx", "cy", "max_flow", "lambda_ref", "flags"):
+        for name in ("fx", "fy", "cx", "cy", "max_flow", "lambda_ref", "flags", "nf_max"):
             v = getattr(self, name)
             if v is not None:
                 setattr(c, name, v)
@@ -187,6 +191,10 @@ class Filter:
 
     def kernels_per_step(self) -> int:
         return _check(lib().sf_kernels_per_step(self._h), "sf_kernels_per_step")
+
+    def nf_max(self) -> int:
+        """Sub-iterations fused per propagation launch (set, or chosen by AUTOTUNE)."""
+        return _check(lib().sf_nf_max(self._h), "sf_nf_max")
 
     def profile(self, enable: bool):
         _check(lib().sf_profile(self._h, int(bool(enable))), "sf_profile")
@@ -294,6 +302,9 @@ class Batch:
 
     def launches_per_step(self):
         return _check(lib().sf_batch_launches_per_step(self._h), "sf_batch_launches_per_step")
+
+    def nf_max(self) -> int:
+        return _check(lib().sf_batch_nf_max(self._h), "sf_batch_nf_max")
 
     def profile(self, enable: bool):
         _check(lib().sf_batch_profile(self._h, int(bool(enable))), "sf_batch_profile")

@@ -2,6 +2,7 @@
 declares; host-side validation works without a GPU (no compute calls)."""
 import ctypes
 import re
+import subprocess
 from pathlib import Path
 
 import pytest
@@ -37,10 +38,21 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(sf.EXPORTS) <= set(declared_functions())
 
 
-def test_struct_layout_matches_header(lib):
-    # sf_params: 4 floats, 4 ints, float, 4 ints, 5 floats, float, int
-    assert ctypes.sizeof(sf.CParams) == 4 * (4 + 4 + 1 + 4 + 5 + 1 + 1)
+def test_struct_layout_matches_header(lib, tmp_path):
+    # sf_params: 4 floats, 4 ints, float, 4 ints, 5 floats, float, int, int
+    assert ctypes.sizeof(sf.CParams) == 4 * (4 + 4 + 1 + 4 + 5 + 1 + 1 + 1)
     assert ctypes.sizeof(sf.CGrid) == 24
+    # the C compiler's view of the header: sizes and every field's offset
+    fields = [f for f, _ in sf.CParams._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "sf.h"\nint main(void) {\n'
+                   '  printf("%zu %zu\\n", sizeof(sf_params), sizeof(sf_grid));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(sf_params, {f}));\n' for f in fields) + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(sf.CParams) and int(out[1]) == ctypes.sizeof(sf.CGrid)
+    assert [int(x) for x in out[2:]] == [getattr(sf.CParams, f).offset for f in fields]
 
 
 def test_params_default(lib):
@@ -64,7 +76,8 @@ def test_create_rejects_bad_shapes_without_touching_the_device(lib, H, W, L):
 
 
 @pytest.mark.parametrize("field,value", [("fx", 0.0), ("lambda_ref", -1.0), ("gamma2", 0.0), ("gamma0", -1.0),
-                                         ("gamma4", 0.0), ("iters0", 5000), ("smooth0", 17)])
+                                         ("gamma4", 0.0), ("iters0", 5000), ("smooth0", 17), ("nf_max", 9),
+                                         ("nf_max", -1)])
 def test_create_rejects_bad_parameters(lib, field, value):
     p = sf.CParams()
     lib.sf_params_default(ctypes.byref(p), 64, 64, 1)

@@ -28,16 +28,17 @@ def _streams():
     ]
 
 
-def _params(seq):
+def _params(seq, nf_max=None):
     return sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
-                     flags=sf.CHECK_CFL | sf.CHECK_FINITE)
+                     flags=sf.CHECK_CFL | sf.CHECK_FINITE, nf_max=nf_max)
 
 
-def test_batch_matches_single_stream_filters_and_oracle():
+@pytest.mark.parametrize("nf_max", [None, 4])
+def test_batch_matches_single_stream_filters_and_oracle(nf_max):
     seqs = _streams()
     dt = seqs[0].dt
     assert all(abs(s.dt - dt) < 1e-15 for s in seqs)
-    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs], [_params(s) for s in seqs])
+    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs], [_params(s, nf_max) for s in seqs])
     singles = [sf.Filter(*s.shape, s.levels, _params(s)) for s in seqs]
     ref = oracle.Filter(*seqs[2].shape, seqs[2].levels,
                         oracle.Params(seqs[2].fx, seqs[2].fy, seqs[2].cx, seqs[2].cy, iters=seqs[2].iters,
@@ -66,7 +67,8 @@ def test_batch_matches_single_stream_filters_and_oracle():
         rf, ri = ref.step(seqs[2].image[k], seqs[2].range[k], dt)
         e = np.abs(batch.slots[2][2].cpu().numpy().astype(np.float64) - rf) * dt / dmu_ref[None]
         assert e.max() <= gu.FLOW_TOL_PX
-    # N = 10 on stream 3 needs two propagation launches, then one solve launch
-    # and a smoothing + reconstruction cascade of three levels
-    assert batch.launches_per_step() == 2 + 1 + 3
+    # N = 10 on stream 3 needs two propagation launches (three at nf_max = 4),
+    # then one solve launch and a smoothing + reconstruction cascade of three levels
+    assert batch.launches_per_step() == (2 if nf_max is None else 3) + 1 + 3
+    assert batch.nf_max() == (nf_max or 8)
     assert batch.status() in (sf.OK, sf.WARN_CFL)

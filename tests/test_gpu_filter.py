@@ -19,20 +19,23 @@ def _cuda():
     oracle.set_threads(8)
 
 
-def _pair(seq, gamma=None, flags=0):
+def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None):
     H, W = seq.shape
     kw = dict(iters=seq.iters, smooth=seq.smooth)
     if gamma is not None:
         kw["gamma"] = gamma
-    g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy,
-                                               flags=flags | sf.CHECK_CFL | sf.CHECK_FINITE, **kw))
+    g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, nf_max=nf_max,
+                                               flags=flags | gpu_flags | sf.CHECK_CFL | sf.CHECK_FINITE, **kw))
     r = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, flags=flags, **kw))
     return g, r
 
 
-def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX):
+def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX, gpu_flags=0, nf_max=None,
+         filt=None):
     """Run both filters; returns per-frame (max px error, max rho error) and the final outputs."""
-    g, r = _pair(seq, flags=flags)
+    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max)
+    if filt is not None:
+        filt.append(g)
     H, W = seq.shape
     _, _, dmu = r.geometry(0)
     flow = torch.empty((3, H, W), device="cuda")
@@ -67,6 +70,27 @@ def test_two_level_scene_per_frame(flags):
     assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
     assert max(e for _, e in errs) <= gu.RHO_TOL
     assert st >= 0
+
+
+@pytest.mark.parametrize("nf_max", [8, 5, 3, 1])
+def test_propagation_split_into_launches(nf_max):
+    # N = [10, 5]: level 1 runs ceil(10 / nf_max) launches, level 2 ceil(5 / nf_max)
+    seq = scenes.scene512(frames=5, H=96, W=128, max_flow=5.0, levels=2, iters=(10, 5), smooth=(2, 4))
+    filt = []
+    errs, _, _, st = _run(seq, 5, nf_max=nf_max, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert filt[0].nf_max() == nf_max
+    assert filt[0].kernels_per_step() == -(-10 // nf_max) + 1 + 2
+
+
+def test_autotune_keeps_a_candidate_and_the_results():
+    seq = scenes.scene512(frames=4, H=128, W=128, max_flow=6.0, levels=2, iters=(6, 3), smooth=(2, 4))
+    filt = []
+    errs, _, _, st = _run(seq, 4, gpu_flags=sf.AUTOTUNE, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert filt[0].nf_max() in (8, 6, 4, 3, 2)
+    assert st == sf.OK
 
 
 def test_three_level_driving_scene_with_sky():
