@@ -30,6 +30,7 @@ _LIB = _HERE / "libsf_oracle.so"
 
 DOMINANT_LITERAL = 1
 SOURCE_SPLIT = 2
+IMU = 32
 
 _lib = None
 
@@ -60,7 +61,9 @@ def lib():
         L.sfo_geometry.argtypes = [i, i, d, d, d, d, _D, _D, _D]
         L.sfo_image_model.argtypes = [i, i, _D, _D, _D, _D, _D, _D]
         L.sfo_invdepth_model.argtypes = [i, i, _D, _U8, _D, _D, _D, _D]
-        L.sfo_propagate.argtypes = [i, i, i, i, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.sfo_propagate.argtypes = [i, i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.sfo_imu_step.argtypes = [i, i, d, _D, _D, _D, _D, _D]
+        L.sfo_set_motion.argtypes = [vp, _D, _D]
         L.sfo_propagate.restype = d
         L.sfo_update.argtypes = [i, i, d, d, d, _D, _D, _D, _D, _D, _D, _U8, _D, _D, _D, _D]
         L.sfo_blend.argtypes = [i, d, d, _D, _U8, _D, _D]
@@ -135,9 +138,11 @@ def invdepth_model(rho, valid, B, dmu):
     return db, g
 
 
-def propagate(w, rho, eta, B, dmu, N, dw=None, Y=None, flags=0, want_margin=False):
+def propagate(w, rho, eta, B, dmu, N, dw=None, Y=None, flags=0, want_margin=False, imu=None):
     """N sub-iterations of the upwind scheme (Sec. 4.6, Eqs. 53-67).
 
+    ``imu`` = (Omega, a) in frame units (rad/frame, m/frame^2), six numbers:
+    with IMU in ``flags`` each sub-iteration ends with the inertial source step.
     Returns (w, dw, rho, Y, cfl[, margin]) -- copies; inputs are not modified.
     """
     w = _f64(w).copy(); rho = _f64(rho).copy()
@@ -145,8 +150,9 @@ def propagate(w, rho, eta, B, dmu, N, dw=None, Y=None, flags=0, want_margin=Fals
     Y = None if Y is None else _f64(Y).copy()
     H, W = rho.shape
     margin = np.empty((H, W)) if want_margin else None
+    m = None if imu is None else np.ascontiguousarray(np.asarray(imu, dtype=np.float64).reshape(6))
     cfl = lib().sfo_propagate(H, W, int(N), int(flags), _d(_f64(eta)), _d(_f64(B)), _d(_f64(dmu)),
-                              _d(w), _d(dw), _d(rho), _d(Y), _d(margin))
+                              _d(w), _d(dw), _d(rho), _d(Y), _d(margin), _d(m))
     out = (w, dw, rho, Y, cfl)
     return out + (margin,) if want_margin else out
 
@@ -236,6 +242,13 @@ class Filter:
 
     def reset(self):
         lib().sfo_reset(self._c)
+
+    def set_motion(self, omega=None, accel=None):
+        """Camera angular velocity (rad/s) and linear acceleration (m/s^2), camera
+        frame, for the next frames' predictions (used with IMU in the flags)."""
+        om = None if omega is None else np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(3))
+        ac = None if accel is None else np.ascontiguousarray(np.asarray(accel, dtype=np.float64).reshape(3))
+        lib().sfo_set_motion(self._c, _d(om), _d(ac))
 
     def step(self, image, rng, dt):
         """One frame; returns (flow [3,H,W] rad/s, invdepth [H,W])."""

@@ -48,6 +48,20 @@
  *      single source of Eq. 53.  The default keeps the printed passes;
  *      SFO_SOURCE_SPLIT applies half of it in each pass (once per
  *      sub-iteration), which is consistent with Eq. 53.
+ *  R23 the inertial source terms the paper drops by the assumption of Sec.
+ *      4.4 (-Omega x w + a_w of the total-derivative equation of Sec. 3,
+ *      a_w = rho a_c - Omega x (w + Omega x eta), so -2 Omega x w -
+ *      Omega x (Omega x eta) + rho a_c in all) are integrated once per
+ *      sub-iteration, after its two axis passes: one explicit Euler step
+ *      with dt = 1/N evaluated at the state the passes left (SFO_IMU).
+ *  R24 the acceleration enters as -rho a_c: with dv_c/dt = -Omega x v_c + a_c
+ *      (the camera's equation of motion, Sec. 3) the derivative of
+ *      rho (v_p - v_c) carries -rho a_c; the derivation prints +rho a_c.
+ *  R25 lower levels: the transported w_h takes the full source; the
+ *      increment dw takes its linear part -2 Omega x dw only (the coarser
+ *      levels carry -Omega x (Omega x eta) and rho a_c; the remainder
+ *      (rho_h - up rho_{h+1}) a_c is dropped).  Omega and a_c enter in frame
+ *      units, Omega dt (rad/frame) and a_c dt^2 (m/frame^2), like w.
  *  G1  grid: level h is a pinhole grid with intrinsics scaled by 2^(1-h);
  *      rays pass through pixel centres; the neighbour rays that define B
  *      and dmu exist analytically beyond the image edge.
@@ -61,6 +75,7 @@
 
 #define SFO_DOMINANT_LITERAL 1
 #define SFO_SOURCE_SPLIT 2
+#define SFO_IMU 32
 
 /* ------------------------------------------------------------------------ */
 /* small helpers                                                              */
@@ -365,11 +380,47 @@ static double axis_pass(int H, int W, int axis, double dt, int flags,
  * u-hat from w^n, then a row pass driven by v-hat from w* (Sec. 4.6).  The
  * fields are updated in place and hold w^N on return [R3].  Top level: dw and
  * Y are NULL (Eqs. 36-37); lower levels transport w, dw, rho and Y by w
- * (Eqs. 38-41 [R7]).  Returns the CFL number dt * max |speed hat| (Eq. 67).
+ * (Eqs. 38-41 [R7]).  With SFO_IMU in flags and imu non-NULL, each
+ * sub-iteration ends with the inertial source step [R23].  Returns the CFL
+ * number dt * max |speed hat| (Eq. 67).
  */
+static void cross3(const double* a, const double* b, double* o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/*
+ * The inertial source terms of one sub-iteration [R23-R25]: with Omega and a
+ * in frame units (imu = (Omega_x, Omega_y, Omega_z, a_x, a_y, a_z)),
+ *   w  <- w  + dt (-2 Omega x w - Omega x (Omega x eta) - rho a)
+ *   dw <- dw + dt (-2 Omega x dw)                     (lower levels)
+ * at every pixel, from the values the two axis passes left.
+ */
+void sfo_imu_step(int H, int W, double dt, const double* imu, const double* eta,
+                  double* w, double* dw, const double* rho)
+{
+    const double* om = imu;
+    const double* acc = imu + 3;
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < H * W; p++) {
+        double ow[3], oe[3], ooe[3];
+        cross3(om, w + p * 3, ow);
+        cross3(om, eta + p * 3, oe);
+        cross3(om, oe, ooe);
+        double odw[3] = {0.0, 0.0, 0.0};
+        if (dw) cross3(om, dw + p * 3, odw);
+        for (int c = 0; c < 3; c++) {
+            w[p * 3 + c] += dt * (-2.0 * ow[c] - ooe[c] - rho[p] * acc[c]);
+            if (dw) dw[p * 3 + c] += dt * (-2.0 * odw[c]);
+        }
+    }
+}
+
 double sfo_propagate(int H, int W, int N, int flags,
                      const double* eta, const double* B, const double* dmu,
-                     double* w, double* dw, double* rho, double* Y, double* margin)
+                     double* w, double* dw, double* rho, double* Y, double* margin, const double* imu)
 {
     size_t n = (size_t)H * W;
     double* w1 = malloc(n * 3 * sizeof(double));
@@ -383,6 +434,7 @@ double sfo_propagate(int H, int W, int N, int flags,
     for (int it = 0; it < N; it++) {
         double c0 = axis_pass(H, W, 0, dt, flags, eta, B, dmu, w, dw, rho, Y, w1, dw1, r1, y1, speed, margin);
         double c1 = axis_pass(H, W, 1, dt, flags, eta, B, dmu, w1, dw1, r1, y1, w, dw, rho, Y, speed, margin);
+        if (imu && (flags & SFO_IMU)) sfo_imu_step(H, W, dt, imu, eta, w, dw, rho);
         if (c0 > cfl) cfl = c0;
         if (c1 > cfl) cfl = c1;
     }
@@ -536,6 +588,9 @@ typedef struct {
     int iters[SFO_MAX_LEVELS], smooth[SFO_MAX_LEVELS];
     double gamma[5];
     double last_cfl;
+    double omega[3], accel[3];      /* camera angular velocity (rad/s) and    */
+                                    /* linear acceleration (m/s^2) over the   */
+                                    /* next frame interval, camera frame [R23] */
     sfo_level lv[SFO_MAX_LEVELS];
 } sfo_ctx;
 
@@ -569,6 +624,16 @@ sfo_ctx* sfo_create(int H, int W, int L, double fx, double fy, double cx, double
         l->valid = calloc(n, 1);
     }
     return c;
+}
+
+/* Camera angular velocity (rad/s) and linear acceleration (m/s^2), camera
+ * frame, used by the following frames' predictions under SFO_IMU [R23]. */
+void sfo_set_motion(sfo_ctx* c, const double* omega, const double* accel)
+{
+    for (int k = 0; k < 3; k++) {
+        c->omega[k] = omega ? omega[k] : 0.0;
+        c->accel[k] = accel ? accel[k] : 0.0;
+    }
 }
 
 void sfo_destroy(sfo_ctx* c)
@@ -649,8 +714,11 @@ double sfo_step(sfo_ctx* c, const double* image, const double* range, double dt,
             memcpy(rho_k, l->rho, n * sizeof(double));
             memcpy(Y_k, l->Yhat, n * sizeof(double));
             /* prediction k -> k+ (Sec. 4.4, 4.6) */
+            /* R25: Omega dt and a_c dt^2, the frame units of w */
+            double imu[6] = {c->omega[0] * dt, c->omega[1] * dt, c->omega[2] * dt,
+                             c->accel[0] * dt * dt, c->accel[1] * dt * dt, c->accel[2] * dt * dt};
             double cf = sfo_propagate(l->H, l->W, c->iters[h], c->flags, l->eta, l->B, l->dmu,
-                                      l->w, top ? NULL : l->dw, l->rho, top ? NULL : l->Yhat, NULL);
+                                      l->w, top ? NULL : l->dw, l->rho, top ? NULL : l->Yhat, NULL, imu);
             if (cf > cfl) cfl = cf;
             /* measurement models at k+1 (Sec. 4.2, 4.3) */
             sfo_image_model(l->H, l->W, l->Y, l->B, l->dmu, Ynew, NULL, gY);

@@ -7,7 +7,9 @@ exactly to rationals) and require agreement to round-off.
 
 Readings follow the oracle's: larger-magnitude dominant speed with ties to the
 minus-side neighbour (R1), row operator in the row pass (R2), replicated
-borders (R13), the full source in both passes unless ``split`` (R22).
+borders (R13), the full source in both passes unless ``split`` (R22), and the
+inertial terms once per sub-iteration after both passes when ``imu`` is given
+(R23-R25).
 """
 from fractions import Fraction as Fr
 
@@ -21,9 +23,14 @@ def _proj(eta, v):
     return [v[k] - eta[k] * d for k in range(3)]
 
 
-def propagate(H, W, N, eta, b1, b2, dmu, w, rho, dw=None, Y=None, split=False):
+def _cross(a, b):
+    return [a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]]
+
+
+def propagate(H, W, N, eta, b1, b2, dmu, w, rho, dw=None, Y=None, split=False, imu=None):
     """Returns (w, rho, dw, Y) after N sub-iterations; all arguments are nested
-    lists [i][j] of Fractions (vectors as 3-lists)."""
+    lists [i][j] of Fractions (vectors as 3-lists); ``imu`` = (Omega, a), two
+    3-lists of Fractions in frame units."""
     dt = Fr(1, N)
     sdt = dt / 2 if split else dt
 
@@ -66,6 +73,16 @@ def propagate(H, W, N, eta, b1, b2, dmu, w, rho, dw=None, Y=None, split=False):
                     if Y is not None:
                         ny[i][j] = upd(Y[im][jm], Y[i][j], Y[ip][jp], with_source=False)
             w, rho, dw, Y = nw, nr, nd, ny
+        if imu is not None:
+            om, acc = imu
+            for i in range(H):
+                for j in range(W):
+                    ow = _cross(om, w[i][j])
+                    ooe = _cross(om, _cross(om, eta[i][j]))
+                    w[i][j] = [w[i][j][k] + dt * (-2 * ow[k] - ooe[k] - rho[i][j] * acc[k]) for k in range(3)]
+                    if dw is not None:
+                        od = _cross(om, dw[i][j])
+                        dw[i][j] = [dw[i][j][k] - dt * 2 * od[k] for k in range(3)]
     return w, rho, dw, Y
 
 
