@@ -354,9 +354,10 @@ def run_ours(args):
         achieved = bpl / (prop_ms / 1e3) / 1e9
         frame_bytes = algorithmic_bytes_per_frame(H, W, seq.levels)
         if args.quick:
-            e2e, (mean_epe, max_epe), cpu, batched = None, (None, None), None, None
+            e2e, (mean_epe, max_epe), cpu, batched, imu = None, (None, None), None, None, None
         else:
             e2e = measure_e2e(filt, seq, args.steps)
+            imu = measure_imu(seq, images, ranges, min(args.steps, 100), evict_l2)
             mean_epe, max_epe = epe_vs_oracle(seq, frames=3)
             cpu = cpu_baseline(seq)
             filt.close()
@@ -388,6 +389,7 @@ def run_ours(args):
             "kernels": shares,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "imu": imu,
             "batched": batched,
             "gpu_launches": kstep * args.steps,
             "clocks": clocks,
@@ -483,6 +485,57 @@ def measure_batch(steps, warmup, dev):
     }
     batch.close()
     return out
+
+
+def measure_imu(seq, images, ranges, steps, evict_l2):
+    """The same workload with the inertial source terms (SF_IMU): every frame
+    sets the camera's angular velocity and acceleration (a_c = dv/dt +
+    Omega x v from the sequence's camera motion) and steps; device time per
+    frame and of the propagation launch."""
+    import torch
+    from paper_2406_18031_b300 import sf
+    H, W = seq.shape
+    params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
+                       flags=sf.CHECK_CFL | sf.IMU)
+    filt = sf.Filter(H, W, seq.levels, params)
+    flow = torch.empty((3, H, W), device="cuda")
+    inv = torch.empty((H, W), device="cuda")
+    stream = torch.cuda.current_stream()
+    motion = []
+    for k in range(seq.frames):
+        kn = min(k + 1, seq.frames - 1)
+        acc = (seq.v[kn] - seq.v[k]) / seq.dt + np.cross(seq.omega[k], seq.v[k])
+        motion.append((seq.omega[k].tolist(), acc.tolist()))
+
+    def step(k):
+        kk = k % seq.frames
+        filt.set_motion(*motion[kk], stream=stream)
+        filt.step(images[kk], ranges[kk], seq.dt, flow, inv, stream=stream)
+
+    for k in range(4):
+        step(k)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        evict_l2(k)
+        starts[k].record(stream)
+        step(4 + k)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    filt.profile(True)
+    for k in range(steps):
+        evict_l2(k)
+        step(4 + steps + k)
+    torch.cuda.synchronize()
+    filt.profile(False)
+    slots = filt.profile_read()
+    status = filt.status()
+    filt.close()
+    return {"value": 1e3 / ms, "unit": "frames/s", "ms_per_step": ms,
+            "k_propagate_ms_per_launch": slots[0][0] / max(slots[0][1], 1),
+            "motion": "Omega and a_c = dv/dt + Omega x v of the sequence's camera, set every frame (sf_set_motion)",
+            "status": sf.strerror(status)}
 
 
 def measure_e2e(filt, seq, steps):

@@ -58,6 +58,17 @@ extern "C" {
                                  Eq. 53) instead of dt in both printed passes */
 #define SF_CHECK_CFL 4        /* record SF_WARN_CFL when Eq. 67 is violated   */
 #define SF_CHECK_FINITE 8     /* record SF_ENONFINITE for NaN/Inf output flow */
+#define SF_IMU 32             /* add the inertial source terms to the prediction:
+                                 the terms the paper drops by its assumption in
+                                 Sec. 4.4, -Omega x w + a_w of the total-derivative
+                                 equation of Sec. 3 with a_w = -rho a_c -
+                                 Omega x (w + Omega x eta) (acceleration sign from
+                                 the camera's equation of motion dv_c/dt =
+                                 -Omega x v_c + a_c; the derivation prints
+                                 +rho a_c), integrated once per sub-iteration after
+                                 the two axis passes; lower levels turn their
+                                 increment by -2 Omega x dw.  Omega and a_c come
+                                 from sf_set_motion / sf_batch_motion.          */
 #define SF_AUTOTUNE 16        /* at creation, time the propagation launches of one
                                  frame for each nf_max in {8, 6, 4, 3, 2} that
                                  splits the N_h differently and keep the fastest
@@ -140,6 +151,16 @@ int sf_set_state(sf_ctx* c, int level, const float* src, float dt_prev, void* st
  * launch per pyramid level); a negative code for a NULL context. */
 int sf_kernels_per_step(const sf_ctx* c);
 
+/* Camera motion over the next frame interval for SF_IMU: omega = angular
+ * velocity (rad/s, 3 floats), accel = linear acceleration with respect to an
+ * inertial frame (m/s^2, 3 floats), both in the camera frame (Sec. 3; an IMU
+ * measures them).  Host pointers; NULL means zero.  Copied to the device on
+ * `stream` (pageable copy: the call returns once the values are staged);
+ * the next sf_step calls on that stream use them, converted to frame units
+ * with that step's dt (Omega dt, a dt^2).  SF_EINVAL for a NULL context or a
+ * non-finite value.  Without SF_IMU the values are not read. */
+int sf_set_motion(sf_ctx* c, const float* omega, const float* accel, void* stream);
+
 /* The nf_max the context runs with (sf_params.nf_max, or the autotuner's
  * choice under SF_AUTOTUNE); a negative code for a NULL context.  The paper
  * has no such setting: it is how the N sub-iterations of Sec. 4.6 are cut
@@ -203,6 +224,14 @@ int sf_batch_launches_per_step(const sf_batch* b);
  * params[0].flags' SF_AUTOTUNE). */
 int sf_batch_nf_max(const sf_batch* b);
 
+/* Stream s's motion slot for SF_IMU (the batch takes SF_IMU from
+ * params[0].flags): *motion receives a device pointer to 6 floats, Omega
+ * (rad/s) then a_c (m/s^2), camera frame, zero at creation and owned by the
+ * batch.  Write it on the stepping stream before sf_batch_step; the step
+ * reads it on the device (so graph replays see new values) and converts it
+ * with dt as sf_set_motion does. */
+int sf_batch_motion(sf_batch* b, int s, float** motion);
+
 /* As sf_profile / sf_profile_read for a batch; while profiling, steps run as
  * plain launches (no graph replay) so each launch can be timed. */
 int sf_batch_profile(sf_batch* b, int enable);
@@ -237,6 +266,14 @@ typedef struct sf_grid {
 int sf_propagate(const sf_grid* g, int N, int flags, float wscale,
                  const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
                  int* status, void* stream);
+
+/* sf_propagate with the inertial source terms of SF_IMU (set or not in
+ * flags): imu = host pointer to 6 floats in frame units, Omega dt (rad per
+ * frame) then a_c dt^2 (m per frame^2); the source step runs once per
+ * sub-iteration with dt = 1/N.  SF_EINVAL for a NULL or non-finite imu. */
+int sf_propagate_imu(const sf_grid* g, int N, int flags, float wscale, const float* imu,
+                     const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
+                     int* status, void* stream);
 
 /* sf_propagate without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory --

@@ -106,23 +106,34 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
 // need 16-byte alignment whatever the size of the job struct
 inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
-template <bool C8, bool LIT>
-int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
+template <bool C8, bool LIT, bool IMU>
+int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
 {
-    if (set_smem_attr((const void*)k_propagate<C8, LIT>, p.smem)) return SF_ECUDA;
-    k_propagate<C8, LIT><<<p.nwork, kPrThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale, flags,
-                                                              status);
+    if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU>, p.smem)) return SF_ECUDA;
+    k_propagate<C8, LIT, IMU><<<p.nwork, kPrThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale,
+                                                                   flags, status, mscale);
     return last_error();
 }
 
-int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st)
+template <bool C8, bool LIT>
+int launch_propagate_l(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
+{
+    if (flags & SF_IMU) return launch_propagate_t<C8, LIT, true>(p, parity, wscale, flags, status, mscale, st);
+    return launch_propagate_t<C8, LIT, false>(p, parity, wscale, flags, status, mscale, st);
+}
+
+// one propagation launch; with SF_IMU in flags the jobs' motion slots hold
+// (Omega, a) and mscale converts them to frame units (Omega mscale,
+// a mscale^2): the frame time in seconds, or 1 for values already per frame
+int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st,
+                     float mscale = 1.0f)
 {
     if (p.nwork == 0) return SF_OK;
     const bool lit = (flags & SF_DOMINANT_LITERAL) != 0;
-    if (p.c8) return lit ? launch_propagate_t<true, true>(p, parity, wscale, flags, status, st)
-                         : launch_propagate_t<true, false>(p, parity, wscale, flags, status, st);
-    return lit ? launch_propagate_t<false, true>(p, parity, wscale, flags, status, st)
-               : launch_propagate_t<false, false>(p, parity, wscale, flags, status, st);
+    if (p.c8) return lit ? launch_propagate_l<true, true>(p, parity, wscale, flags, status, mscale, st)
+                         : launch_propagate_l<true, false>(p, parity, wscale, flags, status, mscale, st);
+    return lit ? launch_propagate_l<false, true>(p, parity, wscale, flags, status, mscale, st)
+               : launch_propagate_l<false, false>(p, parity, wscale, flags, status, mscale, st);
 }
 
 int launch_solve(const Plan& p, const UpdArgs& a, cudaStream_t st)
@@ -254,6 +265,7 @@ struct EngineStream {
     float* range;
     float* flow;
     float* inv;
+    float* motion;        // Omega (rad/s) and a (m/s^2) over the next frame, device (6 floats)
 };
 
 struct Engine {
@@ -268,6 +280,7 @@ struct Engine {
     Plan solve;                 // every level of every stream
     std::vector<Plan> smooth;   // cascade: depth d handles level L - 1 - d of every stream
     void* io = nullptr;         // slots of a batch
+    float* motion = nullptr;    // every stream's motion slot (8 floats each), zeroed
     Profiler prof;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     float graph_dt[2] = {0.0f, 0.0f};
@@ -293,6 +306,7 @@ void engine_free(Engine& E)
     for (auto& s : E.st)
         for (int h = 0; h < s.L; ++h) cudaFree(s.lv[h].block);
     cudaFree(E.io);
+    cudaFree(E.motion);
     cudaFree(E.status);
 }
 
@@ -368,6 +382,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
                     j.nf = nf;
                     j.dt = 1.0f / (float)lv.N;
                     j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
+                    j.motion = s.motion;
                     jobs.push_back(j);
                     add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
                     c8 |= !top;
@@ -512,6 +527,9 @@ int engine_init(Engine& E)
         r = engine_levels(s, st);
         if (r) break;
     }
+    if (!r && cudaMalloc(&E.motion, E.st.size() * 8 * sizeof(float)) != cudaSuccess) { E.motion = nullptr; r = SF_ENOMEM; }
+    if (!r) r = cudaMemsetAsync(E.motion, 0, E.st.size() * 8 * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    for (size_t k = 0; k < E.st.size() && !r; ++k) E.st[k].motion = E.motion + 8 * k;
     if (!r && cudaMalloc(&E.status, sizeof(int)) != cudaSuccess) { E.status = nullptr; r = SF_ENOMEM; }
     if (!r) r = cudaMemsetAsync(E.status, 0, sizeof(int), st) == cudaSuccess ? SF_OK : SF_ECUDA;
     if (!r) r = engine_prop_plans(E, st);
@@ -539,7 +557,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
     if (!a.init) {
         for (auto& pl : E.prop) {
             ProfScope ps(E.prof, slot++, st);
-            r = launch_propagate(pl, E.parity, wscale, E.flags, E.status, st);
+            r = launch_propagate(pl, E.parity, wscale, E.flags, E.status, st, dt);
             if (r) return r;
         }
     } else {
@@ -761,6 +779,20 @@ int sf_nf_max(const sf_ctx* c)
     return c->E.nf_max;
 }
 
+int sf_set_motion(sf_ctx* c, const float* omega, const float* accel, void* stream)
+{
+    if (!c) return SF_EINVAL;
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k) {
+        if (omega) m[k] = omega[k];
+        if (accel) m[3 + k] = accel[k];
+    }
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(m[k])) return SF_EINVAL;
+    return cudaMemcpyAsync(c->E.st[0].motion, m, sizeof(m), cudaMemcpyHostToDevice, (cudaStream_t)stream) ==
+                   cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
 void sf_destroy(sf_ctx* c) { destroy_ctx(c); }
 
 const char* sf_strerror(int code)
@@ -888,6 +920,13 @@ int sf_batch_nf_max(const sf_batch* b)
     return b->E.nf_max;
 }
 
+int sf_batch_motion(sf_batch* b, int s, float** motion)
+{
+    if (!b || !motion || s < 0 || s >= (int)b->E.st.size()) return SF_EINVAL;
+    *motion = b->E.st[s].motion;
+    return SF_OK;
+}
+
 int sf_batch_profile(sf_batch* b, int enable)
 {
     if (!b) return SF_EINVAL;
@@ -909,8 +948,11 @@ void sf_batch_destroy(sf_batch* b) { destroy_batch(b); }
 // C ABI: stage entry points
 // ---------------------------------------------------------------------------
 
-int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* s0_in, const float* s1_in,
-                 float* s0_out, float* s1_out, int* status, void* stream)
+namespace {
+
+// sf_propagate / sf_propagate_imu: imu (host, 6 floats, frame units) or null
+int stage_propagate(const sf_grid* g, int N, int flags, float wscale, const float* imu, const float* s0_in,
+                    const float* s1_in, float* s0_out, float* s1_out, int* status, void* stream)
 {
     if (!g || g->H < 1 || g->W < 1 || N < 1 || !s0_in || !s0_out) return SF_EINVAL;
     if ((s1_in == nullptr) != (s1_out == nullptr)) return SF_EINVAL;
@@ -946,14 +988,17 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
         Plan pl;
         pl.c8 = c8;
         pl.smem = prop_smem_bytes();
-        // the job and work list travel through stream-ordered scratch
+        // the job, its work list and the motion travel through stream-ordered scratch
         void* mem = nullptr;
         const size_t woff = work_offset(sizeof(PropJob));
-        const size_t bytes = woff + work.size() * sizeof(int4);
+        const size_t moff = woff + work_offset(work.size() * sizeof(int4));
+        const size_t bytes = moff + 8 * sizeof(float);
         if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) { r = SF_ENOMEM; break; }
-        std::vector<unsigned char> host(bytes);
+        if (imu) j.motion = (const float*)((unsigned char*)mem + moff);
+        std::vector<unsigned char> host(bytes, 0);
         std::memcpy(host.data(), &j, sizeof(PropJob));
         std::memcpy(host.data() + woff, work.data(), work.size() * sizeof(int4));
+        if (imu) std::memcpy(host.data() + moff, imu, 6 * sizeof(float));
         r = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SF_OK : SF_ECUDA;
         if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;  // host buffer lifetime
         pl.jobs = mem;
@@ -966,6 +1011,23 @@ int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* 
     }
     if (scratch) cudaFreeAsync(scratch, st);
     return r;
+}
+
+}  // namespace
+
+int sf_propagate(const sf_grid* g, int N, int flags, float wscale, const float* s0_in, const float* s1_in,
+                 float* s0_out, float* s1_out, int* status, void* stream)
+{
+    return stage_propagate(g, N, flags, wscale, nullptr, s0_in, s1_in, s0_out, s1_out, status, stream);
+}
+
+int sf_propagate_imu(const sf_grid* g, int N, int flags, float wscale, const float* imu, const float* s0_in,
+                     const float* s1_in, float* s0_out, float* s1_out, int* status, void* stream)
+{
+    if (!imu) return SF_EINVAL;
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(imu[k])) return SF_EINVAL;
+    return stage_propagate(g, N, flags | SF_IMU, wscale, imu, s0_in, s1_in, s0_out, s1_out, status, stream);
 }
 
 int sf_update(const sf_grid* g, int level, int top, int S, int init, const float* gamma, float lambda_ref,

@@ -40,6 +40,7 @@ struct PropJob {
     int apply_wscale;       // first launch of the frame: rescale w, dw on load
     float dt;               // 1 / N of the whole frame
     int tiles_x;
+    const float* motion;    // inertial source terms: Omega (3), a (3); frame units after x mscale, x mscale^2
 };
 
 // Register-resident tiles: a CTA of kPrWarps warps holds a kPrW x kPrH region
@@ -145,10 +146,35 @@ __device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, bool h
     return k;
 }
 
-template <bool C8, bool LITERAL>
+// The inertial source terms of one sub-iteration (readings R23-R25), applied
+// after its two axis passes: w <- w + dt (-2 Om x w - Om x (Om x eta) - rho a)
+// and, below the top, dw <- dw - 2 dt Om x dw (Om, a in frame units).
+__device__ __forceinline__ void inertial_step(float4& w, float4& d, bool has1, float ex, float ey, float ez,
+                                              const float* om, const float* ac, float dt)
+{
+    const float oex = fmaf(om[1], ez, -om[2] * ey), oey = fmaf(om[2], ex, -om[0] * ez),
+                oez = fmaf(om[0], ey, -om[1] * ex);
+    const float ooex = fmaf(om[1], oez, -om[2] * oey), ooey = fmaf(om[2], oex, -om[0] * oez),
+                ooez = fmaf(om[0], oey, -om[1] * oex);
+    const float owx = fmaf(om[1], w.z, -om[2] * w.y), owy = fmaf(om[2], w.x, -om[0] * w.z),
+                owz = fmaf(om[0], w.y, -om[1] * w.x);
+    const float m2dt = -2.0f * dt;
+    w.x = fmaf(dt, -fmaf(w.w, ac[0], ooex), fmaf(m2dt, owx, w.x));
+    w.y = fmaf(dt, -fmaf(w.w, ac[1], ooey), fmaf(m2dt, owy, w.y));
+    w.z = fmaf(dt, -fmaf(w.w, ac[2], ooez), fmaf(m2dt, owz, w.z));
+    if (has1) {
+        const float odx = fmaf(om[1], d.z, -om[2] * d.y), ody = fmaf(om[2], d.x, -om[0] * d.z),
+                    odz = fmaf(om[0], d.y, -om[1] * d.x);
+        d.x = fmaf(m2dt, odx, d.x);
+        d.y = fmaf(m2dt, ody, d.y);
+        d.z = fmaf(m2dt, odz, d.z);
+    }
+}
+
+template <bool C8, bool LITERAL, bool IMU>
 __global__ void __launch_bounds__(kPrThreads, 1)
 k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int parity, float wscale,
-            int flags, int* __restrict__ status)
+            int flags, int* __restrict__ status, float mscale)
 {
     extern __shared__ float4 smem4[];
     float4* geo = smem4;                                   // [kPrH][kPrW]
@@ -169,6 +195,14 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     const float ws = J.apply_wscale ? wscale : 1.0f;
     const float dt = J.dt;
     const float sdt = (flags & kSourceSplit) ? 0.5f * dt : dt;
+    float om[3] = {0.f, 0.f, 0.f}, ac[3] = {0.f, 0.f, 0.f};   // frame units
+    if (IMU && J.motion) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            om[c] = J.motion[c] * mscale;
+            ac[c] = J.motion[3 + c] * (mscale * mscale);
+        }
+    }
 
     const int c0 = 2 * lane;                               // my region columns c0, c0 + 1
     const int j0 = ox + c0, j1 = j0 + 1;                   // ... image columns
@@ -291,6 +325,7 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 const Coef kk = coefficients<LITERAL>(vm, vp, mi, pi, src, dt, sdt, bad, row_in && col_in[q]);
                 na[q] = step4(a[k][q], kk.minus ? prev_a[q] : next_a[q], kk.kself, kk.knb);
                 if (has1) nb[q] = step4y(b[k][q], sel4(kk.minus, prev_b[q], next_b[q]), kk.kself, kk.knb, kk.kselfy);
+                if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
                 prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
                 a[k][q] = na[q];
                 if (has1) b[k][q] = nb[q];

@@ -18,7 +18,7 @@ LIB_PATH = _PKG / "libsf.so"
 
 MAX_LEVELS = 4
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, WARN_CFL = 0, -1, -2, -3, -4, -5, 1
-DOMINANT_LITERAL, SOURCE_SPLIT, CHECK_CFL, CHECK_FINITE, AUTOTUNE = 1, 2, 4, 8, 16
+DOMINANT_LITERAL, SOURCE_SPLIT, CHECK_CFL, CHECK_FINITE, AUTOTUNE, IMU = 1, 2, 4, 8, 16, 32
 
 
 class SFError(RuntimeError):
@@ -42,9 +42,9 @@ class CGrid(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
-           "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
+           "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_set_motion", "sf_propagate_imu", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
-           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_profile",
+           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
            "sf_batch_destroy"]
 
@@ -75,6 +75,9 @@ def lib():
         L.sf_strerror.argtypes = [i]
         L.sf_strerror.restype = ctypes.c_char_p
         L.sf_propagate.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
+        L.sf_propagate_imu.argtypes = [P(CGrid), i, i, f, P(f), vp, vp, vp, vp, vp, vp]
+        L.sf_set_motion.argtypes = [vp, P(f), P(f), vp]
+        L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
         L.sf_batch_buffers.argtypes = [vp, i, P(vp), P(vp), P(vp), P(vp)]
         L.sf_batch_step.argtypes = [vp, f, vp]
@@ -196,6 +199,12 @@ class Filter:
         """Sub-iterations fused per propagation launch (set, or chosen by AUTOTUNE)."""
         return _check(lib().sf_nf_max(self._h), "sf_nf_max")
 
+    def set_motion(self, omega=None, accel=None, stream=None):
+        """Angular velocity (rad/s) and linear acceleration (m/s^2) for IMU steps."""
+        om = None if omega is None else (ctypes.c_float * 3)(*[float(x) for x in omega])
+        ac = None if accel is None else (ctypes.c_float * 3)(*[float(x) for x in accel])
+        _check(lib().sf_set_motion(self._h, om, ac, _stream(stream)), "sf_set_motion")
+
     def profile(self, enable: bool):
         _check(lib().sf_profile(self._h, int(bool(enable))), "sf_profile")
 
@@ -239,6 +248,15 @@ def propagate(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wsca
     """Stage entry point ``sf_propagate`` on [H, W, 4] float32 CUDA tensors."""
     return _check(lib().sf_propagate(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in), _ptr(s1_in),
                                      _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)), "sf_propagate")
+
+
+def propagate_imu(g: CGrid, N, imu, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
+                  stream=None):
+    """``sf_propagate_imu``: imu = (Omega, a) in frame units, six numbers."""
+    m = (ctypes.c_float * 6)(*[float(x) for x in np.asarray(imu, dtype=np.float64).reshape(6)])
+    return _check(lib().sf_propagate_imu(ctypes.byref(g), int(N), int(flags), float(wscale), m, _ptr(s0_in),
+                                         _ptr(s1_in), _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)),
+                  "sf_propagate_imu")
 
 
 def propagate_noalloc(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
@@ -290,6 +308,11 @@ class Batch:
             _check(lib().sf_batch_buffers(h, s, *[ctypes.byref(x) for x in ptrs]), "sf_batch_buffers")
             self.slots.append(tuple(_wrap(x.value, shp) for x, shp in
                                     zip(ptrs, [(H, W), (H, W), (3, H, W), (H, W)])))
+        self.motion = []      # per stream: 6-float device view, Omega (rad/s) then a (m/s^2)
+        for s in range(n):
+            mp = ctypes.c_void_p()
+            _check(lib().sf_batch_motion(h, s, ctypes.byref(mp)), "sf_batch_motion")
+            self.motion.append(_wrap(mp.value, (6,)))
 
     def step(self, dt, stream=None):
         return _check(lib().sf_batch_step(self._h, float(dt), _stream(stream)), "sf_batch_step")

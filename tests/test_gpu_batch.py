@@ -33,6 +33,38 @@ def _params(seq, nf_max=None):
                      flags=sf.CHECK_CFL | sf.CHECK_FINITE, nf_max=nf_max)
 
 
+def test_batch_inertial_terms_match_single_stream_filters():
+    # SF_IMU: each stream's motion slot, written on the device before the step,
+    # against single-stream filters given the same motion by sf_set_motion
+    seqs = _streams()[:3]
+    dt = seqs[0].dt
+    P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth,
+                   flags=sf.CHECK_CFL | sf.CHECK_FINITE | sf.IMU) for q in seqs]
+    batch = sf.Batch([q.shape for q in seqs], [q.levels for q in seqs], P)
+    singles = [sf.Filter(*q.shape, q.levels, p) for q, p in zip(seqs, P)]
+    rng = np.random.default_rng(4)
+    stream = torch.cuda.Stream()
+    outs = [(torch.empty((3, *q.shape), device="cuda"), torch.empty(q.shape, device="cuda")) for q in seqs]
+    for k in range(5):
+        with torch.cuda.stream(stream):
+            for s, q in enumerate(seqs):
+                om, acc = rng.normal(size=3) * 2.0, rng.normal(size=3) * 5.0   # rad/s, m/s^2
+                img, rg, _, _ = batch.slots[s]
+                img.copy_(torch.from_numpy(q.image[k]).cuda())
+                rg.copy_(torch.from_numpy(q.range[k]).cuda())
+                batch.motion[s].copy_(torch.tensor(np.concatenate([om, acc]), dtype=torch.float32))
+                singles[s].set_motion(om, acc, stream=stream)
+                singles[s].step(torch.from_numpy(q.image[k]).cuda(), torch.from_numpy(q.range[k]).cuda(), dt,
+                                outs[s][0], outs[s][1], stream=stream)
+            batch.step(dt, stream=stream)
+        stream.synchronize()
+        for s, q in enumerate(seqs):
+            _, _, dmu = oracle.geometry(*q.shape, q.fx, q.fy, q.cx, q.cy)
+            e = np.abs(batch.slots[s][2].cpu().numpy().astype(np.float64) - outs[s][0].cpu().numpy()) * dt / dmu[None]
+            assert e.max() <= gu.FLOW_TOL_PX, (k, s, e.max())
+    assert batch.status() in (sf.OK, sf.WARN_CFL)
+
+
 @pytest.mark.parametrize("nf_max", [None, 4])
 def test_batch_matches_single_stream_filters_and_oracle(nf_max):
     seqs = _streams()

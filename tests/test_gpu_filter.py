@@ -101,6 +101,29 @@ def test_three_level_driving_scene_with_sky():
     assert max(e for _, e in errs) <= gu.RHO_TOL
 
 
+def test_inertial_terms_whole_frames():
+    # SF_IMU on both filters, each frame's prediction driven by the camera's
+    # angular velocity and its acceleration a_c = dv/dt + Omega x v (the
+    # camera's equation of motion in Sec. 3), as an IMU would report them
+    seq = scenes.scene512(frames=7, H=96, W=128, max_flow=4.0, levels=2, iters=(4, 2), smooth=(2, 4))
+    H, W = seq.shape
+    g, r = _pair(seq, flags=oracle.IMU)
+    _, _, dmu = r.geometry(0)
+    flow = torch.empty((3, H, W), device="cuda")
+    inv = torch.empty((H, W), device="cuda")
+    for k in range(6):
+        om = seq.omega[k]
+        acc = (seq.v[k + 1] - seq.v[k]) / seq.dt + np.cross(om, seq.v[k])
+        g.set_motion(om, acc)
+        r.set_motion(gu.f32(om), gu.f32(acc))
+        g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, flow, inv)
+        rf, ri = r.step(seq.image[k], seq.range[k], seq.dt)
+        e = float((np.abs(flow.cpu().numpy().astype(np.float64) - rf) * seq.dt / dmu[None]).max())
+        assert e <= gu.FLOW_TOL_PX, (k, e)
+        assert np.abs(inv.cpu().numpy() - ri).max() <= gu.RHO_TOL
+    assert g.status() == sf.OK
+
+
 def test_frame_time_change():
     seq = scenes.plane64(frames=6)
     dts = [seq.dt, seq.dt, seq.dt / 2, seq.dt / 2, seq.dt * 1.5, seq.dt]

@@ -66,6 +66,43 @@ def test_propagate_matches_oracle(H, W, N, top, flags):
         assert bool(int(status.item()) & 1) == (cfl > 1.0), cfl
 
 
+@pytest.mark.parametrize("H,W", [(80, 72), (33, 47)])
+@pytest.mark.parametrize("N", [1, 3, 12])
+@pytest.mark.parametrize("top", [True, False])
+def test_propagate_inertial_terms_match_oracle(H, W, N, top):
+    # SF_IMU: the source step -2 Om x w - Om x (Om x eta) - rho a after each
+    # sub-iteration (and -2 Om x dw below the top), Om and a in frame units
+    rng = np.random.default_rng(300 + H + N + 7 * top)
+    fx = fy = W / 2.0 + 3.0
+    g, eta, B, dmu = gu.level_grid(H, W, fx, fy, W / 2.0 - 1.5, H / 2.0 + 0.5, 1)
+    w = gu.cfl_scaled(gu.flow_field(rng, H, W, dmu, max_px=1.0), eta, B, dmu, min(0.6 * N, 0.1 * min(H, W)))
+    rho = gu.f32(0.2 + 0.15 * gu.smooth_field(rng, H, W))
+    dw = None if top else gu.f32(gu.flow_field(rng, H, W, dmu, max_px=0.3 * N) * 0.5)
+    Y = None if top else gu.f32(0.5 + 0.4 * gu.smooth_field(rng, H, W, n_waves=6))
+    d = float(dmu.mean())
+    om = rng.normal(size=3); om *= 0.4 * d / np.linalg.norm(om)          # ~0.4 px/frame of rotation
+    ac = rng.normal(size=3); ac *= 0.3 * d / np.linalg.norm(ac) / 0.35   # rho a ~ 0.3 px/frame
+    imu = gu.f32(np.concatenate([om, ac]))
+    s0 = np.concatenate([w, rho[..., None]], -1)
+    s1 = None if top else np.concatenate([dw, Y[..., None]], -1)
+    o0 = torch.empty((H, W, 4), device="cuda")
+    o1 = None if top else torch.empty((H, W, 4), device="cuda")
+    sf.propagate_imu(g, N, imu, _t(s0), o0, None if top else _t(s1), o1)
+    torch.cuda.synchronize()
+    rw, rdw, rr, ry, _ = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y, flags=oracle.IMU,
+                                          imu=imu.astype(np.float64))
+    out0 = o0.cpu().numpy()
+    assert gu.px_err(out0[..., :3], rw, dmu) <= gu.FLOW_TOL_PX
+    assert np.abs(out0[..., 3] - rr).max() <= gu.RHO_TOL
+    if not top:
+        out1 = o1.cpu().numpy()
+        assert gu.px_err(out1[..., :3], rdw, dmu) <= gu.FLOW_TOL_PX
+        assert np.abs(out1[..., 3] - ry).max() <= gu.Y_TOL
+    # and the terms matter at this size: without them the flow differs
+    rw0 = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y)[0]
+    assert gu.px_err(out0[..., :3], rw0, dmu) > 100 * gu.FLOW_TOL_PX
+
+
 def test_propagate_flags_cfl_violation():
     H = W = 40
     g, eta, B, dmu = gu.level_grid(H, W, 20.0, 20.0, 20.0, 20.0, 1)
