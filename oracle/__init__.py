@@ -64,6 +64,8 @@ def lib():
         L.sfo_propagate.argtypes = [i, i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D]
         L.sfo_imu_step.argtypes = [i, i, d, _D, _D, _D, _D, _D]
         L.sfo_set_motion.argtypes = [vp, _D, _D]
+        L.sfo_remap_pinhole.argtypes = [i, i, d, d, d, d, _D, i, i, _D, _D, _D, _D, _D]
+        L.sfo_remap_equirect.argtypes = [i, i, d, d, d, d, _D, i, i, _D, _D, _D, _D]
         L.sfo_propagate.restype = d
         L.sfo_update.argtypes = [i, i, d, d, d, _D, _D, _D, _D, _D, _D, _U8, _D, _D, _D, _D]
         L.sfo_blend.argtypes = [i, d, d, _D, _U8, _D, _D]
@@ -200,6 +202,33 @@ def upsample_add(wc, dw=None):
     out = np.empty((H, W, 3))
     lib().sfo_upsample_add(Hc, Wc, _d(wc), H, W, _d(None if dw is None else _f64(dw)), _d(out))
     return out
+
+
+# --------------------------------------------------------------------------
+# remapping camera data onto the grid (readings R26, R27)
+# --------------------------------------------------------------------------
+
+def remap_pinhole(H, W, grid_K, R, cam_K, image, rng=None):
+    """Grid (H x W, intrinsics grid_K = fx, fy, cx, cy) <- pinhole camera frame
+    (cam_K, image/rng of any size); R = camera <- grid rotation.  Returns
+    (image, range) on the grid (range None when rng is None)."""
+    image = _f64(image); Hs, Ws = image.shape
+    Rm = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(9))
+    K = np.ascontiguousarray(np.asarray(cam_K, dtype=np.float64).reshape(4))
+    oi = np.empty((H, W)); orng = np.empty((H, W)) if rng is not None else None
+    lib().sfo_remap_pinhole(H, W, *[float(x) for x in grid_K], _d(Rm), Hs, Ws, _d(K), _d(image),
+                            _d(None if rng is None else _f64(rng)), _d(oi), _d(orng))
+    return oi, orng
+
+
+def remap_equirect(H, W, grid_K, R, image, rng=None):
+    """Grid <- equirectangular panorama (longitude across columns)."""
+    image = _f64(image); Hs, Ws = image.shape
+    Rm = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(9))
+    oi = np.empty((H, W)); orng = np.empty((H, W)) if rng is not None else None
+    lib().sfo_remap_equirect(H, W, *[float(x) for x in grid_K], _d(Rm), Hs, Ws, _d(image),
+                             _d(None if rng is None else _f64(rng)), _d(oi), _d(orng))
+    return oi, orng
 
 
 # --------------------------------------------------------------------------

@@ -62,6 +62,19 @@
  *      levels carry -Omega x (Omega x eta) and rho a_c; the remainder
  *      (rho_h - up rho_{h+1}) a_c is dropped).  Omega and a_c enter in frame
  *      units, Omega dt (rad/frame) and a_c dt^2 (m/frame^2), like w.
+ *  R26 remapping camera data onto the grid (the paper maps its panoramic
+ *      renders and camera frames onto the grid before filtering and counts
+ *      that in its runtime, Sec. 6, without describing the resampling): each
+ *      grid ray, rotated into the camera frame by R, is projected into the
+ *      source image; brightness is bilinear between pixel centres with
+ *      replicated edges, range is the nearest pixel's (no mixing of depths
+ *      across an occlusion edge); a ray behind the camera or outside the
+ *      source image gets brightness 0 and range 0 (no measurement).
+ *  R27 panoramas are equirectangular: column u spans longitude
+ *      phi = 2 pi (u / Ws) - pi, row v latitude theta = pi/2 - pi (v / Hs)
+ *      (pixel k covers [k, k+1)); the ray (cos th sin phi, -sin th,
+ *      cos th cos phi) in the camera frame (x right, y down, z forward);
+ *      longitude wraps around.
  *  G1  grid: level h is a pinhole grid with intrinsics scaled by 2^(1-h);
  *      rays pass through pixel centres; the neighbour rays that define B
  *      and dmu exist analytically beyond the image edge.
@@ -786,4 +799,83 @@ void sfo_get_geometry(const sfo_ctx* c, int h, double* eta, double* B, double* d
     if (eta) memcpy(eta, l->eta, n * 3 * sizeof(double));
     if (B) memcpy(B, l->B, n * 6 * sizeof(double));
     if (dmu) memcpy(dmu, l->dmu, n * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Remapping camera data onto the grid [R26, R27]                             */
+/* ------------------------------------------------------------------------ */
+
+/* Source sampling at continuous pixel coordinates (u, v) of an Hs x Ws image
+ * whose pixel k covers [k, k+1): bilinear brightness between pixel centres
+ * with replicated edges (columns wrap when `wrap`), nearest-pixel range. */
+static void sample_source(int Hs, int Ws, const double* img, const double* rng, double u, double v, int wrap,
+                          double* Y, double* lam)
+{
+    double p = u - 0.5, q = v - 0.5;
+    double j0f = floor(p), i0f = floor(q);
+    double fx = p - j0f, fy = q - i0f;
+    int j0 = (int)j0f, i0 = (int)i0f, j1 = j0 + 1, i1 = i0 + 1;
+    if (wrap) { j0 = ((j0 % Ws) + Ws) % Ws; j1 = ((j1 % Ws) + Ws) % Ws; }
+    else { j0 = clampi(j0, 0, Ws - 1); j1 = clampi(j1, 0, Ws - 1); }
+    i0 = clampi(i0, 0, Hs - 1); i1 = clampi(i1, 0, Hs - 1);
+    *Y = (1.0 - fy) * ((1.0 - fx) * img[i0 * Ws + j0] + fx * img[i0 * Ws + j1]) +
+         fy * ((1.0 - fx) * img[i1 * Ws + j0] + fx * img[i1 * Ws + j1]);
+    if (rng) {
+        int jn = (int)floor(u), in = clampi((int)floor(v), 0, Hs - 1);
+        jn = wrap ? ((jn % Ws) + Ws) % Ws : clampi(jn, 0, Ws - 1);
+        *lam = rng[in * Ws + jn];
+    }
+}
+
+/* the grid ray of pixel (i, j) (not normalised) rotated into the camera frame */
+static void grid_ray_in_camera(double gfx, double gfy, double gcx, double gcy, const double* R, int i, int j,
+                               double* d)
+{
+    double m[3] = {(j + 0.5 - gcx) / gfx, (i + 0.5 - gcy) / gfy, 1.0};
+    for (int r = 0; r < 3; r++) d[r] = R[3 * r] * m[0] + R[3 * r + 1] * m[1] + R[3 * r + 2] * m[2];
+}
+
+/* A pinhole camera frame (intrinsics cam = fx, fy, cx, cy of an Hs x Ws image)
+ * onto the H x W grid with intrinsics (gfx, gfy, gcx, gcy); R = camera <- grid
+ * rotation, row-major.  rng / out_rng may be NULL. */
+void sfo_remap_pinhole(int H, int W, double gfx, double gfy, double gcx, double gcy, const double* R, int Hs,
+                       int Ws, const double* cam, const double* img, const double* rng, double* out_img,
+                       double* out_rng)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; i++) {
+        for (int j = 0; j < W; j++) {
+            double d[3], Y = 0.0, lam = 0.0;
+            grid_ray_in_camera(gfx, gfy, gcx, gcy, R, i, j, d);
+            if (d[2] > 0.0) {
+                double u = cam[0] * d[0] / d[2] + cam[2];
+                double v = cam[1] * d[1] / d[2] + cam[3];
+                if (u >= 0.0 && u <= Ws && v >= 0.0 && v <= Hs) sample_source(Hs, Ws, img, rng, u, v, 0, &Y, &lam);
+            }
+            out_img[i * W + j] = Y;
+            if (out_rng) out_rng[i * W + j] = lam;
+        }
+    }
+}
+
+/* An equirectangular panorama (Hs x Ws) onto the grid [R27]. */
+void sfo_remap_equirect(int H, int W, double gfx, double gfy, double gcx, double gcy, const double* R, int Hs,
+                        int Ws, const double* img, const double* rng, double* out_img, double* out_rng)
+{
+    const double pi = 3.14159265358979323846;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; i++) {
+        for (int j = 0; j < W; j++) {
+            double d[3], Y = 0.0, lam = 0.0;
+            grid_ray_in_camera(gfx, gfy, gcx, gcy, R, i, j, d);
+            double n = sqrt(dot3(d, d));
+            double phi = atan2(d[0], d[2]);
+            double theta = asin(-d[1] / n);
+            double u = (phi + pi) / (2.0 * pi) * Ws;
+            double v = (pi / 2.0 - theta) / pi * Hs;
+            sample_source(Hs, Ws, img, rng, u, v, 1, &Y, &lam);
+            out_img[i * W + j] = Y;
+            if (out_rng) out_rng[i * W + j] = lam;
+        }
+    }
 }
