@@ -328,6 +328,37 @@ int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const flo
                    float dt, float* flow_out, float* invdepth_out, int check_finite,
                    int* status, void* stream);
 
+/* ----------------------------------------------------------------------
+ * Mapping camera data onto the filter's grid.  The paper maps its panoramic
+ * renders and camera frames onto its grid before filtering and counts that
+ * step in its runtime (Sec. 6, "Urban Canyon" and "ZED" experiments); the
+ * resampling itself is not described there.  Every grid pixel (i, j) of
+ * `dst` (the level-1 sf_grid of a filter) casts the ray through its centre,
+ * ((j + 0.5 - cx)/fx, (i + 0.5 - cy)/fy, 1), rotated into the source's frame
+ * by R (3 x 3 row-major, source <- grid; x right, y down, z forward).
+ * Brightness: bilinear between source pixel centres, edges replicated.
+ * Range: the value of the source pixel containing the projected point (no
+ * interpolation across occlusion edges).  A source pixel k covers [k, k+1).
+ * src_image, src_range: device Hs x Ws float32; out_image, out_range: device
+ * dst->H x dst->W float32; src_range and out_range are both NULL or both
+ * set.  SF_EINVAL for bad sizes, pointers or non-finite R / intrinsics
+ * (checked before any device call).  Asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+
+/* A pinhole frame with intrinsics cam = (fx, fy, cx, cy) (pixels): rays
+ * behind the camera or projecting outside [0, Ws] x [0, Hs] get brightness 0
+ * and range 0 (no measurement). */
+int sf_remap_pinhole(const sf_grid* dst, const float* R, int Hs, int Ws, const float* cam,
+                     const float* src_image, const float* src_range, float* out_image,
+                     float* out_range, void* stream);
+
+/* An equirectangular panorama: column u spans longitude 2 pi u / Ws - pi
+ * (0 = forward, +x to the right), row v latitude pi/2 - pi v / Hs (up
+ * first); the direction of (longitude phi, latitude th) is
+ * (cos th sin phi, -sin th, cos th cos phi); longitude wraps around. */
+int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const float* src_image,
+                      const float* src_range, float* out_image, float* out_range, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1102,6 +1102,53 @@ int sf_update(const sf_grid* g, int level, int top, int S, int init, const float
     return r;
 }
 
+namespace {
+
+int remap_launch(int mode, const sf_grid* dst, const float* R, int Hs, int Ws, const float* cam,
+                 const float* src_image, const float* src_range, float* out_image, float* out_range, void* stream)
+{
+    if (!dst || dst->H < 1 || dst->W < 1 || !R || Hs < 1 || Ws < 1 || !src_image || !out_image) return SF_EINVAL;
+    if ((src_range == nullptr) != (out_range == nullptr)) return SF_EINVAL;
+    if (!(dst->fx > 0) || !(dst->fy > 0) || !std::isfinite(dst->fx) || !std::isfinite(dst->fy) ||
+        !std::isfinite(dst->cx) || !std::isfinite(dst->cy))
+        return SF_EINVAL;
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(R[k])) return SF_EINVAL;
+    RemapArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if (mode == 0) {
+        if (!cam || !(cam[0] > 0) || !(cam[1] > 0)) return SF_EINVAL;
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(cam[k])) return SF_EINVAL;
+        a.cfx = cam[0]; a.cfy = cam[1]; a.ccx = cam[2]; a.ccy = cam[3];
+    }
+    const Grid g = make_grid(*dst);
+    a.H = dst->H; a.W = dst->W;
+    a.gax = g.ax; a.gbx = g.bx; a.gay = g.ay; a.gby = g.by;
+    for (int k = 0; k < 9; ++k) a.R[k] = R[k];
+    a.Hs = Hs; a.Ws = Ws;
+    a.img = src_image; a.rng = src_range;
+    a.out_img = out_image; a.out_rng = out_range;
+    const dim3 block(kRemapTX, kRemapTY), grid(ceil_div(dst->W, kRemapTX), ceil_div(dst->H, kRemapTY));
+    if (mode == 0) k_remap<0><<<grid, block, 0, (cudaStream_t)stream>>>(a);
+    else k_remap<1><<<grid, block, 0, (cudaStream_t)stream>>>(a);
+    return last_error();
+}
+
+}  // namespace
+
+int sf_remap_pinhole(const sf_grid* dst, const float* R, int Hs, int Ws, const float* cam, const float* src_image,
+                     const float* src_range, float* out_image, float* out_range, void* stream)
+{
+    return remap_launch(0, dst, R, Hs, Ws, cam, src_image, src_range, out_image, out_range, stream);
+}
+
+int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const float* src_image,
+                      const float* src_range, float* out_image, float* out_range, void* stream)
+{
+    return remap_launch(1, dst, R, Hs, Ws, nullptr, src_image, src_range, out_image, out_range, stream);
+}
+
 int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const float* const* s1, float dt,
                    float* flow_out, float* invdepth_out, int check_finite, int* status, void* stream)
 {

@@ -16,6 +16,9 @@
 //                 the reconstruction of Eq. 26 and the level-1 outputs.
 //   k_reconstruct Eq. 26 for one level, plus the level-1 outputs (stage
 //                 entry point sf_reconstruct).
+//   k_remap       a pinhole camera frame or an equirectangular panorama
+//                 resampled onto the grid (the mapping step the paper times
+//                 with the filter).
 //   k_pack/k_unpack  interleaved float4 state <-> planar checkpoint layout.
 #pragma once
 
@@ -865,6 +868,87 @@ __global__ void __launch_bounds__(kThreads) k_reconstruct(ReconArgs a)
     if (a.check_finite && a.status) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, kStatusNonFinite);
     }
+}
+
+// --------------------------------------------------------------------------
+// remapping camera data onto the grid (readings R26, R27)
+// --------------------------------------------------------------------------
+
+struct RemapArgs {
+    int H, W;                  // grid
+    float gax, gbx, gay, gby;  // grid ray of pixel (i, j): (j gax + gbx, i gay + gby, 1)
+    float R[9];                // camera <- grid rotation, row-major
+    int Hs, Ws;                // source image
+    float cfx, cfy, ccx, ccy;  // pinhole source: intrinsics
+    const float* img;
+    const float* rng;          // may be null
+    float* out_img;
+    float* out_rng;            // may be null
+};
+
+constexpr int kRemapTX = 32, kRemapTY = 8;
+
+// bilinear brightness between pixel centres (replicated edges; columns wrap
+// when WRAP) and nearest-pixel range at continuous source coordinates (u, v)
+template <bool WRAP>
+__device__ __forceinline__ void remap_sample(const RemapArgs& a, float u, float v, float& Y, float& lam)
+{
+    const float p = u - 0.5f, q = v - 0.5f;
+    const float pf = floorf(p), qf = floorf(q);
+    const float fx = p - pf, fy = q - qf;
+    int j0 = (int)pf, i0 = (int)qf, j1 = j0 + 1, i1 = i0 + 1;
+    if (WRAP) {
+        j0 = j0 < 0 ? j0 + a.Ws : (j0 >= a.Ws ? j0 - a.Ws : j0);
+        j1 = j1 < 0 ? j1 + a.Ws : (j1 >= a.Ws ? j1 - a.Ws : j1);
+    } else {
+        j0 = clampi(j0, 0, a.Ws - 1);
+        j1 = clampi(j1, 0, a.Ws - 1);
+    }
+    i0 = clampi(i0, 0, a.Hs - 1);
+    i1 = clampi(i1, 0, a.Hs - 1);
+    const float* r0 = a.img + (size_t)i0 * a.Ws;
+    const float* r1 = a.img + (size_t)i1 * a.Ws;
+    const float y00 = __ldg(r0 + j0), y01 = __ldg(r0 + j1), y10 = __ldg(r1 + j0), y11 = __ldg(r1 + j1);
+    Y = (1.0f - fy) * fmaf(fx, y01 - y00, y00) + fy * fmaf(fx, y11 - y10, y10);
+    if (a.rng) {
+        int jn = (int)floorf(u);
+        const int in = clampi((int)floorf(v), 0, a.Hs - 1);
+        jn = WRAP ? (jn < 0 ? jn + a.Ws : (jn >= a.Ws ? jn - a.Ws : jn)) : clampi(jn, 0, a.Ws - 1);
+        lam = __ldg(a.rng + (size_t)in * a.Ws + jn);
+    }
+}
+
+// One grid pixel per thread, 32 x 8 thread blocks: each grid ray rotated into
+// the camera frame, projected (MODE 0: pinhole source; MODE 1:
+// equirectangular panorama), sampled; rays outside a pinhole source (or
+// behind it) get brightness 0 and range 0.
+template <int MODE>
+__global__ void __launch_bounds__(kRemapTX * kRemapTY) k_remap(RemapArgs a)
+{
+    const int j = blockIdx.x * kRemapTX + threadIdx.x;
+    const int i = blockIdx.y * kRemapTY + threadIdx.y;
+    if (i >= a.H || j >= a.W) return;
+    const float mx = fmaf((float)j, a.gax, a.gbx), my = fmaf((float)i, a.gay, a.gby);
+    const float dx = fmaf(a.R[0], mx, fmaf(a.R[1], my, a.R[2]));
+    const float dy = fmaf(a.R[3], mx, fmaf(a.R[4], my, a.R[5]));
+    const float dz = fmaf(a.R[6], mx, fmaf(a.R[7], my, a.R[8]));
+    float Y = 0.0f, lam = 0.0f;
+    if (MODE == 0) {
+        if (dz > 0.0f) {
+            const float u = fmaf(a.cfx, dx / dz, a.ccx), v = fmaf(a.cfy, dy / dz, a.ccy);
+            if (u >= 0.0f && u <= (float)a.Ws && v >= 0.0f && v <= (float)a.Hs) remap_sample<false>(a, u, v, Y, lam);
+        }
+    } else {
+        constexpr float kPi = 3.14159265358979f;
+        const float phi = atan2f(dx, dz);
+        const float theta = asinf(fminf(1.0f, fmaxf(-1.0f, -dy * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))))));
+        const float u = (phi + kPi) * (0.5f / kPi) * (float)a.Ws;
+        const float v = (0.5f * kPi - theta) * (1.0f / kPi) * (float)a.Hs;
+        remap_sample<true>(a, u, v, Y, lam);
+    }
+    const size_t o = (size_t)i * a.W + j;
+    a.out_img[o] = Y;
+    if (a.out_rng) a.out_rng[o] = lam;
 }
 
 // interleaved (s0, s1) float4 state <-> 8 planar float planes w(3) rho dw(3) Y

@@ -46,7 +46,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
-           "sf_batch_destroy"]
+           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect"]
 
 
 def lib():
@@ -77,6 +77,8 @@ def lib():
         L.sf_propagate.argtypes = [P(CGrid), i, i, f, vp, vp, vp, vp, vp, vp]
         L.sf_propagate_imu.argtypes = [P(CGrid), i, i, f, P(f), vp, vp, vp, vp, vp, vp]
         L.sf_set_motion.argtypes = [vp, P(f), P(f), vp]
+        L.sf_remap_pinhole.argtypes = [P(CGrid), P(f), i, i, P(f), vp, vp, vp, vp, vp]
+        L.sf_remap_equirect.argtypes = [P(CGrid), P(f), i, i, vp, vp, vp, vp, vp]
         L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
         L.sf_batch_buffers.argtypes = [vp, i, P(vp), P(vp), P(vp), P(vp)]
@@ -285,6 +287,23 @@ def reconstruct(grids, s0, s1, dt, flow_out=None, invdepth_out=None, check_finit
     p1 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s1])
     return _check(lib().sf_reconstruct(L, ga, p0, p1, float(dt), _ptr(flow_out), _ptr(invdepth_out),
                                        int(bool(check_finite)), _ptr(status), _stream(stream)), "sf_reconstruct")
+
+
+def remap_pinhole(dst: CGrid, R, cam, image, out_image, rng=None, out_range=None, stream=None):
+    """``sf_remap_pinhole``: a pinhole frame (device [Hs, Ws]) onto the grid ``dst``."""
+    Rm = (ctypes.c_float * 9)(*[float(x) for x in np.asarray(R, dtype=np.float64).reshape(9)])
+    K = (ctypes.c_float * 4)(*[float(x) for x in cam])
+    Hs, Ws = image.shape
+    return _check(lib().sf_remap_pinhole(ctypes.byref(dst), Rm, Hs, Ws, K, _ptr(image), _ptr(rng), _ptr(out_image),
+                                         _ptr(out_range), _stream(stream)), "sf_remap_pinhole")
+
+
+def remap_equirect(dst: CGrid, R, image, out_image, rng=None, out_range=None, stream=None):
+    """``sf_remap_equirect``: an equirectangular panorama (device [Hs, Ws]) onto the grid ``dst``."""
+    Rm = (ctypes.c_float * 9)(*[float(x) for x in np.asarray(R, dtype=np.float64).reshape(9)])
+    Hs, Ws = image.shape
+    return _check(lib().sf_remap_equirect(ctypes.byref(dst), Rm, Hs, Ws, _ptr(image), _ptr(rng), _ptr(out_image),
+                                          _ptr(out_range), _stream(stream)), "sf_remap_equirect")
 
 
 class Batch:

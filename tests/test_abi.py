@@ -113,3 +113,18 @@ def test_stage_entry_points_validate_arguments(lib):
                          None, None, None, None, None) == sf.EINVAL
     grids = (sf.CGrid * 1)(g)
     assert lib.sf_reconstruct(0, grids, None, None, ctypes.c_float(1.0), None, None, 0, None, None) == sf.EINVAL
+
+
+def test_remap_rejects_bad_arguments_without_touching_the_device(lib):
+    g = sf.grid(16, 16, 8.0, 8.0, 8.0, 8.0)
+    x = ctypes.c_void_p(256)                       # never dereferenced: rejected first
+    eye = (ctypes.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    bad = (ctypes.c_float * 9)(1, 0, 0, 0, float("nan"), 0, 0, 0, 1)
+    cam = (ctypes.c_float * 4)(8.0, 8.0, 8.0, 8.0)
+    nocam = (ctypes.c_float * 4)(0.0, 8.0, 8.0, 8.0)
+    assert lib.sf_remap_pinhole(ctypes.byref(g), bad, 16, 16, cam, x, None, x, None, None) == sf.EINVAL
+    assert lib.sf_remap_pinhole(ctypes.byref(g), eye, 16, 16, nocam, x, None, x, None, None) == sf.EINVAL
+    assert lib.sf_remap_pinhole(ctypes.byref(g), eye, 0, 16, cam, x, None, x, None, None) == sf.EINVAL
+    assert lib.sf_remap_pinhole(ctypes.byref(g), eye, 16, 16, cam, x, x, x, None, None) == sf.EINVAL
+    assert lib.sf_remap_equirect(ctypes.byref(g), eye, 16, -2, x, None, x, None, None) == sf.EINVAL
+    assert lib.sf_remap_equirect(None, eye, 16, 32, x, None, x, None, None) == sf.EINVAL
