@@ -359,6 +359,24 @@ int sf_remap_pinhole(const sf_grid* dst, const float* R, int Hs, int Ws, const f
 int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const float* src_image,
                       const float* src_range, float* out_image, float* out_range, void* stream);
 
+/* ----------------------------------------------------------------------
+ * Learned propagation surrogate (no counterpart in the paper: a small
+ * convolutional network trained on the plain propagation's own output).
+ * ---------------------------------------------------------------------- */
+
+/* One 3x3 convolution layer, stride 1, zero padding 1, on the tensor cores
+ * (BF16 operands, FP32 accumulation):
+ *   y[n,i,j,co] = act(bias[co] + sum_{dy,dx,ci} w[3 dy + dx][co][ci] x[n, i+dy-1, j+dx-1, ci])
+ * act = ReLU when relu != 0, else identity.  x: device N x H x W x Cin
+ * bfloat16 (NHWC); w: device 9 x Cout x Cin bfloat16; bias: device Cout
+ * float32 or NULL; y: device N x H x W x Cout bfloat16 or NULL; y32: the
+ * same in float32 or NULL (at least one of y, y32).  Cin and Cout are 16 or
+ * 32; pointers 16-byte aligned.  status (device int, may be NULL) gets bit 4
+ * if a bounded wait for the tensor cores gave up.  SF_EINVAL for bad
+ * shapes or pointers (checked before any device call). */
+int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w,
+               const float* bias, int relu, void* y, float* y32, int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -232,6 +232,27 @@ def remap_equirect(H, W, grid_K, R, image, rng=None):
 
 
 # --------------------------------------------------------------------------
+# propagation surrogate: one 3x3 convolution layer (plain definition)
+# --------------------------------------------------------------------------
+
+def conv3x3(x, w, b=None, relu=False):
+    """y[n, i, j, co] = act(b[co] + sum_{dy, dx, ci} w[3 dy + dx, co, ci] x[n, i + dy - 1, j + dx - 1, ci])
+    with zero padding, in float64.  x: [N, H, W, Cin]; w: [9, Cout, Cin]."""
+    x = np.asarray(x, dtype=np.float64); w = np.asarray(w, dtype=np.float64)
+    N, H, W, Cin = x.shape
+    Cout = w.shape[1]
+    xp = np.zeros((N, H + 2, W + 2, Cin))
+    xp[:, 1:H + 1, 1:W + 1] = x
+    y = np.zeros((N, H, W, Cout))
+    for dy in range(3):
+        for dx in range(3):
+            y += xp[:, dy:dy + H, dx:dx + W, :] @ w[3 * dy + dx].T
+    if b is not None:
+        y += np.asarray(b, dtype=np.float64)
+    return np.maximum(y, 0.0) if relu else y
+
+
+# --------------------------------------------------------------------------
 # whole filter
 # --------------------------------------------------------------------------
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "sf.h"
+#include "sf_conv.cuh"
 #include "sf_kernels.cuh"
 
 using namespace sfdev;
@@ -584,6 +585,7 @@ int engine_status(Engine& E)
     int s = 0;
     if (cudaMemcpy(&s, E.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SF_ECUDA;
     if (cudaMemset(E.status, 0, sizeof(int)) != cudaSuccess) return SF_ECUDA;
+    if (s & kStatusTimeout) return SF_ETIMEOUT;
     if (s & kStatusNonFinite) return SF_ENONFINITE;
     if (s & kStatusCfl) return SF_WARN_CFL;
     return SF_OK;
@@ -1147,6 +1149,33 @@ int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const 
                       const float* src_range, float* out_image, float* out_range, void* stream)
 {
     return remap_launch(1, dst, R, Hs, Ws, nullptr, src_image, src_range, out_image, out_range, stream);
+}
+
+int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w, const float* bias, int relu,
+               void* y, float* y32, int* status, void* stream)
+{
+    if (N < 1 || H < 1 || W < 1 || (Cin != 16 && Cin != 32) || (Cout != 16 && Cout != 32) || !x || !w ||
+        (!y && !y32))
+        return SF_EINVAL;
+    if (!aligned16(x) || !aligned16(w) || !aligned16(y) || !aligned16(y32)) return SF_EINVAL;
+    if ((double)N * H * W * (Cin > Cout ? Cin : Cout) > 2147483647.0) return SF_EINVAL;
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = N; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout;
+    a.x = (const __nv_bfloat16*)x;
+    a.w = (const __nv_bfloat16*)w;
+    a.bias = bias;
+    a.relu = relu != 0;
+    a.y = (__nv_bfloat16*)y;
+    a.y32 = y32;
+    a.tiles_x = ceil_div(W, kConvM);
+    a.n_tiles = N * H * a.tiles_x;
+    a.status = status;
+    const size_t smem = conv_smem_bytes(Cin, Cout);
+    if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
+    const int grid = std::min(a.n_tiles, 148 * 4);
+    k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
+    return last_error();
 }
 
 int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const float* const* s1, float dt,

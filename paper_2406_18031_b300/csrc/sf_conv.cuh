@@ -1,0 +1,249 @@
+// sf_conv.cuh -- 3x3 convolution layers of the propagation surrogate on the
+// 5th-generation tensor cores (tcgen05, sm_103a): BF16 operands staged in
+// shared memory, FP32 accumulators in tensor memory.
+//
+// Implicit GEMM per tile of 128 consecutive output pixels of one image row:
+// D[128 x Cout] = sum over the 9 taps of A_tap[128 x Cin] B_tap[Cin x Cout]
+// (K = 16 per instruction, 9 Cin / 16 instructions per tile).  The three
+// input rows the tile needs are staged once, "channel-chunk major": chunk c
+// (8 channels, 16 bytes) of slot p at  c * P * 16 + p * 16.  Any 8
+// consecutive slots of one chunk are then a core matrix (8 rows x 16 bytes,
+// rows 16 bytes apart), so the A operand of tap (dy, dx) is the same buffer
+// with its start moved by dx slots: no im2col copy.  Descriptors use the
+// no-swizzle K-major layout: leading byte offset = distance between the two
+// K-adjacent core matrices of an instruction (the next chunk, P * 16 bytes),
+// stride byte offset = distance between M-adjacent core matrices (8 slots,
+// 128 bytes).  The weights use the same layout with Cout rows.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "sf_device.cuh"
+
+namespace sfdev {
+
+constexpr int kConvM = 128;           // output pixels per tile (TMEM lanes)
+constexpr int kConvThreads = 128;     // 4 warps: warp w owns TMEM lanes 32w .. 32w + 31
+constexpr int kConvSlots = 136;       // staged pixels per row: 128 + 2 halo, rounded up
+constexpr int kConvTmemCols = 32;     // FP32 accumulator columns (Cout <= 32)
+constexpr int kConvSpinLimit = 1 << 22;
+
+struct ConvArgs {
+    int N, H, W, Cin, Cout;
+    const __nv_bfloat16* x;      // N x H x W x Cin
+    const __nv_bfloat16* w;      // 9 x Cout x Cin (tap-major, tap = 3 dy + dx)
+    const float* bias;           // Cout (may be null)
+    int relu;
+    __nv_bfloat16* y;            // N x H x W x Cout (bf16 output), or null
+    float* y32;                  // N x H x W x Cout (fp32 output), or null
+    int tiles_x;                 // ceil(W / 128)
+    int n_tiles;                 // N * H * tiles_x
+    int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
+};
+
+__host__ __device__ inline size_t conv_smem_bytes(int Cin, int Cout)
+{
+    const size_t a = (size_t)3 * (Cin / 8) * kConvSlots * 16;
+    const size_t b = (size_t)9 * (Cin / 8) * Cout * 16;
+    return a + b + 16;   // + the mbarrier (8 bytes, 8-aligned) and the TMEM address
+}
+
+// shared::cta address of a generic pointer into shared memory
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, leading and stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n, M = 128
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kConvM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < kConvSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// One CTA per group of tiles (persistent).  Every tile: stage its three input
+// rows, one thread issues the 9 Cin / 16 MMAs and commits them to an
+// mbarrier, every warp reads its 32 TMEM lanes (= pixels), adds the bias,
+// applies ReLU and stores the tile.
+__global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
+{
+    extern __shared__ __align__(16) unsigned char csm[];
+    const int C8 = a.Cin / 8;
+    const size_t a_bytes = (size_t)3 * C8 * kConvSlots * 16;
+    const size_t b_bytes = (size_t)9 * C8 * a.Cout * 16;
+    unsigned char* As = csm;
+    unsigned char* Bs = csm + a_bytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(csm + a_bytes + b_bytes);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights: B_tap[n][k] at tap * (C8 Cout 16) + chunk * (Cout 16) + n * 16
+    for (int idx = tid; idx < 9 * a.Cout * C8; idx += kConvThreads) {
+        const int c = idx % C8, n = (idx / C8) % a.Cout, tap = idx / (C8 * a.Cout);
+        const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.Cout + n) * a.Cin + 8 * c);
+        *reinterpret_cast<uint4*>(Bs + (size_t)tap * C8 * a.Cout * 16 + (size_t)c * a.Cout * 16 + n * 16) = v;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(kConvTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t idesc = umma_idesc_bf16(a.Cout);
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs), mb = smem_u32(mbar);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const int tx = t % a.tiles_x, row = t / a.tiles_x;
+        const int yy = row % a.H, nn = row / a.H;
+        const int x0 = tx * kConvM;
+        // stage rows yy - 1 .. yy + 1, columns x0 - 1 .. x0 + 134 (zero outside the image)
+        for (int idx = tid; idx < 3 * kConvSlots * C8; idx += kConvThreads) {
+            const int c = idx % C8, p = (idx / C8) % kConvSlots, dy = idx / (C8 * kConvSlots);
+            const int iy = yy + dy - 1, ix = x0 + p - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W && p < kConvM + 2)
+                v = *reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + iy) * a.W + ix) * a.Cin + 8 * c);
+            *reinterpret_cast<uint4*>(As + (size_t)dy * C8 * kConvSlots * 16 + (size_t)c * kConvSlots * 16 + p * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int first = 1;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
+                for (int s = 0; s < C8 / 2; ++s) {
+                    const uint32_t aa = a_base + (uint32_t)(dy * C8 * kConvSlots * 16 + 2 * s * kConvSlots * 16 + dx * 16);
+                    const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * s * a.Cout * 16);
+                    umma_bf16(tmem, umma_desc(aa, kConvSlots * 16, 128), umma_desc(bb, a.Cout * 16, 128), idesc,
+                              first ? 0 : 1);
+                    first = 0;
+                }
+            }
+            umma_commit(mb);
+        }
+        const bool done = mbar_wait(mb, phase);
+        if (!__syncthreads_and(done)) {   // every thread leaves together; the MMAs may still run
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: pixel x0 + 32 warp + lane
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+        const int px = x0 + 32 * warp + (tid & 31);
+        if (px < a.W) {
+            const size_t o = (((size_t)nn * a.H + yy) * a.W + px) * a.Cout;
+            float r[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                float u = v[k] + ((a.bias && k < a.Cout) ? a.bias[k] : 0.0f);
+                r[k] = a.relu ? fmaxf(u, 0.0f) : u;
+            }
+            if (a.y) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (8 * q >= a.Cout) break;
+                    uint4 pk;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(r[8 * q + 0], r[8 * q + 1]);
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(r[8 * q + 2], r[8 * q + 3]);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(r[8 * q + 4], r[8 * q + 5]);
+                    __nv_bfloat162 h3 = __floats2bfloat162_rn(r[8 * q + 6], r[8 * q + 7]);
+                    pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                    pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                    pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                    pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                    *reinterpret_cast<uint4*>(a.y + o + 8 * q) = pk;
+                }
+            }
+            if (a.y32) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (4 * q >= a.Cout) break;
+                    *reinterpret_cast<float4*>(a.y32 + o + 4 * q) =
+                        make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+                }
+            }
+        }
+        // the next tile restages the rows and overwrites TMEM
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0 && a.status) atomicOr(a.status, kStatusTimeout);
+        mbar_wait(mb, phase);             // give the MMAs in flight a second bounded wait
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kConvTmemCols)
+                     : "memory");
+    }
+}
+
+}  // namespace sfdev

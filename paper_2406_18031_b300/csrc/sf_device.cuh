@@ -24,6 +24,7 @@ namespace sfdev {
 // bits of the device status word
 constexpr int kStatusCfl = 1;
 constexpr int kStatusNonFinite = 2;
+constexpr int kStatusTimeout = 4;    // a bounded wait on the device gave up
 
 // flags (same values as the public SF_* flags)
 constexpr int kDominantLiteral = 1;

@@ -46,7 +46,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
-           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect"]
+           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3"]
 
 
 def lib():
@@ -78,6 +78,7 @@ def lib():
         L.sf_propagate_imu.argtypes = [P(CGrid), i, i, f, P(f), vp, vp, vp, vp, vp, vp]
         L.sf_set_motion.argtypes = [vp, P(f), P(f), vp]
         L.sf_remap_pinhole.argtypes = [P(CGrid), P(f), i, i, P(f), vp, vp, vp, vp, vp]
+        L.sf_conv3x3.argtypes = [i, i, i, i, i, vp, vp, vp, i, vp, vp, vp, vp]
         L.sf_remap_equirect.argtypes = [P(CGrid), P(f), i, i, vp, vp, vp, vp, vp]
         L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
@@ -107,14 +108,14 @@ def _check(code, what):
     return code
 
 
-def _ptr(t):
+def _ptr(t, itemsize=4):
     """Device pointer of a CUDA tensor (or None -> NULL)."""
     if t is None:
         return None
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
-    if not t.is_contiguous() or t.dtype.itemsize != 4:
-        raise ValueError("expected a contiguous 32-bit tensor")
+    if not t.is_contiguous() or t.dtype.itemsize != itemsize:
+        raise ValueError(f"expected a contiguous {8 * itemsize}-bit tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -304,6 +305,15 @@ def remap_equirect(dst: CGrid, R, image, out_image, rng=None, out_range=None, st
     Hs, Ws = image.shape
     return _check(lib().sf_remap_equirect(ctypes.byref(dst), Rm, Hs, Ws, _ptr(image), _ptr(rng), _ptr(out_image),
                                           _ptr(out_range), _stream(stream)), "sf_remap_equirect")
+
+
+def conv3x3(x, w, bias=None, relu=False, y=None, y32=None, status=None, stream=None):
+    """``sf_conv3x3``: x [N, H, W, Cin] and w [9, Cout, Cin] bfloat16 CUDA tensors; writes y
+    (bfloat16) and/or y32 (float32), [N, H, W, Cout]."""
+    N, H, W, Cin = x.shape
+    Cout = w.shape[1]
+    return _check(lib().sf_conv3x3(N, H, W, Cin, Cout, _ptr(x, 2), _ptr(w, 2), _ptr(bias), int(bool(relu)),
+                                   _ptr(y, 2), _ptr(y32), _ptr(status), _stream(stream)), "sf_conv3x3")
 
 
 class Batch:

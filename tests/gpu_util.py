@@ -81,3 +81,15 @@ def oracle_level_data(image, rng_, levels, lambda_ref=1.0):
         Y, rho, valid = oracle.downsample(Y, rho, valid)
         out.append((Y, rho, valid))
     return out
+
+
+def bf16_round(a):
+    """float32 -> the nearest bfloat16 (ties to even), returned as float32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def bf16_bits(a):
+    """float32 values exactly representable in bfloat16 -> their uint16 bit patterns."""
+    return (np.ascontiguousarray(a, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)

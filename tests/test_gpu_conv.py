@@ -1,0 +1,65 @@
+"""Parity of the tensor-core 3x3 convolution (sf_conv3x3) with the oracle.
+
+Inputs and weights are bfloat16 values; the oracle convolves exactly those
+values in float64.  FP32 accumulation of 9 Cin bf16 products: the float32
+output is within 1e-5 of the sum of |x w| per output (about 200 float32
+roundings of a partial sum); the bfloat16 output within one bf16 ulp of the
+oracle's value rounded to bfloat16, plus that float32 error (the float32 sum
+may sit on the other side of a rounding boundary, or of zero under ReLU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_18031_b300 import sf
+from tests import gpu_util as gu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _bf16_tensor(a):
+    bits = gu.bf16_bits(a).astype(np.int16)
+    return torch.from_numpy(bits).cuda().view(torch.bfloat16)
+
+
+def _case(N, H, W, Cin, Cout, relu, seed):
+    rng = np.random.default_rng(seed)
+    x = gu.bf16_round(rng.normal(size=(N, H, W, Cin)).astype(np.float32))
+    w = gu.bf16_round((rng.normal(size=(9, Cout, Cin)) / np.sqrt(9 * Cin)).astype(np.float32))
+    b = rng.normal(size=Cout).astype(np.float32) * 0.1
+    y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    y32 = torch.empty((N, H, W, Cout), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sf.conv3x3(_bf16_tensor(x), _bf16_tensor(w), torch.from_numpy(b).cuda(), relu, y, y32, st)
+    torch.cuda.synchronize()
+    ref = oracle.conv3x3(x, w, b, relu)
+    mag = oracle.conv3x3(np.abs(x), np.abs(w), np.abs(b))
+    got32 = y32.cpu().numpy()
+    assert np.all(np.abs(got32 - ref) <= 1e-5 * mag + 1e-7), np.abs(got32 - ref).max()
+    got = y.float().cpu().numpy()
+    # one bf16 ulp of the value plus the float32 accumulation error (which can
+    # also move a value across zero under ReLU)
+    tol = np.abs(gu.bf16_round(ref.astype(np.float32))) * 2.0 ** -7 + 1e-5 * mag + 1e-7
+    assert np.all(np.abs(got - gu.bf16_round(ref.astype(np.float32))) <= tol)
+    assert int(st.item()) == 0
+
+
+@pytest.mark.parametrize("Cin,Cout", [(16, 16), (16, 32), (32, 16), (32, 32)])
+@pytest.mark.parametrize("relu", [False, True])
+def test_conv_small_ragged(Cin, Cout, relu):
+    # two tiles per row, the second 72 pixels wide
+    _case(2, 5, 200, Cin, Cout, relu, seed=Cin + Cout + relu)
+
+
+def test_conv_larger_frame():
+    _case(1, 64, 512, 32, 32, True, seed=3)
+
+
+def test_conv_narrow_image():
+    _case(3, 9, 37, 16, 32, False, seed=4)
