@@ -377,6 +377,51 @@ int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const 
 int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w,
                const float* bias, int relu, void* y, float* y32, int* status, void* stream);
 
+/* The surrogate network: 4 such layers, 16 -> 32 -> 32 -> 32 -> 16 channels,
+ * ReLU after the first three.  Input features of a pixel of the top level:
+ * w / (4 dmu) (3 channels, px/frame over 4), rho, eta_x, eta_y, 10 zeros;
+ * output channels 0..3: the change over one frame in the same units, so the
+ * prediction is w + 4 dmu o[0..2], rho + o[3].  It replaces the N
+ * sub-iterations of the top-level propagation (Sec. 4.6) once trained on
+ * (state, plain prediction) pairs.  Parameters: per layer the weights
+ * 9 x Cout x Cin (tap-major) then Cout biases, FP32 master copy; BF16 copies
+ * feed the tensor cores. */
+typedef struct sf_surrogate sf_surrogate;
+
+/* Seeded He-normal initialisation (a small last layer: nearly no change). */
+int sf_surrogate_create(unsigned long long seed, sf_surrogate** out);
+void sf_surrogate_destroy(sf_surrogate* s);
+/* Number of FP32 parameters (a negative code for NULL). */
+int sf_surrogate_num_params(const sf_surrogate* s);
+/* Copy the FP32 parameters to (set = 0) or from (set != 0) host memory;
+ * setting rebuilds the BF16 copies; non-finite values give SF_EINVAL. */
+int sf_surrogate_params(sf_surrogate* s, float* host, int set);
+/* Gradient of the last training step's loss (FP32, parameter layout). */
+int sf_surrogate_grads(sf_surrogate* s, float* host);
+/* Predict: s0 = n frames of the grid g's top-level state (device
+ * n x H x W float4 (w_x, w_y, w_z, rho), w in rad/frame) -> p0 (same layout).
+ * Activation buffers grow on demand (about 450 bytes per pixel). */
+int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0,
+                         void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the mean squared error, over
+ * the 4 used output channels in the network's units, between the
+ * prediction from s0 and `target` (the plain propagation's p0 of the same
+ * states).  *loss_out (host, may be NULL) receives the loss before the step
+ * (the call then waits for the stream).  SF_ETIMEOUT if a tensor-core wait
+ * gave up. */
+int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const float* s0,
+                            const float* target, float lr, float* loss_out, void* stream);
+/* The surrogate as the top-level prediction with its fallback: p0 = the
+ * surrogate's prediction of s0, checked against one plain step (the plain
+ * propagation with N = 1): if the largest flow difference over all pixels
+ * and frames exceeds threshold_px (px/frame; NaN always does), p0 is
+ * recomputed by the plain propagation with N sub-iterations.
+ * *residual_px and *used_plain (host, may be NULL) receive the largest
+ * difference and whether the fallback ran.  Waits for the stream (the
+ * decision is taken on the host). */
+int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, const float* s0, float* p0,
+                           float threshold_px, float* residual_px, int* used_plain, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,11 +18,13 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <random>
 #include <vector>
 
 #include "sf.h"
 #include "sf_conv.cuh"
 #include "sf_kernels.cuh"
+#include "sf_surrogate.cuh"
 
 using namespace sfdev;
 
@@ -1176,6 +1178,305 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     const int grid = std::min(a.n_tiles, 148 * 4);
     k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
     return last_error();
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: the learned propagation surrogate
+// ---------------------------------------------------------------------------
+
+struct sf_surrogate {
+    static constexpr int kL = 4;
+    const int cin[kL] = {kSurrIn, kSurrHidden, kSurrHidden, kSurrHidden};
+    const int cout[kL] = {kSurrHidden, kSurrHidden, kSurrHidden, kSurrOut};
+    // parameters and optimiser state: per layer w (9 cout cin) then b (cout)
+    float* param = nullptr;     // FP32 master copy
+    float* grad = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    size_t off[kL + 1] = {};
+    __nv_bfloat16* w16[kL] = {};
+    __nv_bfloat16* w16t[kL] = {};
+    void* wblock = nullptr;
+    // activations, sized for cap pixels
+    size_t cap = 0;
+    void* ablock = nullptr;
+    __nv_bfloat16 *x0 = nullptr, *a[3] = {}, *dy = nullptr, *dA = nullptr, *dB = nullptr;
+    float* y32 = nullptr;
+    float* loss = nullptr;
+    int* status = nullptr;
+    int steps = 0;
+};
+
+namespace {
+
+inline size_t layer_params(int cin, int cout) { return (size_t)9 * cin * cout + cout; }
+
+void surrogate_free(sf_surrogate* s)
+{
+    if (!s) return;
+    cudaFree(s->wblock);
+    cudaFree(s->ablock);
+    delete s;
+}
+
+int surrogate_capacity(sf_surrogate* s, size_t px)
+{
+    if (px <= s->cap) return SF_OK;
+    cudaFree(s->ablock);
+    s->ablock = nullptr;
+    s->cap = 0;
+    const size_t b16 = px * 2;   // bytes per channel (bf16)
+    const size_t bytes = b16 * kSurrIn + 3 * b16 * kSurrHidden + b16 * kSurrOut + 2 * b16 * kSurrHidden +
+                         px * kSurrOut * sizeof(float) + 256;
+    if (cudaMalloc(&s->ablock, bytes) != cudaSuccess) { s->ablock = nullptr; return SF_ENOMEM; }
+    unsigned char* p = (unsigned char*)s->ablock;
+    auto take = [&](size_t n) { unsigned char* q = p; p += (n + 255) & ~(size_t)255; return q; };
+    s->x0 = (__nv_bfloat16*)take(b16 * kSurrIn);
+    for (int k = 0; k < 3; ++k) s->a[k] = (__nv_bfloat16*)take(b16 * kSurrHidden);
+    s->dy = (__nv_bfloat16*)take(b16 * kSurrOut);
+    s->dA = (__nv_bfloat16*)take(b16 * kSurrHidden);
+    s->dB = (__nv_bfloat16*)take(b16 * kSurrHidden);
+    s->y32 = (float*)take(px * kSurrOut * sizeof(float));
+    s->cap = px;
+    return SF_OK;
+}
+
+int conv_launch(const sf_surrogate* s, int N, int H, int W, int cin, int cout, const __nv_bfloat16* x,
+                const __nv_bfloat16* w, const float* b, int relu, __nv_bfloat16* y, float* y32, cudaStream_t st)
+{
+    return sf_conv3x3(N, H, W, cin, cout, x, w, b, relu, y, y32, s->status, st);
+}
+
+inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 148 * 8); }
+
+// features, the four layers (the three hidden activations kept for the
+// backward pass), FP32 output in y32
+int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, cudaStream_t st)
+{
+    const size_t px = (size_t)n * g.H * g.W;
+    k_surr_features<<<grid_stride_blocks(px), 256, 0, st>>>(g, n, s0, s->x0);
+    int r = last_error();
+    const __nv_bfloat16* in = s->x0;
+    for (int l = 0; l < 3 && !r; ++l) {
+        r = conv_launch(s, n, g.H, g.W, s->cin[l], s->cout[l], in, s->w16[l], s->param + s->off[l] + 9 * s->cin[l] *
+                        s->cout[l], 1, s->a[l], nullptr, st);
+        in = s->a[l];
+    }
+    if (!r)
+        r = conv_launch(s, n, g.H, g.W, s->cin[3], s->cout[3], in, s->w16[3],
+                        s->param + s->off[3] + 9 * s->cin[3] * s->cout[3], 0, nullptr, s->y32, st);
+    return r;
+}
+
+}  // namespace
+
+int sf_surrogate_create(unsigned long long seed, sf_surrogate** out)
+{
+    if (!out) return SF_EINVAL;
+    *out = nullptr;
+    sf_surrogate* s = new (std::nothrow) sf_surrogate();
+    if (!s) return SF_ENOMEM;
+    for (int l = 0; l < sf_surrogate::kL; ++l) s->off[l + 1] = s->off[l] + layer_params(s->cin[l], s->cout[l]);
+    const size_t np = s->off[sf_surrogate::kL];
+    size_t n16 = 0;
+    for (int l = 0; l < sf_surrogate::kL; ++l) n16 += 9 * (size_t)s->cin[l] * s->cout[l];
+    const size_t bytes = 4 * np * sizeof(float) + 2 * n16 * sizeof(__nv_bfloat16) + 2 * sizeof(float) + 256 * 12;
+    if (cudaMalloc(&s->wblock, bytes) != cudaSuccess) { s->wblock = nullptr; surrogate_free(s); return SF_ENOMEM; }
+    unsigned char* p = (unsigned char*)s->wblock;
+    auto take = [&](size_t nb) { unsigned char* q = p; p += (nb + 255) & ~(size_t)255; return q; };
+    s->param = (float*)take(np * sizeof(float));
+    s->grad = (float*)take(np * sizeof(float));
+    s->m1 = (float*)take(np * sizeof(float));
+    s->m2 = (float*)take(np * sizeof(float));
+    for (int l = 0; l < sf_surrogate::kL; ++l) {
+        s->w16[l] = (__nv_bfloat16*)take(9 * (size_t)s->cin[l] * s->cout[l] * 2);
+        s->w16t[l] = (__nv_bfloat16*)take(9 * (size_t)s->cin[l] * s->cout[l] * 2);
+    }
+    s->loss = (float*)take(sizeof(float));
+    s->status = (int*)take(sizeof(int));
+    // He-normal weights over the used inputs, zero biases, a small last layer
+    // (the untrained network predicts nearly no change)
+    std::vector<float> h(np, 0.0f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.0f, 1.0f);
+    const int used_in[sf_surrogate::kL] = {6, kSurrHidden, kSurrHidden, kSurrHidden};
+    for (int l = 0; l < sf_surrogate::kL; ++l) {
+        const float sd = std::sqrt(2.0f / (9.0f * used_in[l])) * (l == sf_surrogate::kL - 1 ? 0.1f : 1.0f);
+        for (size_t k = 0; k < 9 * (size_t)s->cin[l] * s->cout[l]; ++k) {
+            const int ci = (int)(k % s->cin[l]);
+            h[s->off[l] + k] = ci < used_in[l] ? sd * nd(rng) : 0.0f;
+        }
+    }
+    int r = cudaMemcpy(s->param, h.data(), np * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaMemset(s->m1, 0, np * sizeof(float)) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaMemset(s->m2, 0, np * sizeof(float)) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaMemset(s->status, 0, sizeof(int)) == cudaSuccess ? SF_OK : SF_ECUDA;
+    for (int l = 0; l < sf_surrogate::kL && !r; ++l) {
+        k_weights_bf16<<<64, 256>>>(s->cin[l], s->cout[l], s->param + s->off[l], s->w16[l], s->w16t[l]);
+        r = last_error();
+    }
+    if (!r) r = cudaDeviceSynchronize() == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (r) { surrogate_free(s); return r; }
+    *out = s;
+    return SF_OK;
+}
+
+void sf_surrogate_destroy(sf_surrogate* s) { surrogate_free(s); }
+
+int sf_surrogate_num_params(const sf_surrogate* s)
+{
+    if (!s) return SF_EINVAL;
+    return (int)s->off[sf_surrogate::kL];
+}
+
+int sf_surrogate_params(sf_surrogate* s, float* host, int set)
+{
+    if (!s || !host) return SF_EINVAL;
+    const size_t np = s->off[sf_surrogate::kL];
+    if (!set) return cudaMemcpy(host, s->param, np * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? SF_OK : SF_ECUDA;
+    for (size_t k = 0; k < np; ++k)
+        if (!std::isfinite(host[k])) return SF_EINVAL;
+    if (cudaMemcpy(s->param, host, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return SF_ECUDA;
+    for (int l = 0; l < sf_surrogate::kL; ++l) {
+        k_weights_bf16<<<64, 256>>>(s->cin[l], s->cout[l], s->param + s->off[l], s->w16[l], s->w16t[l]);
+        if (last_error()) return SF_ECUDA;
+    }
+    return cudaDeviceSynchronize() == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0, void* stream)
+{
+    if (!s || !g || g->H < 1 || g->W < 1 || n < 1 || !s0 || !p0 || !aligned16(s0) || !aligned16(p0)) return SF_EINVAL;
+    const size_t px = (size_t)n * g->H * g->W;
+    if (px * kSurrHidden > 2147483647ull) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = surrogate_capacity(s, px);
+    const Grid gg = make_grid(*g);
+    if (!r) r = surrogate_forward(s, gg, n, (const float4*)s0, st);
+    if (!r) {
+        k_surr_head<<<grid_stride_blocks(px), 256, 0, st>>>(gg, n, (const float4*)s0, s->y32, (float4*)p0);
+        r = last_error();
+    }
+    return r;
+}
+
+int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const float* s0, const float* target, float lr,
+                            float* loss_out, void* stream)
+{
+    if (!s || !g || g->H < 1 || g->W < 1 || n < 1 || !s0 || !target || !aligned16(s0) || !aligned16(target) ||
+        !(lr >= 0.0f) || !std::isfinite(lr))
+        return SF_EINVAL;
+    const size_t px = (size_t)n * g->H * g->W;
+    if (px * kSurrHidden > 2147483647ull) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = surrogate_capacity(s, px);
+    const Grid gg = make_grid(*g);
+    const size_t np = s->off[sf_surrogate::kL];
+    if (!r) r = surrogate_forward(s, gg, n, (const float4*)s0, st);
+    if (!r) r = cudaMemsetAsync(s->loss, 0, sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) r = cudaMemsetAsync(s->grad, 0, np * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (!r) {
+        k_surr_loss_grad<<<grid_stride_blocks(px), 256, 0, st>>>(gg, n, (const float4*)s0, (const float4*)target,
+                                                                   s->y32, s->dy, 1.0f / (4.0f * (float)px), s->loss);
+        r = last_error();
+    }
+    // backward: dy of layer l is `d`, its input activation `in`
+    const __nv_bfloat16* d = s->dy;
+    __nv_bfloat16* bufs[2] = {s->dA, s->dB};
+    const int wg_blocks = std::min(n * g->H * ((g->W + 127) / 128), 148 * 2);
+    for (int l = sf_surrogate::kL - 1; l >= 0 && !r; --l) {
+        const __nv_bfloat16* in = l == 0 ? s->x0 : s->a[l - 1];
+        const size_t wsm = wgrad_smem_bytes(s->cin[l], s->cout[l]);
+        if (set_smem_attr((const void*)k_wgrad, wsm)) { r = SF_ECUDA; break; }
+        k_wgrad<<<wg_blocks, kWgThreads, wsm, st>>>(n, g->H, g->W, s->cin[l], s->cout[l], in, d,
+                                                    s->grad + s->off[l], s->grad + s->off[l] + 9 * s->cin[l] * s->cout[l]);
+        r = last_error();
+        if (r || l == 0) break;
+        __nv_bfloat16* dx = bufs[l & 1];
+        r = conv_launch(s, n, g->H, g->W, s->cout[l], s->cin[l], d, s->w16t[l], nullptr, 0, dx, nullptr, st);
+        if (r) break;
+        k_relu_mask<<<grid_stride_blocks(px * s->cin[l]), 256, 0, st>>>(px * s->cin[l], dx, s->a[l - 1]);
+        r = last_error();
+        d = dx;
+    }
+    // Adam
+    if (!r) {
+        s->steps++;
+        AdamArgs h;
+        h.lr = lr; h.beta1 = 0.9f; h.beta2 = 0.999f; h.eps = 1e-8f;
+        h.c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)s->steps)));
+        h.c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)s->steps)));
+        for (int l = 0; l < sf_surrogate::kL && !r; ++l) {
+            const size_t nw = 9 * (size_t)s->cin[l] * s->cout[l];
+            float* base = s->param + s->off[l];
+            k_adam_layer<<<64, 256, 0, st>>>(s->cin[l], s->cout[l], h, base, s->grad + s->off[l], s->m1 + s->off[l],
+                                             s->m2 + s->off[l], base + nw, s->grad + s->off[l] + nw,
+                                             s->m1 + s->off[l] + nw, s->m2 + s->off[l] + nw, s->w16[l], s->w16t[l]);
+            r = last_error();
+        }
+    }
+    if (!r && loss_out) {
+        float sum = 0.0f;
+        r = cudaMemcpyAsync(&sum, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+        if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+        *loss_out = sum / (4.0f * (float)px);
+    }
+    if (!r) {
+        int stv = 0;
+        if (cudaMemcpyAsync(&stv, s->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SF_ECUDA;
+        if (stv & kStatusTimeout) return SF_ETIMEOUT;
+    }
+    return r;
+}
+
+int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, const float* s0, float* p0,
+                           float threshold_px, float* residual_px, int* used_plain, void* stream)
+{
+    if (!s || !g || g->H < 1 || g->W < 1 || n < 1 || N < 1 || !s0 || !p0 || !aligned16(s0) || !aligned16(p0) ||
+        !(threshold_px >= 0.0f))
+        return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t px = (size_t)n * g->H * g->W;
+    const Grid gg = make_grid(*g);
+    // the surrogate's prediction, then one plain step (N = 1) of every frame
+    int r = sf_surrogate_forward(s, g, n, s0, p0, stream);
+    float4* one = nullptr;
+    unsigned* dmax = nullptr;
+    if (!r && cudaMallocAsync((void**)&one, px * sizeof(float4) + 256, st) != cudaSuccess) r = SF_ENOMEM;
+    if (!r) {
+        dmax = (unsigned*)(one + px);
+        r = cudaMemsetAsync(dmax, 0, sizeof(unsigned), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    }
+    const size_t frame = (size_t)g->H * g->W;
+    for (int k = 0; k < n && !r; ++k)
+        r = sf_propagate(g, 1, 0, 1.0f, s0 + 4 * frame * k, nullptr, (float*)(one + frame * k), nullptr, nullptr, stream);
+    if (!r) {
+        k_surr_maxdiff<<<grid_stride_blocks(px), 256, 0, st>>>(gg, n, (const float4*)p0, one, dmax);
+        r = last_error();
+    }
+    unsigned bits = 0;
+    if (!r) r = cudaMemcpyAsync(&bits, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (one) cudaFreeAsync(one, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (r) return r;
+    float res;
+    std::memcpy(&res, &bits, sizeof(res));
+    if (residual_px) *residual_px = res;
+    const int fallback = !(res <= threshold_px);
+    if (used_plain) *used_plain = fallback;
+    // the fallback: the plain propagation with the full N sub-iterations
+    for (int k = 0; k < n && fallback && !r; ++k)
+        r = sf_propagate(g, N, 0, 1.0f, s0 + 4 * frame * k, nullptr, p0 + 4 * frame * k, nullptr, nullptr, stream);
+    return r;
+}
+
+int sf_surrogate_grads(sf_surrogate* s, float* host)
+{
+    if (!s || !host) return SF_EINVAL;
+    return cudaMemcpy(host, s->grad, s->off[sf_surrogate::kL] * sizeof(float), cudaMemcpyDeviceToHost) ==
+                   cudaSuccess ? SF_OK : SF_ECUDA;
 }
 
 int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const float* const* s1, float dt,

@@ -1,0 +1,228 @@
+// sf_surrogate.cuh -- the learned propagation surrogate: a 4-layer 3x3
+// convolutional network (16 -> 32 -> 32 -> 32 -> 16 channels, BF16
+// activations and weights, FP32 accumulation on the tensor cores) that maps
+// the top-level state (w, rho) of one frame to its prediction for the next,
+// trained on pairs that the plain propagation produces.  The convolutions are
+// k_conv3x3 (forward, and backward-data with flipped, transposed weights);
+// this file holds the per-pixel feature and head kernels, the loss gradient,
+// the weight gradient, the ReLU mask and the Adam step.
+//
+// Features of a pixel: w / (4 dmu) (3, px/frame over 4), rho, eta_x, eta_y,
+// and 10 zero channels.  Output channels 0..3 are the change over one frame
+// in the same units: w' = w + 4 dmu o[0..2], rho' = rho + o[3].
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "sf_device.cuh"
+
+namespace sfdev {
+
+constexpr int kSurrIn = 16;        // input channels (6 used)
+constexpr int kSurrHidden = 32;
+constexpr int kSurrOut = 16;       // output channels (4 used)
+constexpr float kSurrFlowScale = 4.0f;
+
+__device__ __forceinline__ float pixel_dmu(const Geo& g) { return g.dd * sqrtf(g.omx2); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// state (w, rho) of n frames -> BF16 features (16 channels)
+__global__ void k_surr_features(Grid g, int n, const float4* __restrict__ s0, __nv_bfloat16* __restrict__ x0)
+{
+    const size_t hw = (size_t)g.H * g.W, total = hw * n;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(p % hw), i = q / g.W, j = q % g.W;
+        const Geo geo = pixel_geometry(g, i, j);
+        const float s = 1.0f / (kSurrFlowScale * pixel_dmu(geo));
+        const float4 f = s0[p];
+        uint4* o = reinterpret_cast<uint4*>(x0 + p * kSurrIn);
+        o[0] = make_uint4(pack_bf16x2(f.x * s, f.y * s), pack_bf16x2(f.z * s, f.w), pack_bf16x2(geo.ex, geo.ey), 0u);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// network output (FP32, 16 channels) + state -> predicted state
+__global__ void k_surr_head(Grid g, int n, const float4* __restrict__ s0, const float* __restrict__ y32,
+                            float4* __restrict__ p0)
+{
+    const size_t hw = (size_t)g.H * g.W, total = hw * n;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(p % hw), i = q / g.W, j = q % g.W;
+        const float d = kSurrFlowScale * pixel_dmu(pixel_geometry(g, i, j));
+        const float4 f = s0[p];
+        const float4 o = *reinterpret_cast<const float4*>(y32 + p * kSurrOut);
+        p0[p] = make_float4(fmaf(d, o.x, f.x), fmaf(d, o.y, f.y), fmaf(d, o.z, f.z), f.w + o.w);
+    }
+}
+
+// Mean squared error over the 4 used output channels against the target
+// prediction (in the network's units) and its gradient dy (BF16, 16
+// channels, zero in the unused ones); the sum of squares goes to *loss.
+__global__ void k_surr_loss_grad(Grid g, int n, const float4* __restrict__ s0, const float4* __restrict__ target,
+                                 const float* __restrict__ y32, __nv_bfloat16* __restrict__ dy, float scale,
+                                 float* __restrict__ loss)
+{
+    const size_t hw = (size_t)g.H * g.W, total = hw * n;
+    float acc = 0.0f;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(p % hw), i = q / g.W, j = q % g.W;
+        const float inv = 1.0f / (kSurrFlowScale * pixel_dmu(pixel_geometry(g, i, j)));
+        const float4 f = s0[p], t = target[p];
+        const float4 o = *reinterpret_cast<const float4*>(y32 + p * kSurrOut);
+        const float e0 = o.x - (t.x - f.x) * inv, e1 = o.y - (t.y - f.y) * inv, e2 = o.z - (t.z - f.z) * inv;
+        const float e3 = o.w - (t.w - f.w);
+        acc += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+        uint4* d = reinterpret_cast<uint4*>(dy + p * kSurrOut);
+        d[0] = make_uint4(pack_bf16x2(2.0f * scale * e0, 2.0f * scale * e1),
+                          pack_bf16x2(2.0f * scale * e2, 2.0f * scale * e3), 0u, 0u);
+        d[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// da *= (a > 0): the ReLU of the layer whose output was a
+__global__ void k_relu_mask(size_t n, __nv_bfloat16* __restrict__ da, const __nv_bfloat16* __restrict__ a)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(a[k]) > 0.0f)) da[k] = __float2bfloat16(0.0f);
+}
+
+// Weight and bias gradients of a 3x3 layer: dW[tap][co][ci] += sum over
+// pixels of dy[p][co] x[p + off(tap)][ci] (zero padding), db[co] += sum dy.
+// Tiles of 128 pixels of one row; a CTA walks several tiles, each thread
+// keeps its outputs (tap, co, ci) in registers and adds them to global
+// memory once.
+constexpr int kWgThreads = 256;
+constexpr int kWgPerThread = 9 * 32 * 32 / kWgThreads;   // 36 outputs per thread at most
+
+__host__ __device__ inline size_t wgrad_smem_bytes(int Cin, int Cout)
+{
+    return (size_t)(3 * 130 * Cin + 128 * Cout) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kWgThreads) k_wgrad(int N, int H, int W, int Cin, int Cout,
+                                                     const __nv_bfloat16* __restrict__ x,
+                                                     const __nv_bfloat16* __restrict__ dy, float* __restrict__ dW,
+                                                     float* __restrict__ db)
+{
+    extern __shared__ float wsm[];
+    float* xs = wsm;                       // [3][130][Cin]
+    float* ys = wsm + 3 * 130 * Cin;       // [128][Cout]
+    const int tid = threadIdx.x;
+    const int n_out = 9 * Cout * Cin;
+    float acc[kWgPerThread];
+#pragma unroll
+    for (int k = 0; k < kWgPerThread; ++k) acc[k] = 0.0f;
+    float bacc = 0.0f;
+    const int tiles_x = (W + 127) / 128, n_tiles = N * H * tiles_x;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int tx = t % tiles_x, row = t / tiles_x, yy = row % H, nn = row / H, x0 = tx * 128;
+        __syncthreads();
+        for (int idx = tid; idx < 3 * 130 * Cin; idx += kWgThreads) {
+            const int c = idx % Cin, p = (idx / Cin) % 130, r = idx / (Cin * 130);
+            const int iy = yy + r - 1, ix = x0 + p - 1;
+            float v = 0.0f;
+            if (iy >= 0 && iy < H && ix >= 0 && ix < W)
+                v = __bfloat162float(x[(((size_t)nn * H + iy) * W + ix) * Cin + c]);
+            xs[(r * 130 + p) * Cin + c] = v;
+        }
+        for (int idx = tid; idx < 128 * Cout; idx += kWgThreads) {
+            const int c = idx % Cout, p = idx / Cout, ix = x0 + p;
+            ys[p * Cout + c] = ix < W ? __bfloat162float(dy[(((size_t)nn * H + yy) * W + ix) * Cout + c]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kWgPerThread; ++k) {
+            const int o = tid + k * kWgThreads;
+            if (o < n_out) {
+                const int ci = o % Cin, co = (o / Cin) % Cout, tap = o / (Cin * Cout);
+                const int r = tap / 3, dx = tap % 3;
+                float s = 0.0f;
+                const float* xr = xs + (r * 130 + dx) * Cin + ci;
+                const float* yr = ys + co;
+                for (int p = 0; p < 128; ++p) s = fmaf(yr[p * Cout], xr[p * Cin], s);
+                acc[k] += s;
+            }
+        }
+        if (tid < Cout)
+            for (int p = 0; p < 128; ++p) bacc += ys[p * Cout + tid];
+    }
+#pragma unroll
+    for (int k = 0; k < kWgPerThread; ++k) {
+        const int o = tid + k * kWgThreads;
+        if (o < n_out) atomicAdd(dW + o, acc[k]);
+    }
+    if (tid < Cout) atomicAdd(db + tid, bacc);
+}
+
+// Adam on one layer's FP32 master weights and biases; writes the BF16
+// forward weights w16[tap][co][ci] and the backward-data weights
+// w16t[tap][ci][co] = w[8 - tap][co][ci] (flipped taps, swapped channels).
+struct AdamArgs {
+    float lr, beta1, beta2, eps, c1, c2;   // c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)
+};
+
+__global__ void k_adam_layer(int Cin, int Cout, AdamArgs h, float* __restrict__ w, const float* __restrict__ gw,
+                             float* __restrict__ mw, float* __restrict__ vw, float* __restrict__ b,
+                             const float* __restrict__ gb, float* __restrict__ mb, float* __restrict__ vb,
+                             __nv_bfloat16* __restrict__ w16, __nv_bfloat16* __restrict__ w16t)
+{
+    const int nw = 9 * Cout * Cin;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nw + Cout; k += gridDim.x * blockDim.x) {
+        float *p, *m, *v;
+        float gr;
+        if (k < nw) { p = w + k; m = mw + k; v = vw + k; gr = gw[k]; }
+        else { p = b + (k - nw); m = mb + (k - nw); v = vb + (k - nw); gr = gb[k - nw]; }
+        const float mm = fmaf(h.beta1, *m - gr, gr);            // beta1 m + (1 - beta1) g
+        const float vv = fmaf(h.beta2, *v - gr * gr, gr * gr);
+        *m = mm;
+        *v = vv;
+        const float nwv = *p - h.lr * (mm * h.c1) / (sqrtf(vv * h.c2) + h.eps);
+        *p = nwv;
+        if (k < nw) {
+            const int ci = k % Cin, co = (k / Cin) % Cout, tap = k / (Cin * Cout);
+            w16[k] = __float2bfloat16(nwv);
+            w16t[((size_t)(8 - tap) * Cin + ci) * Cout + co] = __float2bfloat16(nwv);
+        }
+    }
+}
+
+// largest |a - b| of the flow over pixels, in px/frame (w / dmu), into
+// *out as the bit pattern of a non-negative float (atomicMax on ints orders
+// non-negative floats)
+__global__ void k_surr_maxdiff(Grid g, int n, const float4* __restrict__ a, const float4* __restrict__ b,
+                               unsigned* __restrict__ out)
+{
+    const size_t hw = (size_t)g.H * g.W, total = hw * n;
+    float m = 0.0f;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(p % hw), i = q / g.W, j = q % g.W;
+        const float inv = 1.0f / pixel_dmu(pixel_geometry(g, i, j));
+        const float4 u = a[p], v = b[p];
+        const float d = fmaxf(fabsf(u.x - v.x), fmaxf(fabsf(u.y - v.y), fabsf(u.z - v.z))) * inv;
+        m = fmaxf(m, d == d ? d : 3.0e38f);     // NaN counts as the largest difference
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// BF16 copies of FP32 weights (after a set or at creation)
+__global__ void k_weights_bf16(int Cin, int Cout, const float* __restrict__ w, __nv_bfloat16* __restrict__ w16,
+                               __nv_bfloat16* __restrict__ w16t)
+{
+    const int nw = 9 * Cout * Cin;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += gridDim.x * blockDim.x) {
+        const int ci = k % Cin, co = (k / Cin) % Cout, tap = k / (Cin * Cout);
+        const __nv_bfloat16 h = __float2bfloat16(w[k]);
+        w16[k] = h;
+        w16t[((size_t)(8 - tap) * Cin + ci) * Cout + co] = h;
+    }
+}
+
+}  // namespace sfdev

@@ -46,7 +46,9 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
-           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3"]
+           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_surrogate_create",
+           "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
+           "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate"]
 
 
 def lib():
@@ -79,6 +81,15 @@ def lib():
         L.sf_set_motion.argtypes = [vp, P(f), P(f), vp]
         L.sf_remap_pinhole.argtypes = [P(CGrid), P(f), i, i, P(f), vp, vp, vp, vp, vp]
         L.sf_conv3x3.argtypes = [i, i, i, i, i, vp, vp, vp, i, vp, vp, vp, vp]
+        L.sf_surrogate_create.argtypes = [ctypes.c_ulonglong, P(vp)]
+        L.sf_surrogate_destroy.argtypes = [vp]
+        L.sf_surrogate_destroy.restype = None
+        L.sf_surrogate_num_params.argtypes = [vp]
+        L.sf_surrogate_params.argtypes = [vp, P(f), i]
+        L.sf_surrogate_grads.argtypes = [vp, P(f)]
+        L.sf_surrogate_forward.argtypes = [vp, P(CGrid), i, vp, vp, vp]
+        L.sf_surrogate_train_step.argtypes = [vp, P(CGrid), i, vp, vp, f, P(f), vp]
+        L.sf_surrogate_propagate.argtypes = [vp, P(CGrid), i, i, vp, vp, f, P(f), P(i), vp]
         L.sf_remap_equirect.argtypes = [P(CGrid), P(f), i, i, vp, vp, vp, vp, vp]
         L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
@@ -314,6 +325,65 @@ def conv3x3(x, w, bias=None, relu=False, y=None, y32=None, status=None, stream=N
     Cout = w.shape[1]
     return _check(lib().sf_conv3x3(N, H, W, Cin, Cout, _ptr(x, 2), _ptr(w, 2), _ptr(bias), int(bool(relu)),
                                    _ptr(y, 2), _ptr(y32), _ptr(status), _stream(stream)), "sf_conv3x3")
+
+
+class Surrogate:
+    """The learned propagation surrogate (``sf_surrogate_*``)."""
+
+    LAYERS = ((16, 32), (32, 32), (32, 32), (32, 16))
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().sf_surrogate_create(int(seed), ctypes.byref(h)), "sf_surrogate_create")
+        self._h = h
+        self.n_params = _check(lib().sf_surrogate_num_params(h), "sf_surrogate_num_params")
+
+    def params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(lib().sf_surrogate_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0),
+               "sf_surrogate_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(lib().sf_surrogate_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1),
+               "sf_surrogate_params")
+
+    def grads(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(lib().sf_surrogate_grads(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "sf_surrogate_grads")
+        return out
+
+    def forward(self, g: CGrid, s0, p0, stream=None):
+        """s0, p0: [n, H, W, 4] float32 CUDA tensors (top-level state, w in rad/frame)."""
+        n = s0.shape[0] if s0.dim() == 4 else 1
+        return _check(lib().sf_surrogate_forward(self._h, ctypes.byref(g), n, _ptr(s0), _ptr(p0), _stream(stream)),
+                      "sf_surrogate_forward")
+
+    def train_step(self, g: CGrid, s0, target, lr, stream=None):
+        n = s0.shape[0] if s0.dim() == 4 else 1
+        loss = ctypes.c_float()
+        _check(lib().sf_surrogate_train_step(self._h, ctypes.byref(g), n, _ptr(s0), _ptr(target), float(lr),
+                                             ctypes.byref(loss), _stream(stream)), "sf_surrogate_train_step")
+        return loss.value
+
+    def propagate(self, g: CGrid, N, s0, p0, threshold_px, stream=None):
+        """Prediction with the plain fallback; returns (residual px, used_plain)."""
+        n = s0.shape[0] if s0.dim() == 4 else 1
+        res = ctypes.c_float(); used = ctypes.c_int()
+        _check(lib().sf_surrogate_propagate(self._h, ctypes.byref(g), n, int(N), _ptr(s0), _ptr(p0),
+                                            float(threshold_px), ctypes.byref(res), ctypes.byref(used),
+                                            _stream(stream)), "sf_surrogate_propagate")
+        return res.value, bool(used.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sf_surrogate_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
 
 
 class Batch:

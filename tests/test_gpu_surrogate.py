@@ -1,0 +1,123 @@
+"""The learned propagation surrogate on the GPU against the oracle's float64
+statement of the same network (oracle/surrogate.py), which rounds to
+bfloat16 at the points where the CUDA path stores bfloat16.
+
+Forward: the prediction agrees within 2^-7 of the largest output (one
+bfloat16 ulp of a value that may round differently when its float32 and
+float64 sums straddle a rounding boundary) plus 1e-4 (float32 accumulation),
+in the network's units.  Gradients: relative L2 error per layer within 3e-2
+(bfloat16 output and input gradients).  Training: 400 Adam steps on pairs
+produced by the plain propagation lower the loss at least five-fold."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate as S
+from paper_2406_18031_b300 import sf
+from tests import gpu_util as gu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+
+
+def _states(rng, n, H, W, dmu, eta, B, max_px):
+    out = []
+    for _ in range(n):
+        w = gu.cfl_scaled(gu.flow_field(rng, H, W, dmu, max_px=1.0), eta, B, dmu, max_px)
+        rho = gu.f32(0.2 + 0.15 * gu.smooth_field(rng, H, W))
+        out.append(np.concatenate([w, rho[..., None]], -1))
+    return gu.f32(np.stack(out))
+
+
+def _layer_slices():
+    k, out = 0, []
+    for cin, cout in S.LAYERS:
+        out.append(slice(k, k + 9 * cin * cout + cout))
+        k += 9 * cin * cout + cout
+    return out
+
+
+def test_forward_matches_oracle():
+    rng = np.random.default_rng(1)
+    H, W = 40, 160
+    g, eta, B, dmu = gu.level_grid(H, W, 80.0, 80.0, 80.0, 20.0, 1)
+    net = sf.Surrogate(seed=3)
+    p = net.params()
+    p[-16 - 9 * 16 * 32:] *= 10.0          # a larger last layer than at creation: visible outputs
+    net.set_params(p)
+    s0 = _states(rng, 2, H, W, dmu, eta, B, 1.5)
+    p0 = torch.empty_like(torch.from_numpy(s0)).cuda()
+    net.forward(g, torch.from_numpy(s0).cuda(), p0)
+    torch.cuda.synchronize()
+    _, y = S.forward(S.features(eta, dmu, s0), p, q=S.bf16)
+    ref = np.empty_like(s0, dtype=np.float64)
+    ref[..., 0:3] = s0[..., 0:3] + 4 * dmu[None, ..., None] * y[..., 0:3]
+    ref[..., 3] = s0[..., 3] + y[..., 3]
+    got = p0.cpu().numpy().astype(np.float64)
+    tol = 2.0 ** -7 * np.abs(y[..., :4]).max() + 1e-4
+    assert np.abs((got[..., 0:3] - ref[..., 0:3]) / (4 * dmu[None, ..., None])).max() <= tol
+    assert np.abs(got[..., 3] - ref[..., 3]).max() <= tol
+
+
+def test_gradients_match_oracle():
+    rng = np.random.default_rng(2)
+    H, W = 24, 136
+    g, eta, B, dmu = gu.level_grid(H, W, 70.0, 70.0, 68.0, 12.0, 1)
+    net = sf.Surrogate(seed=5)
+    p = net.params()
+    p[-16 - 9 * 16 * 32:] *= 10.0
+    net.set_params(p)
+    s0 = _states(rng, 2, H, W, dmu, eta, B, 1.0)
+    tgt = gu.f32(s0 + rng.normal(size=s0.shape) * np.concatenate([np.broadcast_to(dmu[..., None], (H, W, 3)) * 0.3,
+                                                                    np.full((H, W, 1), 0.01)], -1)[None])
+    loss = net.train_step(g, torch.from_numpy(s0).cuda(), torch.from_numpy(tgt).cuda(), lr=0.0)
+    gg = net.grads()
+    ref_loss, ref_g = S.loss_and_grads(S.features(eta, dmu, s0), p, S.residual_target(eta, dmu, s0, tgt), q=S.bf16)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    for sl in _layer_slices():
+        err = np.linalg.norm(gg[sl] - ref_g[sl]) / np.linalg.norm(ref_g[sl])
+        assert err <= 3e-2, err
+    np.testing.assert_array_equal(net.params(), p)     # lr = 0 leaves the parameters
+
+
+def test_training_on_plain_propagation_pairs_lowers_the_loss():
+    rng = np.random.default_rng(3)
+    H, W, N = 64, 256, 2
+    g, eta, B, dmu = gu.level_grid(H, W, 128.0, 128.0, 128.0, 32.0, 1)
+    s0 = _states(rng, 8, H, W, dmu, eta, B, 1.5)
+    s0_t = torch.from_numpy(s0).cuda()
+    tgt = torch.empty_like(s0_t)
+    for k in range(s0.shape[0]):
+        sf.propagate(g, N, s0_t[k], tgt[k])
+    net = sf.Surrogate(seed=7)
+    losses = [net.train_step(g, s0_t, tgt, lr=2e-3) for _ in range(400)]
+    assert np.isfinite(losses).all()
+    assert min(losses[-20:]) < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+def test_fallback_to_the_plain_propagation():
+    rng = np.random.default_rng(4)
+    H, W, N = 32, 192, 3
+    g, eta, B, dmu = gu.level_grid(H, W, 96.0, 96.0, 96.0, 16.0, 1)
+    s0 = torch.from_numpy(_states(rng, 2, H, W, dmu, eta, B, 1.0)).cuda()
+    net = sf.Surrogate(seed=9)
+    fwd = torch.empty_like(s0); net.forward(g, s0, fwd)
+    plain = torch.empty_like(s0)
+    for k in range(2):
+        sf.propagate(g, N, s0[k], plain[k])
+    out = torch.empty_like(s0)
+    res, used = net.propagate(g, N, s0, out, threshold_px=1e30)
+    torch.cuda.synchronize()
+    assert not used and res > 0
+    assert torch.equal(out, fwd)
+    res2, used2 = net.propagate(g, N, s0, out, threshold_px=0.5 * res)
+    torch.cuda.synchronize()
+    assert used2 and abs(res2 - res) <= 1e-6 * res
+    assert torch.equal(out, plain)
