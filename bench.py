@@ -354,11 +354,13 @@ def run_ours(args):
         achieved = bpl / (prop_ms / 1e3) / 1e9
         frame_bytes = algorithmic_bytes_per_frame(H, W, seq.levels)
         if args.quick:
-            e2e, (mean_epe, max_epe), cpu, batched, imu, remap = None, (None, None), None, None, None, None
+            e2e, (mean_epe, max_epe), cpu, batched, imu, remap, surrogate = (None, (None, None), None, None, None,
+                                                                              None, None)
         else:
             e2e = measure_e2e(filt, seq, args.steps)
             imu = measure_imu(seq, images, ranges, min(args.steps, 100), evict_l2)
             remap = measure_remap(seq, images, ranges, min(args.steps, 100), evict_l2)
+            surrogate = measure_surrogate(min(args.steps, 30), dev)
             mean_epe, max_epe = epe_vs_oracle(seq, frames=3)
             cpu = cpu_baseline(seq)
             filt.close()
@@ -392,6 +394,7 @@ def run_ours(args):
             "e2e": e2e,
             "imu": imu,
             "remap": remap,
+            "surrogate": surrogate,
             "batched": batched,
             "gpu_launches": kstep * args.steps,
             "clocks": clocks,
@@ -595,6 +598,147 @@ def measure_remap(seq, images, ranges, steps, evict_l2):
             "remap_equirect_2048x1024_to_512_us": remap_ms * 1e3,
             "remap_pinhole_1440x720_to_1024_us": pin_ms * 1e3,
             "note": "the paper's runtime includes this mapping step; each timed call starts with a cold L2"}
+
+
+SURR_TRAIN_STEPS = 1500
+
+
+def surrogate_flops_per_px():
+    """Multiply-adds x 2 of the four 3x3 layers per pixel (16-32-32-32-16)."""
+    return 2 * 9 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16)
+
+
+def measure_surrogate(steps, dev):
+    """The learned propagation surrogate on 16 single-level 1024 x 1024
+    streams (plane scenes, peak flow below 4 px/frame, N = 4): trained here on
+    pairs from the plain propagation (random smooth states of 8 x 256^2
+    pixels, SURR_TRAIN_STEPS Adam steps), then (a) one-frame prediction
+    error against the plain propagation on held-out states, (b) the batch
+    step with the plain propagation against the batch step with the
+    surrogate predicting the top level, (c) the flow difference between the
+    two batches after the timed frames."""
+    import torch
+    from paper_2406_18031_b300 import scenes, sf
+    rng = np.random.default_rng(17)
+
+    def states(n, H, W, g_eta_dmu, max_px):
+        eta, dmu = g_eta_dmu
+        out = []
+        for _ in range(n):
+            f = np.zeros((H, W, 3))
+            for c in range(3):
+                for _w in range(4):
+                    k = rng.uniform(0.02, 0.2, size=2) * rng.choice([-1, 1], size=2)
+                    i, j = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+                    f[..., c] += rng.uniform(0.3, 1.0) * np.sin(k[0] * i + k[1] * j + rng.uniform(0, 6.3))
+            f *= max_px / np.abs(f).max()
+            w = f * dmu[..., None] * np.array([1.0, 1.0, 0.3])
+            rho = 0.2 + 0.1 * np.sin(np.arange(H)[:, None] * 0.05 + np.arange(W)[None] * 0.03)
+            out.append(np.concatenate([w, rho[..., None]], -1))
+        return torch.from_numpy(np.stack(out).astype(np.float32)).to(dev)
+
+    def geometry(H, W, f):
+        j = (np.arange(W) + 0.5 - W / 2) / f
+        i = (np.arange(H) + 0.5 - H / 2) / f
+        x, y = np.meshgrid(j, i)
+        d = np.stack([x, y, np.ones_like(x)], -1)
+        eta = d / np.linalg.norm(d, axis=-1, keepdims=True)
+        dmu = (1.0 / f) / np.sqrt((x + 1.0 / f) ** 2 + y ** 2 + 1.0) * np.sqrt(1.0 - eta[..., 0] ** 2)
+        return eta, dmu
+
+    N = 4
+    # training pairs
+    Ht = Wt = 256
+    gt = sf.grid(Ht, Wt, Wt / 2, Wt / 2, Wt / 2, Ht / 2)
+    geo_t = geometry(Ht, Wt, Wt / 2)
+    s_train = states(8, Ht, Wt, geo_t, 3.0)
+    t_train = torch.empty_like(s_train)
+    for k in range(8):
+        sf.propagate(gt, N, s_train[k], t_train[k])
+    net = sf.Surrogate(seed=2024)
+    t0 = time.perf_counter()
+    losses = [net.train_step(gt, s_train, t_train, lr=2e-3 if k < SURR_TRAIN_STEPS // 2 else 5e-4)
+              for k in range(SURR_TRAIN_STEPS)]
+    train_s = time.perf_counter() - t0
+    # held-out prediction error (px/frame)
+    s_test = states(4, Ht, Wt, geo_t, 3.0)
+    t_test = torch.empty_like(s_test); p_test = torch.empty_like(s_test)
+    for k in range(4):
+        sf.propagate(gt, N, s_test[k], t_test[k])
+    net.forward(gt, s_test, p_test)
+    torch.cuda.synchronize()
+    dmu_t = torch.from_numpy(geo_t[1].astype(np.float32)).to(dev)
+    err = torch.linalg.norm(p_test[..., :3] - t_test[..., :3], dim=-1) / dmu_t
+    # the batch: plain against surrogate
+    H = W = 1024
+    seqs = []
+    for k in range(16):
+        depth = rng.uniform(3.0, 8.0)
+        d = rng.normal(size=3); d[2] = abs(d[2]); d /= np.linalg.norm(d)
+        # largest per-axis image flow (f |v_xy| + sqrt(2) f v_z) / depth / rate just below N px/frame
+        vmag = 0.95 * N * depth * 600.0 / (W / 2.0) / (np.linalg.norm(d[:2]) + np.sqrt(2.0) * d[2])
+        seqs.append(scenes.plane_stream(BATCH_FRAMES, 500 + k, H, W, depth, d * vmag, 600.0, 1, [N], [2],
+                                        period=BATCH_FRAMES))
+    dt = seqs[0].dt
+    frames = [[(torch.from_numpy(q.image[f]).to(dev), torch.from_numpy(q.range[f]).to(dev))
+               for f in range(BATCH_FRAMES)] for q in seqs]
+    stream = torch.cuda.current_stream()
+    out = {}
+    flows = {}
+    for mode in ("plain", "surrogate"):
+        P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
+        batch = sf.Batch([q.shape for q in seqs], [1] * len(seqs), P)
+        if mode == "surrogate":
+            batch.set_surrogate(net)
+
+        def load(k):
+            for s_ in range(len(seqs)):
+                batch.slots[s_][0].copy_(frames[s_][k % BATCH_FRAMES][0])
+                batch.slots[s_][1].copy_(frames[s_][k % BATCH_FRAMES][1])
+
+        for k in range(4):
+            load(k)
+            batch.step(dt, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            load(4 + k)
+            ev[k][0].record(stream)
+            batch.step(dt, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        flows[mode] = [batch.slots[s_][2].clone() for s_ in range(len(seqs))]
+        batch.profile(True)
+        load(4 + steps)
+        batch.step(dt, stream=stream)
+        torch.cuda.synchronize()
+        batch.profile(False)
+        slots = batch.profile_read()
+        out[mode] = {"ms_per_step": ms, "frames_per_s_per_stream": 1e3 / ms,
+                     "top_level_prediction_ms": slots[0][0] if slots else None}
+        batch.close()
+    g1 = sf.grid(H, W, W / 2, W / 2, W / 2, H / 2)
+    dmu1 = torch.from_numpy(geometry(H, W, W / 2)[1].astype(np.float32)).to(dev)
+    diffs = [torch.linalg.norm((a - b).permute(1, 2, 0), dim=-1) * dt / dmu1 for a, b in zip(flows["plain"],
+                                                                                              flows["surrogate"])]
+    d = torch.stack(diffs)
+    px = 16 * H * W
+    surr_ms = out["surrogate"]["top_level_prediction_ms"]
+    return {
+        "workload": "16 single-level 1024x1024 streams, plane scenes, peak flow < 4 px/frame, N=4, smooth 2, 600 Hz",
+        "training": {"pairs": "8 random smooth 256x256 states and their plain predictions (N=4)",
+                     "steps": SURR_TRAIN_STEPS, "seconds": train_s, "loss_first": losses[0],
+                     "loss_last": float(np.mean(losses[-20:]))},
+        "prediction_error_px": {"mean": float(err.mean()), "max": float(err.max()),
+                                "states": "4 held-out random 256x256 states"},
+        "plain": out["plain"], "surrogate": out["surrogate"],
+        "speedup": out["plain"]["ms_per_step"] / out["surrogate"]["ms_per_step"],
+        "flow_difference_px_after_timed_frames": {"mean": float(d.mean()), "max": float(d.max())},
+        "tensor_tflops_in_surrogate": surrogate_flops_per_px() * px / (surr_ms / 1e3) / 1e12 if surr_ms else None,
+        "verdict": ("the surrogate-plus-batched form is faster than the plain GPU form"
+                    if out["plain"]["ms_per_step"] > out["surrogate"]["ms_per_step"]
+                    else "the surrogate-plus-batched form is slower than the plain GPU form"),
+    }
 
 
 def measure_e2e(filt, seq, steps):

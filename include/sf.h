@@ -421,6 +421,13 @@ int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const floa
  * decision is taken on the host). */
 int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, const float* s0, float* p0,
                            float threshold_px, float* residual_px, int* used_plain, void* stream);
+/* Let a filter's top level (every stream's, for a batch) be predicted by the
+ * surrogate instead of the plain propagation (NULL restores the plain one).
+ * The lower levels keep the plain propagation.  The surrogate's buffers are
+ * sized here; it serves one filter or batch at a time and must outlive the
+ * attachment.  Steady-state batch steps re-capture their graphs. */
+int sf_set_surrogate(sf_ctx* c, sf_surrogate* s);
+int sf_batch_set_surrogate(sf_batch* b, sf_surrogate* s);
 
 #ifdef __cplusplus
 }

@@ -275,6 +275,7 @@ struct Engine {
     std::vector<EngineStream> st;
     int flags = 0;
     int nf_max = kNfLimit;      // sub-iterations fused per propagation launch (tuned or set)
+    sf_surrogate* surr = nullptr;   // when set, predicts every stream's top level instead of k_propagate
     int parity = 0;
     int initialised = 0;
     float dt_prev = 0.0f;
@@ -293,6 +294,7 @@ struct Engine {
     {
         int n = (int)prop.size() + 1;
         for (auto& p : smooth) n += p.nwork ? 1 : 0;
+        if (surr) n += 6 * (int)st.size();   // features, four layers, head per stream
         return n;
     }
 };
@@ -347,7 +349,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
     // segment writes the prediction planes, earlier ones alternate with t0/t1.
     int maxseg = 0;
     for (auto& s : E.st)
-        for (int h = 0; h < s.L; ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, nfmax));
+        for (int h = 0; h < s.L - (E.surr ? 1 : 0); ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, nfmax));
     E.prop.resize(maxseg);
     for (int k = 0; k < maxseg; ++k) {
         std::vector<PropJob> jobs;
@@ -362,6 +364,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
                     const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
                     if (nf != want) continue;
                     const bool top = h == s.L - 1;
+                    if (top && E.surr) continue;
                     auto out_of = [&](int seg, float4*& o0, float4*& o1) {
                         const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
                         o0 = to_pred ? lv.p0 : lv.t0;
@@ -563,8 +566,22 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
             r = launch_propagate(pl, E.parity, wscale, E.flags, E.status, st, dt);
             if (r) return r;
         }
+        if (E.surr) {
+            ProfScope ps(E.prof, slot++, st);
+            for (auto& s : E.st) {
+                sf_level_state& lv = s.lv[s.L - 1];
+                const size_t n = (size_t)lv.grid.H * lv.grid.W;
+                if (wscale != 1.0f) {
+                    k_scale_w<<<(int)std::min<size_t>((n + 255) / 256, 148 * 8), 256, 0, st>>>(lv.s0[E.parity], n,
+                                                                                              wscale);
+                    if (last_error()) return SF_ECUDA;
+                }
+                r = sf_surrogate_forward(E.surr, &lv.grid, 1, (const float*)lv.s0[E.parity], (float*)lv.p0, st);
+                if (r) return r;
+            }
+        }
     } else {
-        slot = (int)E.prop.size();
+        slot = (int)E.prop.size() + (E.surr ? 1 : 0);
     }
     {
         ProfScope ps(E.prof, slot++, st);
@@ -1175,7 +1192,8 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     a.status = status;
     const size_t smem = conv_smem_bytes(Cin, Cout);
     if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
-    const int grid = std::min(a.n_tiles, 148 * 4);
+    const int strips = N * a.tiles_x * ceil_div(H, kConvStrip);
+    const int grid = std::min(strips, 148 * 4);
     k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
     return last_error();
 }
@@ -1470,6 +1488,46 @@ int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, cons
     for (int k = 0; k < n && fallback && !r; ++k)
         r = sf_propagate(g, N, 0, 1.0f, s0 + 4 * frame * k, nullptr, p0 + 4 * frame * k, nullptr, nullptr, stream);
     return r;
+}
+
+namespace {
+
+// attach (or detach, s = null) a surrogate for every stream's top level
+int engine_attach(Engine& E, sf_surrogate* s)
+{
+    int r = SF_OK;
+    if (s) {
+        size_t mx = 0;
+        for (auto& es : E.st) mx = std::max(mx, (size_t)es.lv[es.L - 1].grid.H * es.lv[es.L - 1].grid.W);
+        r = surrogate_capacity(s, mx);
+        // the convolution's shared-memory limit is raised here, outside any stream capture
+        if (!r && set_smem_attr((const void*)k_conv3x3, conv_smem_bytes(kSurrHidden, kSurrHidden))) r = SF_ECUDA;
+        if (r) return r;
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SF_ECUDA;
+    E.surr = s;
+    r = engine_prop_plans(E, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaStreamDestroy(st);
+    for (int q = 0; q < 2; ++q)
+        if (E.graph[q]) { cudaGraphExecDestroy(E.graph[q]); E.graph[q] = nullptr; }
+    E.steps_plain = 0;
+    return r;
+}
+
+}  // namespace
+
+int sf_set_surrogate(sf_ctx* c, sf_surrogate* s)
+{
+    if (!c) return SF_EINVAL;
+    return engine_attach(c->E, s);
+}
+
+int sf_batch_set_surrogate(sf_batch* b, sf_surrogate* s)
+{
+    if (!b) return SF_EINVAL;
+    return engine_attach(b->E, s);
 }
 
 int sf_surrogate_grads(sf_surrogate* s, float* host)

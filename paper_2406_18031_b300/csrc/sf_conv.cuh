@@ -41,11 +41,14 @@ struct ConvArgs {
     int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
+constexpr int kConvRows = 4;          // staged input rows: a ring of 4
+constexpr int kConvStrip = 32;        // output rows per strip (a CTA's unit of work)
+
 __host__ __device__ inline size_t conv_smem_bytes(int Cin, int Cout)
 {
-    const size_t a = (size_t)3 * (Cin / 8) * kConvSlots * 16;
+    const size_t a = (size_t)kConvRows * (Cin / 8) * kConvSlots * 16;
     const size_t b = (size_t)9 * (Cin / 8) * Cout * 16;
-    return a + b + 16;   // + the mbarrier (8 bytes, 8-aligned) and the TMEM address
+    return a + b + 32;   // + two mbarriers (8 bytes each) and the TMEM address
 }
 
 // shared::cta address of a generic pointer into shared memory
@@ -116,20 +119,80 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// One CTA per group of tiles (persistent).  Every tile: stage its three input
-// rows, one thread issues the 9 Cin / 16 MMAs and commits them to an
-// mbarrier, every warp reads its 32 TMEM lanes (= pixels), adds the bias,
-// applies ReLU and stores the tile.
+// stage input row `iy` of image nn, columns x0 - 1 .. x0 + 134 (zero outside
+// the image), into row slot `slot`, channel-chunk major
+__device__ __forceinline__ void conv_stage_row(const ConvArgs& a, unsigned char* As, int C8, int nn, int iy, int x0,
+                                               int slot)
+{
+    unsigned char* dst = As + (size_t)slot * C8 * kConvSlots * 16;
+    const bool row_in = iy >= 0 && iy < a.H;
+    for (int idx = threadIdx.x; idx < kConvSlots * C8; idx += kConvThreads) {
+        const int c = idx % C8, p = idx / C8, ix = x0 + p - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row_in && ix >= 0 && ix < a.W && p < kConvM + 2)
+            v = *reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + iy) * a.W + ix) * a.Cin + 8 * c);
+        *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16 + p * 16) = v;
+    }
+}
+
+// TMEM buffer `buf` (output row yy) -> bias, ReLU, global memory
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int buf, int nn, int yy, int x0)
+{
+    const int warp = threadIdx.x >> 5;
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * buf), v);
+    const int px = x0 + 32 * warp + (threadIdx.x & 31);
+    if (px >= a.W) return;
+    const size_t o = (((size_t)nn * a.H + yy) * a.W + px) * a.Cout;
+    float r[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float u = v[k] + ((a.bias && k < a.Cout) ? a.bias[k] : 0.0f);
+        r[k] = a.relu ? fmaxf(u, 0.0f) : u;
+    }
+    if (a.y) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (8 * q >= a.Cout) break;
+            uint4 pk;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(r[8 * q + 0], r[8 * q + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(r[8 * q + 2], r[8 * q + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(r[8 * q + 4], r[8 * q + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(r[8 * q + 6], r[8 * q + 7]);
+            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+            pk.z = *reinterpret_cast<uint32_t*>(&h2);
+            pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(a.y + o + 8 * q) = pk;
+        }
+    }
+    if (a.y32) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (4 * q >= a.Cout) break;
+            *reinterpret_cast<float4*>(a.y32 + o + 4 * q) = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        }
+    }
+}
+
+// A CTA walks strips of kConvStrip output rows of one 128-pixel column of
+// tiles.  The input rows live in a ring of 4 slots, so each output row stages
+// one new input row; two TMEM accumulators let the MMAs of row y run while
+// the epilogue of row y - 1 and the staging of row y + 2 proceed:
+//   step y:  [sync] MMA(y) -> TMEM[y & 1]  |  wait MMA(y - 1), epilogue(y - 1)
+//            |  stage input row y + 2 into the slot of row y - 2
+// (rows y - 1 .. y + 1 feed MMA(y); row y - 2 was last read by MMA(y - 1)).
 __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
 {
     extern __shared__ __align__(16) unsigned char csm[];
     const int C8 = a.Cin / 8;
-    const size_t a_bytes = (size_t)3 * C8 * kConvSlots * 16;
+    const size_t row_bytes = (size_t)C8 * kConvSlots * 16;
+    const size_t a_bytes = kConvRows * row_bytes;
     const size_t b_bytes = (size_t)9 * C8 * a.Cout * 16;
     unsigned char* As = csm;
     unsigned char* Bs = csm + a_bytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(csm + a_bytes + b_bytes);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(csm + a_bytes + b_bytes);   // two
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     // weights: B_tap[n][k] at tap * (C8 Cout 16) + chunk * (Cout 16) + n * 16
@@ -140,11 +203,12 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(kConvTmemCols)
+                     "r"(2 * kConvTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -153,95 +217,72 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
     const uint32_t idesc = umma_idesc_bf16(a.Cout);
-    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs), mb = smem_u32(mbar);
-    uint32_t phase = 0;
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+    const uint32_t mb[2] = {smem_u32(mbar), smem_u32(mbar + 1)};
+    uint32_t phase[2] = {0u, 0u};
     bool failed = false;
+    int pending = 0;                          // MMA groups issued and not yet waited for (0..2)
 
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        const int tx = t % a.tiles_x, row = t / a.tiles_x;
-        const int yy = row % a.H, nn = row / a.H;
-        const int x0 = tx * kConvM;
-        // stage rows yy - 1 .. yy + 1, columns x0 - 1 .. x0 + 134 (zero outside the image)
-        for (int idx = tid; idx < 3 * kConvSlots * C8; idx += kConvThreads) {
-            const int c = idx % C8, p = (idx / C8) % kConvSlots, dy = idx / (C8 * kConvSlots);
-            const int iy = yy + dy - 1, ix = x0 + p - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W && p < kConvM + 2)
-                v = *reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + iy) * a.W + ix) * a.Cin + 8 * c);
-            *reinterpret_cast<uint4*>(As + (size_t)dy * C8 * kConvSlots * 16 + (size_t)c * kConvSlots * 16 + p * 16) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            int first = 1;
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;
-                for (int s = 0; s < C8 / 2; ++s) {
-                    const uint32_t aa = a_base + (uint32_t)(dy * C8 * kConvSlots * 16 + 2 * s * kConvSlots * 16 + dx * 16);
-                    const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * s * a.Cout * 16);
-                    umma_bf16(tmem, umma_desc(aa, kConvSlots * 16, 128), umma_desc(bb, a.Cout * 16, 128), idesc,
-                              first ? 0 : 1);
-                    first = 0;
+    const int strips_y = (a.H + kConvStrip - 1) / kConvStrip;
+    const int n_strips = a.N * a.tiles_x * strips_y;
+    for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
+        const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
+        const int x0 = tx * kConvM, y_begin = sy * kConvStrip, y_end = min(a.H, y_begin + kConvStrip);
+        for (int r = y_begin - 1; r <= y_begin + 1; ++r) conv_stage_row(a, As, C8, nn, r, x0, (r + 4) & 3);
+        for (int y = y_begin; y < y_end; ++y) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            const int buf = y & 1;
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                int first = 1;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t row_base = a_base + (uint32_t)(((y + dy - 1 + 4) & 3) * row_bytes);
+                    for (int s = 0; s < C8 / 2; ++s) {
+                        const uint32_t aa = row_base + (uint32_t)(2 * s * kConvSlots * 16 + dx * 16);
+                        const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * s * a.Cout * 16);
+                        umma_bf16(tmem + (uint32_t)(kConvTmemCols * buf), umma_desc(aa, kConvSlots * 16, 128),
+                                  umma_desc(bb, a.Cout * 16, 128), idesc, first ? 0 : 1);
+                        first = 0;
+                    }
                 }
+                umma_commit(mb[buf]);
             }
-            umma_commit(mb);
+            ++pending;
+            if (y > y_begin) {
+                const int pb = buf ^ 1;
+                const bool done = mbar_wait(mb[pb], phase[pb]);
+                if (!__syncthreads_and(done)) { failed = true; break; }
+                phase[pb] ^= 1u;
+                --pending;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                conv_epilogue(a, tmem, pb, nn, y - 1, x0);
+            }
+            if (y + 2 <= y_end) conv_stage_row(a, As, C8, nn, y + 2, x0, (y + 2) & 3);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
-        const bool done = mbar_wait(mb, phase);
-        if (!__syncthreads_and(done)) {   // every thread leaves together; the MMAs may still run
-            failed = true;
-            break;
-        }
-        phase ^= 1u;
+        if (failed) break;
+        // drain: the strip's last row
+        const int lb = (y_end - 1) & 1;
+        const bool done = mbar_wait(mb[lb], phase[lb]);
+        if (!__syncthreads_and(done)) { failed = true; break; }
+        phase[lb] ^= 1u;
+        --pending;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: pixel x0 + 32 warp + lane
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-        const int px = x0 + 32 * warp + (tid & 31);
-        if (px < a.W) {
-            const size_t o = (((size_t)nn * a.H + yy) * a.W + px) * a.Cout;
-            float r[32];
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                float u = v[k] + ((a.bias && k < a.Cout) ? a.bias[k] : 0.0f);
-                r[k] = a.relu ? fmaxf(u, 0.0f) : u;
-            }
-            if (a.y) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (8 * q >= a.Cout) break;
-                    uint4 pk;
-                    __nv_bfloat162 h0 = __floats2bfloat162_rn(r[8 * q + 0], r[8 * q + 1]);
-                    __nv_bfloat162 h1 = __floats2bfloat162_rn(r[8 * q + 2], r[8 * q + 3]);
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(r[8 * q + 4], r[8 * q + 5]);
-                    __nv_bfloat162 h3 = __floats2bfloat162_rn(r[8 * q + 6], r[8 * q + 7]);
-                    pk.x = *reinterpret_cast<uint32_t*>(&h0);
-                    pk.y = *reinterpret_cast<uint32_t*>(&h1);
-                    pk.z = *reinterpret_cast<uint32_t*>(&h2);
-                    pk.w = *reinterpret_cast<uint32_t*>(&h3);
-                    *reinterpret_cast<uint4*>(a.y + o + 8 * q) = pk;
-                }
-            }
-            if (a.y32) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (4 * q >= a.Cout) break;
-                    *reinterpret_cast<float4*>(a.y32 + o + 4 * q) =
-                        make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-                }
-            }
-        }
-        // the next tile restages the rows and overwrites TMEM
+        conv_epilogue(a, tmem, lb, nn, y_end - 1, x0);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        __syncthreads();   // the next strip restages every slot and reuses both accumulators
     }
     if (failed) {
         if (tid == 0 && a.status) atomicOr(a.status, kStatusTimeout);
-        mbar_wait(mb, phase);             // give the MMAs in flight a second bounded wait
+        // a second bounded wait for the groups still in flight (oldest first)
+        for (int b = 0; b < 2 && pending > 0; ++b)
+            if (mbar_wait(mb[b], phase[b])) --pending;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kConvTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kConvTmemCols)
                      : "memory");
     }
 }

@@ -951,6 +951,16 @@ __global__ void __launch_bounds__(kRemapTX * kRemapTY) k_remap(RemapArgs a)
     if (a.out_rng) a.out_rng[o] = lam;
 }
 
+// w <- wscale w in place (reading R9, for a top level the surrogate predicts)
+__global__ void k_scale_w(float4* __restrict__ s, size_t n, float wscale)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        float4 v = s[p];
+        v.x *= wscale; v.y *= wscale; v.z *= wscale;
+        s[p] = v;
+    }
+}
+
 // interleaved (s0, s1) float4 state <-> 8 planar float planes w(3) rho dw(3) Y
 __global__ void k_pack(const float4* __restrict__ s0, const float4* __restrict__ s1, float* __restrict__ dst, int n)
 {

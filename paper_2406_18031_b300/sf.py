@@ -48,7 +48,8 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_batch_profile_read",
            "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
-           "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate"]
+           "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
+           "sf_batch_set_surrogate"]
 
 
 def lib():
@@ -90,6 +91,8 @@ def lib():
         L.sf_surrogate_forward.argtypes = [vp, P(CGrid), i, vp, vp, vp]
         L.sf_surrogate_train_step.argtypes = [vp, P(CGrid), i, vp, vp, f, P(f), vp]
         L.sf_surrogate_propagate.argtypes = [vp, P(CGrid), i, i, vp, vp, f, P(f), P(i), vp]
+        L.sf_set_surrogate.argtypes = [vp, vp]
+        L.sf_batch_set_surrogate.argtypes = [vp, vp]
         L.sf_remap_equirect.argtypes = [P(CGrid), P(f), i, i, vp, vp, vp, vp, vp]
         L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
@@ -212,6 +215,11 @@ class Filter:
     def nf_max(self) -> int:
         """Sub-iterations fused per propagation launch (set, or chosen by AUTOTUNE)."""
         return _check(lib().sf_nf_max(self._h), "sf_nf_max")
+
+    def set_surrogate(self, net):
+        """Predict the top level with a trained Surrogate (None: the plain propagation)."""
+        _check(lib().sf_set_surrogate(self._h, None if net is None else net._h), "sf_set_surrogate")
+        self._surrogate = net     # kept alive while attached
 
     def set_motion(self, omega=None, accel=None, stream=None):
         """Angular velocity (rad/s) and linear acceleration (m/s^2) for IMU steps."""
@@ -415,6 +423,10 @@ class Batch:
 
     def step(self, dt, stream=None):
         return _check(lib().sf_batch_step(self._h, float(dt), _stream(stream)), "sf_batch_step")
+
+    def set_surrogate(self, net):
+        _check(lib().sf_batch_set_surrogate(self._h, None if net is None else net._h), "sf_batch_set_surrogate")
+        self._surrogate = net
 
     def status(self):
         code = lib().sf_batch_status(self._h)

@@ -121,3 +121,68 @@ def test_fallback_to_the_plain_propagation():
     torch.cuda.synchronize()
     assert used2 and abs(res2 - res) <= 1e-6 * res
     assert torch.equal(out, plain)
+
+
+def _planar_to_state(planes):
+    """[8, H, W] checkpoint planes -> (s0, s1) as [H, W, 4] float32 tensors."""
+    return planes[0:4].permute(1, 2, 0).contiguous(), planes[4:8].permute(1, 2, 0).contiguous()
+
+
+def test_filter_top_level_predicted_by_the_surrogate():
+    # a single-level filter with the surrogate attached computes, per frame,
+    # the surrogate's prediction of its state followed by the update: the same
+    # as the stage entry points chained by hand
+    from paper_2406_18031_b300 import scenes
+    seq = scenes.plane64(frames=3, H=48, W=160, levels=1, iters=[2])
+    H, W = seq.shape
+    P = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth)
+    net = sf.Surrogate(seed=11)
+    p = net.params(); p[-16 - 9 * 16 * 32:] *= 10.0; net.set_params(p)
+    filt = sf.Filter(H, W, 1, P)
+    filt.set_surrogate(net)
+    img = [torch.from_numpy(seq.image[k]).cuda() for k in range(3)]
+    rng_ = [torch.from_numpy(seq.range[k]).cuda() for k in range(3)]
+    flow = torch.empty((3, H, W), device="cuda")
+    filt.step(img[0], rng_[0], seq.dt, flow)
+    planes, _ = filt.get_state(0)
+    s0, s1 = _planar_to_state(planes)
+    filt.step(img[1], rng_[1], seq.dt, flow)
+    got, _ = filt.get_state(0)
+    g = sf.grid(H, W, seq.fx, seq.fy, seq.cx, seq.cy)
+    p0 = torch.empty_like(s0)
+    net.forward(g, s0[None], p0[None])
+    gam = list(filt.params.gamma)
+    gam[2] = gam[2] / seq.fx ** 2                         # the level-1 prior weight (reading R10)
+    n0, n1 = torch.empty_like(s0), torch.empty_like(s0)
+    sf.update(g, 1, 1, seq.smooth[0], 0, gam, 1.0, img[1], rng_[1], n0, n1, s0, s1, p0, None)
+    torch.cuda.synchronize()
+    ref = torch.cat([n0.permute(2, 0, 1), n1.permute(2, 0, 1)])
+    assert torch.equal(got, ref)
+    assert filt.kernels_per_step() == 6 + 1 + 1      # surrogate, solve, smoothing
+
+
+def test_batch_with_the_surrogate_matches_single_filters():
+    from paper_2406_18031_b300 import scenes
+    seqs = [scenes.plane64(frames=6, seed=21 + k, H=64, W=128 + 64 * k, levels=1, iters=[2]) for k in range(2)]
+    net = sf.Surrogate(seed=12)
+    P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
+    batch = sf.Batch([q.shape for q in seqs], [1, 1], P)
+    batch.set_surrogate(net)
+    singles = [sf.Filter(*q.shape, 1, p) for q, p in zip(seqs, P)]
+    net2 = sf.Surrogate(seed=12)            # same weights, its own buffers
+    for f in singles:
+        f.set_surrogate(net2)
+    stream = torch.cuda.Stream()
+    outs = [torch.empty((3, *q.shape), device="cuda") for q in seqs]
+    dt = seqs[0].dt
+    for k in range(6):
+        with torch.cuda.stream(stream):
+            for s, q in enumerate(seqs):
+                batch.slots[s][0].copy_(torch.from_numpy(q.image[k]).cuda())
+                batch.slots[s][1].copy_(torch.from_numpy(q.range[k]).cuda())
+                singles[s].step(torch.from_numpy(q.image[k]).cuda(), torch.from_numpy(q.range[k]).cuda(), dt,
+                                outs[s], stream=stream)
+            batch.step(dt, stream=stream)
+        stream.synchronize()
+        for s in range(2):
+            assert torch.equal(batch.slots[s][2], outs[s]), (k, s)
