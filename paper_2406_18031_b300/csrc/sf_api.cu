@@ -69,6 +69,29 @@ int set_smem_attr(const void* fn, size_t bytes)
 
 int last_error() { return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA; }
 
+// The frame's kernels are launched with programmatic stream serialisation:
+// each may be scheduled while the previous kernel of the stream finishes, and
+// waits (pdl_wait) before it touches anything that kernel or earlier work
+// produced, so only launch latency and index set-up overlap.
+constexpr bool kUsePdl = true;
+
+template <typename... KArgs, typename... Args>
+int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = kUsePdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
 // A launch: device copies of its jobs and of its work list (one item per CTA).
 struct Plan {
     void* jobs = nullptr;
@@ -113,9 +136,8 @@ template <bool C8, bool LIT, bool IMU>
 int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
 {
     if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU>, p.smem)) return SF_ECUDA;
-    k_propagate<C8, LIT, IMU><<<p.nwork, kPrThreads, p.smem, st>>>((const PropJob*)p.jobs, p.work, parity, wscale,
-                                                                   flags, status, mscale);
-    return last_error();
+    return launch_pdl(k_propagate<C8, LIT, IMU>, dim3(p.nwork), dim3(kPrThreads), p.smem, st, (const PropJob*)p.jobs,
+                      (const int4*)p.work, parity, wscale, flags, status, mscale);
 }
 
 template <bool C8, bool LIT>
@@ -142,8 +164,8 @@ int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* st
 int launch_solve(const Plan& p, const UpdArgs& a, cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
-    k_solve<<<p.nwork, kSolveThreads, 0, st>>>((const SolveJob*)p.jobs, p.work, a);
-    return last_error();
+    return launch_pdl(k_solve, dim3(p.nwork), dim3(kSolveThreads), 0, st, (const SolveJob*)p.jobs,
+                      (const int4*)p.work, a);
 }
 
 int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* status, float* flow, float* inv,
@@ -151,9 +173,8 @@ int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* sta
 {
     if (p.nwork == 0) return SF_OK;
     if (set_smem_attr((const void*)k_smooth_recon, p.smem)) return SF_ECUDA;
-    k_smooth_recon<<<p.nwork, kSmoothThreads, p.smem, st>>>((const SmoothJob*)p.jobs, p.work, q, inv_dt, check_finite,
-                                                             status, flow, inv);
-    return last_error();
+    return launch_pdl(k_smooth_recon, dim3(p.nwork), dim3(kSmoothThreads), p.smem, st, (const SmoothJob*)p.jobs,
+                      (const int4*)p.work, q, inv_dt, check_finite, status, flow, inv);
 }
 
 int launch_reconstruct(const ReconArgs& a, cudaStream_t st)

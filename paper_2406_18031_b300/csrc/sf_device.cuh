@@ -104,4 +104,12 @@ __device__ __forceinline__ float advance_nosrc(float f, float fn, float speed, f
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of the stream still
+// runs; pdl_wait() returns once that kernel has completed and its writes are
+// visible (a no-op for an ordinary launch), and pdl_trigger() lets the next
+// kernel start launching once every CTA of this one has called it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace sfdev

@@ -198,14 +198,7 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     const float ws = J.apply_wscale ? wscale : 1.0f;
     const float dt = J.dt;
     const float sdt = (flags & kSourceSplit) ? 0.5f * dt : dt;
-    float om[3] = {0.f, 0.f, 0.f}, ac[3] = {0.f, 0.f, 0.f};   // frame units
-    if (IMU && J.motion) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            om[c] = J.motion[c] * mscale;
-            ac[c] = J.motion[3 + c] * (mscale * mscale);
-        }
-    }
+    pdl_trigger();
 
     const int c0 = 2 * lane;                               // my region columns c0, c0 + 1
     const int j0 = ox + c0, j1 = j0 + 1;                   // ... image columns
@@ -214,6 +207,27 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     float4 a[kPrRows][2];       // (w, rho)
     float4 b[kPrRows][2];       // (dw, Y)
     float sp[kPrRows][2];       // speed of the next pass of each pixel
+
+    // per-pixel geometry: independent of the previous kernel, so it overlaps
+    // that kernel's tail under a programmatic dependent launch
+#pragma unroll
+    for (int k = 0; k < kPrRows; ++k) {
+        const int i = oy + r0 + k;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const PixGeo G = pix_geo(fmaf((float)(j0 + q), g.ax, g.bx), fmaf((float)i, g.ay, g.by), g.a);
+            geo[(r0 + k) * kPrW + q * 32 + lane] = make_float4(G.ex, G.ey, G.ez, G.cu);
+        }
+    }
+    pdl_wait();
+    float om[3] = {0.f, 0.f, 0.f}, ac[3] = {0.f, 0.f, 0.f};   // frame units
+    if (IMU && J.motion) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            om[c] = J.motion[c] * mscale;
+            ac[c] = J.motion[3 + c] * (mscale * mscale);
+        }
+    }
 
     // load (replicated coordinates outside the image: those pixels are never
     // read by an in-image pixel, whose border neighbours are itself)
@@ -235,10 +249,9 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             } else {
                 b[k][q] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const PixGeo G = pix_geo(fmaf((float)j, g.ax, g.bx), fmaf((float)i, g.ay, g.by), g.a);
-            geo[(r0 + k) * kPrW + q * 32 + lane] = make_float4(G.ex, G.ey, G.ez, G.cu);
-            const float s = fmaf(G.ex, f.x, fmaf(G.ey, f.y, G.ez * f.z));
-            sp[k][q] = G.cu * fmaf(-G.ex, s, f.x);        // u of Eq. 54
+            const float4 G = geo[(r0 + k) * kPrW + q * 32 + lane];   // this thread's own entry
+            const float s = fmaf(G.x, f.x, fmaf(G.y, f.y, G.z * f.z));
+            sp[k][q] = G.w * fmaf(-G.x, s, f.x);           // u of Eq. 54
         }
     }
 
@@ -526,6 +539,8 @@ k_solve(const SolveJob* __restrict__ jobs, const int4* __restrict__ work, UpdArg
         args.image = J.image; args.range = J.range; args.H1 = J.H1; args.W1 = J.W1; args.lambda_ref = J.lambda_ref;
     }
     const int x0 = wk.z, y0 = wk.y;
+    pdl_trigger();
+    pdl_wait();   // the input frame, the prediction and the state come from earlier work on the stream
     switch (J.level) {
     case 1: solve_region<1>(args, g, y0, x0, Yd, Rd); break;
     case 2: solve_region<2>(args, g, y0, x0, Yd, Rd); break;
@@ -696,6 +711,8 @@ k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work
                int check_finite, int* __restrict__ status, float* frame_flow, float* frame_inv)
 {
     extern __shared__ float4 sm4[];
+    pdl_trigger();
+    pdl_wait();   // the solution, Y-hat and the coarser level come from earlier kernels
     const int4 wk = work[blockIdx.x];
     const SmoothJob& J = jobs[wk.x];
     constexpr int T = kSmoothT, CE = kSmoothC;
