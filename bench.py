@@ -772,8 +772,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=512, help="frame size (multiple of 512); >512 is a profiling case")
     ap.add_argument("--quick", action="store_true", help="skip the e2e, oracle-EPE, CPU-baseline and batched legs")
-    ap.add_argument("--workload", choices=["scene512", "batch"], default="scene512",
-                    help="batch: only the 64-stream batched configuration, as its own line")
+    ap.add_argument("--workload", choices=["scene512", "batch", "surrogate", "conv"], default="scene512",
+                    help="batch / surrogate: only that configuration, as its own line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -781,6 +781,10 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch_line(args)
+    if args.workload == "surrogate":
+        return run_surrogate_line(args)
+    if args.workload == "conv":
+        return run_conv_line(args)
     return run_ours(args)
 
 
@@ -800,6 +804,72 @@ def run_batch_line(args):
             "config": {"workload": b["workload"], "global_batch": b["streams"], "l2": b["l2"]},
             "roofline": b["roofline"], "batched": b, "gpu_launches": b["launches_per_step"] * args.steps,
             "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_conv_line(args):
+    """One 3x3 layer of the surrogate (32 -> 32 channels, ReLU) on 16 frames of
+    1024 x 1024, timed alone: the tensor-core convolution's own roofline line
+    (also its profiling command)."""
+    import torch
+    from paper_2406_18031_b300 import build as sfbuild
+    from paper_2406_18031_b300 import sf
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    sfbuild.build()
+    dev = torch.device("cuda", local)
+    n, H, W, C = 16, 1024, 1024, 32
+    g = torch.Generator(device=dev); g.manual_seed(5)
+    x = (torch.randn((n, H, W, C), device=dev, generator=g) * 0.5).to(torch.bfloat16)
+    w = (torch.randn((9, C, C), device=dev, generator=g) * 0.06).to(torch.bfloat16)
+    b = torch.zeros(C, device=dev)
+    y = torch.empty((n, H, W, C), dtype=torch.bfloat16, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sf.conv3x3(x, w, b, True, y, stream=stream)
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        sf.conv3x3(x, w, b, True, y, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+    flops = 2 * 9 * C * C * n * H * W
+    peaks, kind = measured_peaks()
+    tf = flops / (ms / 1e3) / 1e12
+    line = {"metric": "TFLOP/s of one surrogate layer", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "3x3 conv 32->32 + ReLU, NHWC bf16, 16 x 1024 x 1024, FP32 accumulation"},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": tf / peaks["bf16_tflops"], "traffic": None,
+                         "peak_source": f"{kind} bf16_tflops (burst)"},
+            "hbm_gbs_algorithmic": 2 * C * 2 * n * H * W / (ms / 1e3) / 1e9,
+            "gpu_launches": args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_surrogate_line(args):
+    """The surrogate measurement alone, as its own line (also the profiling
+    command for the tensor-core convolution)."""
+    import torch
+    from paper_2406_18031_b300 import build as sfbuild
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    sfbuild.build()
+    dev = torch.device("cuda", local)
+    sampler = ClockSampler(local)
+    r = measure_surrogate(args.steps, dev)
+    clocks = sampler.stop()
+    line = {"metric": METRIC, "value": r["surrogate"]["frames_per_s_per_stream"],
+            "unit": "frames/s per stream (16 streams, surrogate)", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["surrogate"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": r["workload"], "global_batch": 16}, "surrogate": r, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -1213,7 +1213,10 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     a.status = status;
     const size_t smem = conv_smem_bytes(Cin, Cout);
     if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
-    const int strips = N * a.tiles_x * ceil_div(H, kConvStrip);
+    // strips of up to 32 rows, shorter when that leaves fewer than 4 per SM
+    const int columns = N * a.tiles_x;
+    a.strip = std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(148 * 4, columns)))));
+    const int strips = columns * ceil_div(H, a.strip);
     const int grid = std::min(strips, 148 * 4);
     k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
     return last_error();

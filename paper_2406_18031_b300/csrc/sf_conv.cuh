@@ -38,11 +38,12 @@ struct ConvArgs {
     float* y32;                  // N x H x W x Cout (fp32 output), or null
     int tiles_x;                 // ceil(W / 128)
     int n_tiles;                 // N * H * tiles_x
+    int strip;                   // output rows per strip (a CTA's unit of work), 1 .. kConvStrip
     int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
 constexpr int kConvRows = 4;          // staged input rows: a ring of 4
-constexpr int kConvStrip = 32;        // output rows per strip (a CTA's unit of work)
+constexpr int kConvStrip = 32;        // the longest strip of output rows (a CTA's unit of work)
 
 __host__ __device__ inline size_t conv_smem_bytes(int Cin, int Cout)
 {
@@ -126,12 +127,21 @@ __device__ __forceinline__ void conv_stage_row(const ConvArgs& a, unsigned char*
 {
     unsigned char* dst = As + (size_t)slot * C8 * kConvSlots * 16;
     const bool row_in = iy >= 0 && iy < a.H;
-    for (int idx = threadIdx.x; idx < kConvSlots * C8; idx += kConvThreads) {
-        const int c = idx % C8, p = idx / C8, ix = x0 + p - 1;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (row_in && ix >= 0 && ix < a.W && p < kConvM + 2)
-            v = *reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + iy) * a.W + ix) * a.Cin + 8 * c);
-        *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16 + p * 16) = v;
+    // one pixel per thread: its C8 chunks are contiguous in global memory, and
+    // the threads of a warp store one chunk of 32 consecutive slots at a time
+    // (consecutive 16-byte addresses: no bank conflicts)
+    for (int p = threadIdx.x; p < kConvSlots; p += kConvThreads) {
+        const int ix = x0 + p - 1;
+        const bool in = row_in && ix >= 0 && ix < a.W && p < kConvM + 2;
+        const uint4* src = reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + (in ? iy : 0)) * a.W +
+                                                                   (in ? ix : 0)) * a.Cin);
+        uint4 v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < C8) v[c] = in ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < C8) *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16 + p * 16) = v[c];
     }
 }
 
@@ -175,8 +185,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, 
     }
 }
 
-// A CTA walks strips of kConvStrip output rows of one 128-pixel column of
-// tiles.  The input rows live in a ring of 4 slots, so each output row stages
+// A CTA walks strips of output rows of one 128-pixel column of tiles.  The input rows live in a ring of 4 slots, so each output row stages
 // one new input row; two TMEM accumulators let the MMAs of row y run while
 // the epilogue of row y - 1 and the staging of row y + 2 proceed:
 //   step y:  [sync] MMA(y) -> TMEM[y & 1]  |  wait MMA(y - 1), epilogue(y - 1)
@@ -223,11 +232,11 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
     bool failed = false;
     int pending = 0;                          // MMA groups issued and not yet waited for (0..2)
 
-    const int strips_y = (a.H + kConvStrip - 1) / kConvStrip;
+    const int strips_y = (a.H + a.strip - 1) / a.strip;
     const int n_strips = a.N * a.tiles_x * strips_y;
     for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
         const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
-        const int x0 = tx * kConvM, y_begin = sy * kConvStrip, y_end = min(a.H, y_begin + kConvStrip);
+        const int x0 = tx * kConvM, y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
         for (int r = y_begin - 1; r <= y_begin + 1; ++r) conv_stage_row(a, As, C8, nn, r, x0, (r + 4) & 3);
         for (int y = y_begin; y < y_end; ++y) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
