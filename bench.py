@@ -113,6 +113,18 @@ def propagate_flops_per_launch(H, W, levels, iters, nf_max=8):
     return total
 
 
+def update_slot_names(n_slots, update_mode, levels, unit):
+    """Names of the profiled launch slots of one frame: the propagation
+    launches, the solve, then the smoothing launches (mode 1: one per level,
+    top first; mode 2: one for every level, then the reconstruction launches)."""
+    tail = ([f"k_smooth_recon#{unit}{levels - k if unit == 'level' else k}" for k in range(levels)]
+            if update_mode == 1 else
+            ["k_smooth_recon#all"] + [f"k_recon_jobs#{unit}{levels - k if unit == 'level' else k}"
+                                      for k in range(1, levels)])
+    nprop = n_slots - 1 - len(tail)
+    return [f"k_propagate#{k}" for k in range(nprop)] + ["k_solve"] + tail
+
+
 def propagate_bytes_per_launch(H, W, levels):
     """Algorithmic bytes of the first propagation launch: every level's state
     read once and its prediction written once (32 B/px each way below the top,
@@ -290,7 +302,8 @@ def run_ours(args):
     params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
                        flags=sf.CHECK_CFL | sf.AUTOTUNE)
     filt = sf.Filter(H, W, seq.levels, params)
-    nf_max = filt.nf_max()       # the autotuner's choice of sub-iterations per propagation launch
+    nf_max = filt.nf_max()       # the autotuner's choices: sub-iterations per propagation launch,
+    update_mode = filt.update_mode()   # and the form of the update
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -343,8 +356,7 @@ def run_ours(args):
         peaks, peak_kind = measured_peaks()
         kstep = filt.kernels_per_step()
         # dominant kernel: the first propagation launch of each frame (all levels)
-        names = [f"k_propagate#{k}" for k in range(len(slots) - 1 - seq.levels)] + ["k_solve"] + \
-                [f"k_smooth_recon#level{seq.levels - k}" for k in range(seq.levels)]
+        names = update_slot_names(len(slots), filt.update_mode(), seq.levels, "level")
         tot = sum(ms for ms, _ in slots) or 1.0
         shares = {n: {"ms_per_launch": ms / max(c, 1), "launches": c, "share": ms / tot}
                   for n, (ms, c) in zip(names, slots)}
@@ -375,7 +387,7 @@ def run_ours(args):
                        + ("" if args.size == 512 else f", tiled to {args.size}x{args.size} (profiling case)"),
                        "global_batch": ws, "streams_per_gpu": 1, "parallelism": f"replicas x{ws}",
                        "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)",
-                       "nf_max": nf_max, "autotune": True},
+                       "nf_max": nf_max, "update_mode": update_mode, "autotune": True},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
@@ -459,9 +471,7 @@ def measure_batch(steps, warmup, dev):
     px = sum(q.shape[0] * q.shape[1] for q in seqs)
     frame_bytes = sum(algorithmic_bytes_per_frame(q.shape[0], q.shape[1], q.levels) for q in seqs)
     maxL = max(q.levels for q in seqs)
-    nprop = len(slots) - 1 - maxL
-    names = [f"k_propagate#{k}" for k in range(nprop)] + ["k_solve"] + \
-            [f"k_smooth_recon#depth{k}" for k in range(maxL)]
+    names = update_slot_names(len(slots), batch.update_mode(), maxL, "depth")
     tot = sum(ms for ms, _ in slots) or 1.0
     prop_bytes = sum(propagate_bytes_per_launch(q.shape[0], q.shape[1], q.levels) for q in seqs)
     prop_ms = slots[0][0] / max(slots[0][1], 1)
@@ -470,7 +480,8 @@ def measure_batch(steps, warmup, dev):
         "workload": "64 streams: 16x256^2 (2 levels), 32x512^2 and 16x1024^2 (3 levels), peak flow < 4 px/frame, "
                     "cameras oscillating with a 16-frame period, "
                     "N=[4,2(,1)], smooth=[2,4(,4)], plane scenes, 600 Hz",
-        "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(), "autotune": True,
+        "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(),
+        "update_mode": batch.update_mode(), "autotune": True,
         "frames_per_s_per_stream": 1.0 / step_s, "ms_per_step": step_s * 1e3,
         "stream_frames_per_s": len(seqs) / step_s, "mpx_per_s": px / step_s / 1e6,
         "hbm_gbs_algorithmic": frame_bytes / step_s / 1e9,

@@ -72,7 +72,9 @@ extern "C" {
 #define SF_AUTOTUNE 16        /* at creation, time the propagation launches of one
                                  frame for each nf_max in {8, 6, 4, 3, 2} that
                                  splits the N_h differently and keep the fastest
-                                 (overrides sf_params.nf_max; see sf_nf_max)   */
+                                 (overrides sf_params.nf_max; see sf_nf_max);
+                                 with update_mode 0, also time both update modes
+                                 and keep the faster (see sf_update_mode)     */
 
 typedef struct sf_params {
     float fx, fy, cx, cy;          /* level-1 pinhole intrinsics, pixels              */
@@ -90,6 +92,14 @@ typedef struct sf_params {
                                       length (a launch of nf sub-iterations
                                       recomputes an nf-pixel halo around each
                                       (64 - 2 nf)^2 output tile)                   */
+    int update_mode;               /* how the smoothing and reconstruction of Sec. 4.5
+                                      and Eq. 26 are launched: 1 = one launch per
+                                      pyramid depth, top first, each smoothing a level
+                                      and reconstructing it from the coarser level's
+                                      result; 2 = one launch smoothing every level,
+                                      then one light reconstruction launch per lower
+                                      depth (fewer dependent launches, more traffic);
+                                      0 = 1, or the autotuner's choice under SF_AUTOTUNE */
 } sf_params;
 
 typedef struct sf_ctx sf_ctx;      /* opaque; owns all device state of one stream     */
@@ -167,6 +177,9 @@ int sf_set_motion(sf_ctx* c, const float* omega, const float* accel, void* strea
  * into launches. */
 int sf_nf_max(const sf_ctx* c);
 
+/* The update_mode the context runs with (1 or 2; see sf_params). */
+int sf_update_mode(const sf_ctx* c);
+
 /* Per-launch device timing.  sf_profile(c, 1) makes every following sf_step
  * record a CUDA event pair around each of its kernel launches, on the
  * step's stream; sf_profile(c, 0) stops it.  sf_profile_read waits for the
@@ -223,6 +236,7 @@ int sf_batch_launches_per_step(const sf_batch* b);
 /* As sf_nf_max, for the whole batch (every stream uses params[0].nf_max and
  * params[0].flags' SF_AUTOTUNE). */
 int sf_batch_nf_max(const sf_batch* b);
+int sf_batch_update_mode(const sf_batch* b);
 
 /* Stream s's motion slot for SF_IMU (the batch takes SF_IMU from
  * params[0].flags): *motion receives a device pointer to 6 floats, Omega

@@ -177,6 +177,14 @@ int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* sta
                       (const int4*)p.work, q, inv_dt, check_finite, status, flow, inv);
 }
 
+int launch_recon(const Plan& p, int q, float inv_dt, int check_finite, int* status, float* flow, float* inv,
+                 cudaStream_t st)
+{
+    if (p.nwork == 0) return SF_OK;
+    return launch_pdl(k_recon_jobs, dim3(p.nwork), dim3(kThreads), 0, st, (const ReconJob*)p.jobs, (const int4*)p.work,
+                      q, inv_dt, check_finite, status, flow, inv);
+}
+
 int launch_reconstruct(const ReconArgs& a, cudaStream_t st)
 {
     const int n = a.H * a.W;
@@ -202,6 +210,7 @@ int check_params(int H, int W, int L, const sf_params* p)
         if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k])) return SF_EINVAL;
     if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
     if (p->nf_max < 0 || p->nf_max > kNfLimit) return SF_EINVAL;
+    if (p->update_mode < 0 || p->update_mode > 2) return SF_EINVAL;
     for (int h = 0; h < L; ++h) {
         const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
         if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
@@ -303,7 +312,10 @@ struct Engine {
     int* status = nullptr;
     std::vector<Plan> prop;     // propagation launches
     Plan solve;                 // every level of every stream
-    std::vector<Plan> smooth;   // cascade: depth d handles level L - 1 - d of every stream
+    std::vector<Plan> smooth;   // cascade: depth d handles level L - 1 - d of every stream; parallel: one plan
+    std::vector<Plan> recon;    // parallel: reconstruction of depth 1, 2, ... (coarse first)
+    int update_mode = 1;        // 1: smoothing + reconstruction cascade; 2: all smoothing, then reconstruction
+    int update_auto = 0;        // the tuner chooses update_mode
     void* io = nullptr;         // slots of a batch
     float* motion = nullptr;    // every stream's motion slot (8 floats each), zeroed
     Profiler prof;
@@ -315,6 +327,7 @@ struct Engine {
     {
         int n = (int)prop.size() + 1;
         for (auto& p : smooth) n += p.nwork ? 1 : 0;
+        for (auto& p : recon) n += p.nwork ? 1 : 0;
         if (surr) n += 6 * (int)st.size();   // features, four layers, head per stream
         return n;
     }
@@ -329,6 +342,7 @@ void engine_free(Engine& E)
     for (auto& pl : E.prop) free_plan(pl);
     free_plan(E.solve);
     for (auto& pl : E.smooth) free_plan(pl);
+    for (auto& pl : E.recon) free_plan(pl);
     for (auto& s : E.st)
         for (int h = 0; h < s.L; ++h) cudaFree(s.lv[h].block);
     cudaFree(E.io);
@@ -424,6 +438,8 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
     return SF_OK;
 }
 
+int engine_smooth_plans(Engine& E, cudaStream_t st);
+
 int engine_update_plans(Engine& E, cudaStream_t st)
 {
     // ---- solve: every level of every stream, one 32 x 32 tile per CTA
@@ -459,16 +475,30 @@ int engine_update_plans(Engine& E, cudaStream_t st)
         int r = upload_plan(jobs, work, E.solve, st);
         if (r) return r;
     }
-    // ---- smoothing + reconstruction cascade
+    return engine_smooth_plans(E, st);
+}
+
+// smoothing (+ reconstruction) plans of the engine's update mode
+int engine_smooth_plans(Engine& E, cudaStream_t st)
+{
+    for (auto& pl : E.smooth) free_plan(pl);
+    for (auto& pl : E.recon) free_plan(pl);
+    E.smooth.clear();
+    E.recon.clear();
     int maxL = 0;
     for (auto& s : E.st) maxL = std::max(maxL, s.L);
-    E.smooth.resize(maxL);
+    const bool parallel = E.update_mode == 2;
+    // cascade: depth d in plan d; parallel: every depth in plan 0, lower levels deferred
+    E.smooth.resize(parallel ? 1 : maxL);
     for (int d = 0; d < maxL; ++d) {
+        const int plan = parallel ? 0 : d;
+        if (parallel && d > 0) continue;   // plan 0 takes every depth below
         std::vector<SmoothJob> jobs;
         std::vector<int4> work;
         size_t smem = 0;
+        for (int dd = d; dd < (parallel ? maxL : d + 1); ++dd)
         for (auto& s : E.st) {
-            const int h = s.L - 1 - d;
+            const int h = s.L - 1 - dd;
             if (h < 0) continue;
             sf_level_state& lv = s.lv[h];
             SmoothJob j;
@@ -490,13 +520,46 @@ int engine_update_plans(Engine& E, cudaStream_t st)
                 j.invdepth_out = s.inv;
                 j.frame_outputs = s.image == nullptr;   // single-stream filter: per-frame output pointers
             }
+            if (parallel && !j.top) {
+                j.defer = 1;
+                j.s0c[0] = j.s0c[1] = nullptr;
+                j.flow_out = j.invdepth_out = nullptr;
+                j.frame_outputs = 0;
+            }
             j.tiles_x = ceil_div(lv.grid.W, kSmoothT);
             jobs.push_back(j);
             add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kSmoothT, kSmoothT);
             smem = std::max(smem, smooth_smem_bytes(j.S));
         }
-        E.smooth[d].smem = smem;
-        int r = upload_plan(jobs, work, E.smooth[d], st);
+        E.smooth[plan].smem = smem;
+        int r = upload_plan(jobs, work, E.smooth[plan], st);
+        if (r) return r;
+    }
+    if (!parallel) return SF_OK;
+    // reconstruction of the deferred levels, depth 1 (just below the top) first
+    E.recon.resize(std::max(0, maxL - 1));
+    for (int d = 1; d < maxL; ++d) {
+        std::vector<ReconJob> jobs;
+        std::vector<int4> work;
+        for (auto& s : E.st) {
+            const int h = s.L - 1 - d;
+            if (h < 0) continue;
+            sf_level_state& lv = s.lv[h];
+            ReconJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.H = lv.grid.H; j.W = lv.grid.W;
+            j.Hc = s.lv[h + 1].grid.H; j.Wc = s.lv[h + 1].grid.W;
+            for (int q = 0; q < 2; ++q) { j.s0[q] = lv.s0[q]; j.s0c[q] = s.lv[h + 1].s0[q]; }
+            if (h == 0) {
+                j.flow_out = s.flow;
+                j.invdepth_out = s.inv;
+                j.frame_outputs = s.image == nullptr;
+            }
+            jobs.push_back(j);
+            const int n = lv.grid.H * lv.grid.W;
+            for (int p0 = 0; p0 < n; p0 += kReconChunk) work.push_back(make_int4((int)jobs.size() - 1, p0, 0, 0));
+        }
+        int r = upload_plan(jobs, work, E.recon[d - 1], st);
         if (r) return r;
     }
     return SF_OK;
@@ -508,6 +571,8 @@ int engine_update_plans(Engine& E, cudaStream_t st)
 // keep the fastest.  It runs on the engine's zero state: the kernel has no
 // data-dependent branches, so the timing is that of any state, and the
 // propagation of zeros writes zeros, so the engine is left as created.
+int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, float* inv, int slot, cudaStream_t st);
+
 int engine_tune(Engine& E, cudaStream_t st)
 {
     const int cand[] = {8, 6, 4, 3, 2};
@@ -537,11 +602,54 @@ int engine_tune(Engine& E, cudaStream_t st)
         if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
         if (!r && (best_ms < 0.0f || ms < best_ms)) { best_ms = ms; best = nf; }
     }
+    if (r) { if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); return r; }
+    E.nf_max = best;
+    r = engine_prop_plans(E, st);
+    // the update's form, when the parameters leave it open and a stream has a
+    // level below the top: time the solve + smoothing (+ reconstruction) of one
+    // frame in both forms on the zero state (zero inputs and outputs kept in
+    // scratch buffers; the state stays zero) and keep the faster
+    int maxL = 0;
+    size_t npx = 0;
+    for (auto& es : E.st) { maxL = std::max(maxL, es.L); npx = std::max(npx, (size_t)es.H * es.W); }
+    if (!r && E.update_auto && maxL >= 2) {
+        float* scratch = nullptr;
+        if (cudaMalloc(&scratch, 6 * npx * sizeof(float)) != cudaSuccess) scratch = nullptr, r = SF_ENOMEM;
+        if (!r) r = cudaMemsetAsync(scratch, 0, 6 * npx * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
+        UpdArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.image = scratch;
+        a.range = scratch + npx;
+        a.H1 = E.st[0].H;
+        a.W1 = E.st[0].W;
+        a.lambda_ref = E.st[0].p.lambda_ref;
+        float best_u = -1.0f;
+        int best_mode = 1;
+        for (int mode = 1; mode <= 2 && !r; ++mode) {
+            E.update_mode = mode;
+            r = engine_smooth_plans(E, st);
+            for (int it = 0; it < 14 && !r; ++it) {
+                if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
+                a.parity = it & 1;
+                if (!r) r = engine_update_launches(E, a, 1.0f, scratch + 2 * npx, scratch + 5 * npx, 0, st);
+            }
+            if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
+            if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
+            float ms = 0.0f;
+            if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
+            if (!r && (best_u < 0.0f || ms < best_u)) { best_u = ms; best_mode = mode; }
+        }
+        if (!r && cudaStreamSynchronize(st) != cudaSuccess) r = SF_ECUDA;
+        cudaFree(scratch);
+        if (!r) {
+            E.update_mode = best_mode;
+            r = engine_smooth_plans(E, st);
+        }
+        if (!r && cudaMemsetAsync(E.status, 0, sizeof(int), st) != cudaSuccess) r = SF_ECUDA;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (r) return r;
-    E.nf_max = best;
-    return engine_prop_plans(E, st);
+    return r;
 }
 
 // create the streams' levels, the status word and the plans
@@ -565,6 +673,31 @@ int engine_init(Engine& E)
     if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
     cudaStreamDestroy(st);
     return r;
+}
+
+// the update of one frame: solve, smoothing (+ reconstruction) launches
+int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, float* inv, int slot, cudaStream_t st)
+{
+    int r;
+    {
+        ProfScope ps(E.prof, slot++, st);
+        r = launch_solve(E.solve, a, st);
+        if (r) return r;
+    }
+    const int check = (E.flags & SF_CHECK_FINITE) != 0;
+    for (auto& pl : E.smooth) {
+        if (!pl.nwork) continue;
+        ProfScope ps(E.prof, slot++, st);
+        r = launch_smooth(pl, a.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
+        if (r) return r;
+    }
+    for (auto& pl : E.recon) {
+        if (!pl.nwork) continue;
+        ProfScope ps(E.prof, slot++, st);
+        r = launch_recon(pl, a.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
+        if (r) return r;
+    }
+    return SF_OK;
 }
 
 // the launches of one frame (no host synchronisation; capturable)
@@ -604,19 +737,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
     } else {
         slot = (int)E.prop.size() + (E.surr ? 1 : 0);
     }
-    {
-        ProfScope ps(E.prof, slot++, st);
-        r = launch_solve(E.solve, a, st);
-        if (r) return r;
-    }
-    const int check = (E.flags & SF_CHECK_FINITE) != 0;
-    for (auto& pl : E.smooth) {
-        if (!pl.nwork) continue;
-        ProfScope ps(E.prof, slot++, st);
-        r = launch_smooth(pl, E.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
-        if (r) return r;
-    }
-    return SF_OK;
+    return engine_update_launches(E, a, dt, flow, inv, slot, st);
 }
 
 int engine_status(Engine& E)
@@ -710,6 +831,8 @@ int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
     s.H = H; s.W = W; s.L = levels; s.p = *p;
     c->E.flags = p->flags;
     c->E.nf_max = p->nf_max ? p->nf_max : kNfLimit;
+    c->E.update_mode = p->update_mode ? p->update_mode : 1;
+    c->E.update_auto = p->update_mode == 0 && (p->flags & SF_AUTOTUNE);
     r = engine_init(c->E);
     if (r) { destroy_ctx(c); return r; }
     *out = c;
@@ -821,6 +944,12 @@ int sf_nf_max(const sf_ctx* c)
     return c->E.nf_max;
 }
 
+int sf_update_mode(const sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    return c->E.update_mode;
+}
+
 int sf_set_motion(sf_ctx* c, const float* omega, const float* accel, void* stream)
 {
     if (!c) return SF_EINVAL;
@@ -872,6 +1001,8 @@ int sf_batch_create(int n, const int* H, const int* W, const int* levels, const 
     E.st.resize(n);
     E.flags = params[0].flags;
     E.nf_max = params[0].nf_max ? params[0].nf_max : kNfLimit;
+    E.update_mode = params[0].update_mode ? params[0].update_mode : 1;
+    E.update_auto = params[0].update_mode == 0 && (params[0].flags & SF_AUTOTUNE);
     size_t io_floats = 0;
     for (int s = 0; s < n; ++s) io_floats += 6 * (size_t)H[s] * W[s];   // image, range, flow (3), inverse depth
     int r = SF_OK;
@@ -960,6 +1091,12 @@ int sf_batch_nf_max(const sf_batch* b)
 {
     if (!b) return SF_EINVAL;
     return b->E.nf_max;
+}
+
+int sf_batch_update_mode(const sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    return b->E.update_mode;
 }
 
 int sf_batch_motion(sf_batch* b, int s, float** motion)

@@ -655,6 +655,8 @@ struct SmoothJob {
     float* flow_out;       // level 1 only
     float* invdepth_out;
     int frame_outputs;     // level 1 of a single-stream filter: the launch's output pointers
+    int defer;             // lower level whose reconstruction runs later (k_recon_jobs):
+                           // writes (dw, rho) to s0_new, no coarse read, no outputs
     int tiles_x;
 };
 
@@ -806,6 +808,10 @@ k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work
             w = x;
             J.s0_new[q][gi] = x;
             J.s1_new[q][gi] = make_float4(0.f, 0.f, 0.f, yv[k]);
+        } else if (J.defer) {
+            J.s0_new[q][gi] = x;
+            J.s1_new[q][gi] = make_float4(x.x, x.y, x.z, yv[k]);
+            continue;
         } else {
             if (coarse) {
                 // bilinear x2 at pixel centres (reading R14): coarse coordinate i/2 - 1/4
@@ -966,6 +972,66 @@ __global__ void __launch_bounds__(kRemapTX * kRemapTY) k_remap(RemapArgs a)
     const size_t o = (size_t)i * a.W + j;
     a.out_img[o] = Y;
     if (a.out_rng) a.out_rng[o] = lam;
+}
+
+// Reconstruction (Eq. 26) of deferred lower levels, many (stream, level) jobs
+// per launch (one per depth, coarse first): w_h = up(w_{h+1}) + dw_h in place
+// of s0_new = (dw_h, rho); level 1 also writes flow = w / dt and rho.  A CTA
+// handles a chunk of kReconChunk pixels of one job.
+struct ReconJob {
+    int H, W, Hc, Wc;
+    float4* s0[2];             // by the parity of the frame being written
+    const float4* s0c[2];      // coarser level's new state
+    float* flow_out;           // level 1 of a batched stream
+    float* invdepth_out;
+    int frame_outputs;         // level 1 of a single-stream filter: the launch's output pointers
+};
+
+constexpr int kReconChunk = 1024;        // four pixels per thread
+
+__global__ void __launch_bounds__(kThreads) k_recon_jobs(const ReconJob* __restrict__ jobs,
+                                                        const int4* __restrict__ work, int q, float inv_dt,
+                                                        int check_finite, int* __restrict__ status,
+                                                        float* frame_flow, float* frame_inv)
+{
+    pdl_trigger();
+    pdl_wait();
+    const int4 wk = work[blockIdx.x];
+    const ReconJob& J = jobs[wk.x];
+    const int n = J.H * J.W, p1 = min(n, wk.y + kReconChunk);
+    float4* __restrict__ s0 = J.s0[q];
+    const float4* __restrict__ c = J.s0c[q];
+    float* const flow_out = J.frame_outputs ? frame_flow : J.flow_out;
+    float* const inv_out = J.frame_outputs ? frame_inv : J.invdepth_out;
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < kReconChunk / kThreads; ++u) {
+        const int p = wk.y + threadIdx.x + u * kThreads;
+        if (p >= p1) break;
+        const int i = p / J.W, j = p - (p / J.W) * J.W;
+        float4 s = s0[p];
+        const int i0 = (i - 1) >> 1, j0 = (j - 1) >> 1;   // bilinear x2 at pixel centres (reading R14)
+        const float fy = (i & 1) ? 0.25f : 0.75f, fx = (j & 1) ? 0.25f : 0.75f;
+        const int ia = clampi(i0, 0, J.Hc - 1), ib = clampi(i0 + 1, 0, J.Hc - 1);
+        const int ja = clampi(j0, 0, J.Wc - 1), jb = clampi(j0 + 1, 0, J.Wc - 1);
+        const float4 c00 = c[ia * J.Wc + ja], c01 = c[ia * J.Wc + jb];
+        const float4 c10 = c[ib * J.Wc + ja], c11 = c[ib * J.Wc + jb];
+        const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
+        s.x += wy0 * (wx0 * c00.x + fx * c01.x) + fy * (wx0 * c10.x + fx * c11.x);
+        s.y += wy0 * (wx0 * c00.y + fx * c01.y) + fy * (wx0 * c10.y + fx * c11.y);
+        s.z += wy0 * (wx0 * c00.z + fx * c01.z) + fy * (wx0 * c10.z + fx * c11.z);
+        s0[p] = s;
+        if (flow_out) {
+            flow_out[p] = s.x * inv_dt;
+            flow_out[n + p] = s.y * inv_dt;
+            flow_out[2 * n + p] = s.z * inv_dt;
+        }
+        if (inv_out) inv_out[p] = s.w;
+        if (check_finite && (flow_out || inv_out)) bad |= !(isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.w));
+    }
+    if (check_finite && status) {
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
+    }
 }
 
 // w <- wscale w in place (reading R9, for a top level the surrogate predicts)

@@ -28,9 +28,9 @@ def _streams():
     ]
 
 
-def _params(seq, nf_max=None):
+def _params(seq, nf_max=None, update_mode=None):
     return sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
-                     flags=sf.CHECK_CFL | sf.CHECK_FINITE, nf_max=nf_max)
+                     flags=sf.CHECK_CFL | sf.CHECK_FINITE, nf_max=nf_max, update_mode=update_mode)
 
 
 def test_batch_inertial_terms_match_single_stream_filters():
@@ -65,12 +65,13 @@ def test_batch_inertial_terms_match_single_stream_filters():
     assert batch.status() in (sf.OK, sf.WARN_CFL)
 
 
-@pytest.mark.parametrize("nf_max", [None, 4])
-def test_batch_matches_single_stream_filters_and_oracle(nf_max):
+@pytest.mark.parametrize("nf_max,update_mode", [(None, None), (4, None), (None, 2)])
+def test_batch_matches_single_stream_filters_and_oracle(nf_max, update_mode):
     seqs = _streams()
     dt = seqs[0].dt
     assert all(abs(s.dt - dt) < 1e-15 for s in seqs)
-    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs], [_params(s, nf_max) for s in seqs])
+    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs],
+                     [_params(s, nf_max, update_mode) for s in seqs])
     singles = [sf.Filter(*s.shape, s.levels, _params(s)) for s in seqs]
     ref = oracle.Filter(*seqs[2].shape, seqs[2].levels,
                         oracle.Params(seqs[2].fx, seqs[2].fy, seqs[2].cx, seqs[2].cy, iters=seqs[2].iters,
@@ -100,7 +101,9 @@ def test_batch_matches_single_stream_filters_and_oracle(nf_max):
         e = np.abs(batch.slots[2][2].cpu().numpy().astype(np.float64) - rf) * dt / dmu_ref[None]
         assert e.max() <= gu.FLOW_TOL_PX
     # N = 10 on stream 3 needs two propagation launches (three at nf_max = 4),
-    # then one solve launch and a smoothing + reconstruction cascade of three levels
+    # then one solve launch and a smoothing + reconstruction cascade of three
+    # levels (update mode 2: one smoothing launch and two reconstruction launches)
     assert batch.launches_per_step() == (2 if nf_max is None else 3) + 1 + 3
+    assert batch.update_mode() == (update_mode or 1)
     assert batch.nf_max() == (nf_max or 8)
     assert batch.status() in (sf.OK, sf.WARN_CFL)

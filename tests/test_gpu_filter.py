@@ -19,21 +19,22 @@ def _cuda():
     oracle.set_threads(8)
 
 
-def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None):
+def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None, update_mode=None):
     H, W = seq.shape
     kw = dict(iters=seq.iters, smooth=seq.smooth)
     if gamma is not None:
         kw["gamma"] = gamma
     g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, nf_max=nf_max,
+                                               update_mode=update_mode,
                                                flags=flags | gpu_flags | sf.CHECK_CFL | sf.CHECK_FINITE, **kw))
     r = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, flags=flags, **kw))
     return g, r
 
 
 def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX, gpu_flags=0, nf_max=None,
-         filt=None):
+         filt=None, update_mode=None):
     """Run both filters; returns per-frame (max px error, max rho error) and the final outputs."""
-    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max)
+    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max, update_mode=update_mode)
     if filt is not None:
         filt.append(g)
     H, W = seq.shape
@@ -84,12 +85,30 @@ def test_propagation_split_into_launches(nf_max):
     assert filt[0].kernels_per_step() == -(-10 // nf_max) + 1 + 2
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_parallel_update_mode_matches_oracle(levels):
+    # update_mode 2: every level smoothed in one launch, the lower levels then
+    # reconstructed by light launches (coarse first)
+    if levels == 2:
+        seq = scenes.scene512(frames=6, H=128, W=160, max_flow=4.0, levels=2, iters=(4, 2), smooth=(2, 4))
+    else:
+        seq = scenes.drive(frames=5, H=96, W=312, levels=3, iters=(8, 4, 2), smooth=(2, 4, 4))
+    filt = []
+    errs, _, _, st = _run(seq, seq.frames, update_mode=2, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert filt[0].update_mode() == 2
+    N = seq.iters
+    assert filt[0].kernels_per_step() == -(-max(N) // 8) + 1 + 1 + (levels - 1)
+
+
 def test_autotune_keeps_a_candidate_and_the_results():
     seq = scenes.scene512(frames=4, H=128, W=128, max_flow=6.0, levels=2, iters=(6, 3), smooth=(2, 4))
     filt = []
     errs, _, _, st = _run(seq, 4, gpu_flags=sf.AUTOTUNE, filt=filt)
     assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
     assert filt[0].nf_max() in (8, 6, 4, 3, 2)
+    assert filt[0].update_mode() in (1, 2)
     assert st == sf.OK
 
 
