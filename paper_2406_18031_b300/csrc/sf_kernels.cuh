@@ -120,6 +120,22 @@ __device__ __forceinline__ float4 shfl_down4(float4 v)
                        __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
 }
 
+// The same step without selecting the upwind neighbour: with km = c on the
+// minus side and kp = c on the plus side (the other one 0),
+// f' = ks f + km f_minus + kp f_plus, two channels per packed FP32x2
+// instruction; ksw is the self weight of the fourth channel (Y: no source).
+__device__ __forceinline__ float4 upwind4(float4 f, float4 fm, float4 fp, float km, float kp, float ks, float ksw)
+{
+    const float2 km2 = make_float2(km, km), kp2 = make_float2(kp, kp);
+    float2 lo = __fmul2_rn(km2, make_float2(fm.x, fm.y));
+    lo = __ffma2_rn(kp2, make_float2(fp.x, fp.y), lo);
+    lo = __ffma2_rn(make_float2(ks, ks), make_float2(f.x, f.y), lo);
+    float2 hi = __fmul2_rn(km2, make_float2(fm.z, fm.w));
+    hi = __ffma2_rn(kp2, make_float2(fp.z, fp.w), hi);
+    hi = __ffma2_rn(make_float2(ks, ksw), make_float2(f.z, f.w), hi);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 __device__ __forceinline__ float4 sel4(bool c, float4 a, float4 b)
 {
     return make_float4(c ? a.x : b.x, c ? a.y : b.y, c ? a.z : b.z, c ? a.w : b.w);
@@ -278,12 +294,14 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0, p0, src0, dt, sdt, bad, row_in && col_in[0]);
             const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1, p1, src1, dt, sdt, bad, row_in && col_in[1]);
             const float4 aL = shfl_up4(a[k][1]), aR = shfl_down4(a[k][0]);
-            const float4 na0 = step4(a[k][0], k0.minus ? aL : a[k][1], k0.kself, k0.knb);
-            const float4 na1 = step4(a[k][1], k1.minus ? a[k][0] : aR, k1.kself, k1.knb);
+            const float km0 = k0.minus ? k0.knb : 0.0f, kp0 = k0.minus ? 0.0f : k0.knb;
+            const float km1 = k1.minus ? k1.knb : 0.0f, kp1 = k1.minus ? 0.0f : k1.knb;
+            const float4 na0 = upwind4(a[k][0], aL, a[k][1], km0, kp0, k0.kself, k0.kself);
+            const float4 na1 = upwind4(a[k][1], a[k][0], aR, km1, kp1, k1.kself, k1.kself);
             if (has1) {
                 const float4 bL = shfl_up4(b[k][1]), bR = shfl_down4(b[k][0]);
-                const float4 nb0 = step4y(b[k][0], sel4(k0.minus, bL, b[k][1]), k0.kself, k0.knb, k0.kselfy);
-                const float4 nb1 = step4y(b[k][1], sel4(k1.minus, b[k][0], bR), k1.kself, k1.knb, k1.kselfy);
+                const float4 nb0 = upwind4(b[k][0], bL, b[k][1], km0, kp0, k0.kself, k0.kselfy);
+                const float4 nb1 = upwind4(b[k][1], b[k][0], bR, km1, kp1, k1.kself, k1.kselfy);
                 b[k][0] = nb0; b[k][1] = nb1;
             }
             a[k][0] = na0; a[k][1] = na1;
@@ -339,8 +357,9 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
                 const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
                 const Coef kk = coefficients<LITERAL>(vm, vp, mi, pi, src, dt, sdt, bad, row_in && col_in[q]);
-                na[q] = step4(a[k][q], kk.minus ? prev_a[q] : next_a[q], kk.kself, kk.knb);
-                if (has1) nb[q] = step4y(b[k][q], sel4(kk.minus, prev_b[q], next_b[q]), kk.kself, kk.knb, kk.kselfy);
+                const float km = kk.minus ? kk.knb : 0.0f, kp = kk.minus ? 0.0f : kk.knb;
+                na[q] = upwind4(a[k][q], prev_a[q], next_a[q], km, kp, kk.kself, kk.kself);
+                if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], km, kp, kk.kself, kk.kselfy);
                 if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
                 prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
                 a[k][q] = na[q];
