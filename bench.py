@@ -45,9 +45,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "f1af968a07d6bf03",
-    "scene512_k_propagate_bytes": 9_484_544 + 768,
-    "batch_k_propagate_bytes": 1_069_902_592 + 1_020_444_672,
+    "kernel_sources_sha256_16": "898c4945ea6a7e8c",
+    "scene512_k_propagate_bytes": 9_487_104 + 3_840,
+    "batch_k_propagate_bytes": 1_070_515_200 + 1_020_592_896,
 }
 
 
@@ -299,8 +299,10 @@ def run_ours(args):
     ranges = torch.from_numpy(seq.range).to(dev)
     flow = torch.empty((3, H, W), device=dev)
     inv = torch.empty((H, W), device=dev)
+    tuned = not (args.nf_max or args.update_mode)
     params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
-                       flags=sf.CHECK_CFL | sf.AUTOTUNE)
+                       flags=sf.CHECK_CFL | (sf.AUTOTUNE if tuned else 0), nf_max=args.nf_max or None,
+                       update_mode=args.update_mode or None)
     filt = sf.Filter(H, W, seq.levels, params)
     nf_max = filt.nf_max()       # the autotuner's choices: sub-iterations per propagation launch,
     update_mode = filt.update_mode()   # and the form of the update
@@ -387,7 +389,7 @@ def run_ours(args):
                        + ("" if args.size == 512 else f", tiled to {args.size}x{args.size} (profiling case)"),
                        "global_batch": ws, "streams_per_gpu": 1, "parallelism": f"replicas x{ws}",
                        "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)",
-                       "nf_max": nf_max, "update_mode": update_mode, "autotune": True},
+                       "nf_max": nf_max, "update_mode": update_mode, "autotune": tuned},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
@@ -783,6 +785,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=512, help="frame size (multiple of 512); >512 is a profiling case")
     ap.add_argument("--quick", action="store_true", help="skip the e2e, oracle-EPE, CPU-baseline and batched legs")
+    ap.add_argument("--nf-max", type=int, default=0,
+                    help="sub-iterations per propagation launch (skips the autotuner; for profiling)")
+    ap.add_argument("--update-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="form of the update (skips the autotuner; for profiling)")
     ap.add_argument("--workload", choices=["scene512", "batch", "surrogate", "conv"], default="scene512",
                     help="batch / surrogate: only that configuration, as its own line")
     args = ap.parse_args()
