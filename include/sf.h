@@ -391,6 +391,14 @@ int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const 
 int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w,
                const float* bias, int relu, void* y, float* y32, int* status, void* stream);
 
+/* Self-test of the convolution's bounded wait: runs one tile whose MMAs are
+ * never issued, so its mbarrier wait cannot complete; the kernel gives up
+ * after a short poll limit, sets the timeout bit, frees its tensor memory and
+ * returns.  Returns SF_ETIMEOUT when that happened (the expected outcome),
+ * SF_OK when the wait somehow completed, another code on a CUDA error.  The
+ * device stays usable afterwards.  Waits for `stream`. */
+int sf_selftest_conv_timeout(void* stream);
+
 /* The surrogate network: 4 such layers, 16 -> 32 -> 32 -> 32 -> 16 channels,
  * ReLU after the first three.  Input features of a pixel of the top level:
  * w / (4 dmu) (3 channels, px/frame over 4), rho, eta_x, eta_y, 10 zeros;

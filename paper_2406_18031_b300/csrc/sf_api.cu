@@ -1348,6 +1348,7 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     a.tiles_x = ceil_div(W, kConvM);
     a.n_tiles = N * H * a.tiles_x;
     a.status = status;
+    a.spin_limit = kConvSpinLimit;
     const size_t smem = conv_smem_bytes(Cin, Cout);
     if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
     // strips of up to 32 rows, shorter when that leaves fewer than 4 per SM
@@ -1448,6 +1449,37 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
 }
 
 }  // namespace
+
+int sf_selftest_conv_timeout(void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    // one tile: 1 x 1 x 128 pixels, 16 -> 16 channels, zero data
+    const size_t xb = 128 * 16 * 2, wb = 9 * 16 * 16 * 2, yb = 128 * 16 * 2;
+    unsigned char* mem = nullptr;
+    if (cudaMallocAsync((void**)&mem, xb + wb + yb + 256, st) != cudaSuccess) return SF_ENOMEM;
+    int r = cudaMemsetAsync(mem, 0, xb + wb + yb + 256, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = 1; a.H = 1; a.W = 128; a.Cin = 16; a.Cout = 16;
+    a.x = (const __nv_bfloat16*)mem;
+    a.w = (const __nv_bfloat16*)(mem + xb);
+    a.y = (__nv_bfloat16*)(mem + xb + wb);
+    a.tiles_x = 1; a.n_tiles = 1; a.strip = 1;
+    a.status = (int*)(mem + xb + wb + yb);
+    a.spin_limit = 1024;      // a short limit: the test ends in well under a second
+    a.no_commit = 1;          // nothing is issued, so the wait cannot complete
+    if (!r && set_smem_attr((const void*)k_conv3x3, conv_smem_bytes(16, 16))) r = SF_ECUDA;
+    if (!r) {
+        k_conv3x3<<<1, kConvThreads, conv_smem_bytes(16, 16), st>>>(a);
+        r = last_error();
+    }
+    int s = 0;
+    if (!r) r = cudaMemcpyAsync(&s, a.status, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaFreeAsync(mem, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (r) return r;
+    return (s & kStatusTimeout) ? SF_ETIMEOUT : SF_OK;
+}
 
 int sf_surrogate_create(unsigned long long seed, sf_surrogate** out)
 {

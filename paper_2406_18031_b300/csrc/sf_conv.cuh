@@ -39,6 +39,8 @@ struct ConvArgs {
     int tiles_x;                 // ceil(W / 128)
     int n_tiles;                 // N * H * tiles_x
     int strip;                   // output rows per strip (a CTA's unit of work), 1 .. kConvStrip
+    int spin_limit;              // polls of an mbarrier before a wait gives up
+    int no_commit;               // self-test of the bounded wait: issue nothing, so no wait completes
     int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
@@ -87,9 +89,9 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar)
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit)
 {
-    for (int it = 0; it < kConvSpinLimit; ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             const int buf = y & 1;
-            if (tid == 0) {
+            if (tid == 0 && !a.no_commit) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 int first = 1;
                 for (int tap = 0; tap < 9; ++tap) {
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
             ++pending;
             if (y > y_begin) {
                 const int pb = buf ^ 1;
-                const bool done = mbar_wait(mb[pb], phase[pb]);
+                const bool done = mbar_wait(mb[pb], phase[pb], a.spin_limit);
                 if (!__syncthreads_and(done)) { failed = true; break; }
                 phase[pb] ^= 1u;
                 --pending;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
         if (failed) break;
         // drain: the strip's last row
         const int lb = (y_end - 1) & 1;
-        const bool done = mbar_wait(mb[lb], phase[lb]);
+        const bool done = mbar_wait(mb[lb], phase[lb], a.spin_limit);
         if (!__syncthreads_and(done)) { failed = true; break; }
         phase[lb] ^= 1u;
         --pending;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
         if (tid == 0 && a.status) atomicOr(a.status, kStatusTimeout);
         // a second bounded wait for the groups still in flight (oldest first)
         for (int b = 0; b < 2 && pending > 0; ++b)
-            if (mbar_wait(mb[b], phase[b])) --pending;
+            if (mbar_wait(mb[b], phase[b], a.spin_limit)) --pending;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (warp == 0) {

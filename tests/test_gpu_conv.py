@@ -63,3 +63,10 @@ def test_conv_larger_frame():
 
 def test_conv_narrow_image():
     _case(3, 9, 37, 16, 32, False, seed=4)
+
+
+def test_bounded_wait_gives_up_and_leaves_the_device_usable():
+    # a tile whose MMAs are never issued: its completion wait cannot succeed;
+    # the kernel must report the timeout, free its tensor memory and return
+    assert sf.lib().sf_selftest_conv_timeout(None) == sf.ETIMEOUT
+    _case(1, 3, 130, 16, 16, True, seed=5)       # and the next convolution still works
