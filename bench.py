@@ -372,13 +372,14 @@ def run_ours(args):
         achieved = bpl / (prop_ms / 1e3) / 1e9
         frame_bytes = algorithmic_bytes_per_frame(H, W, seq.levels)
         if args.quick:
-            e2e, (mean_epe, max_epe), cpu, batched, imu, remap, surrogate = (None, (None, None), None, None, None,
-                                                                              None, None)
+            e2e, (mean_epe, max_epe), cpu, batched, imu, remap, surrogate, frame1024 = (
+                None, (None, None), None, None, None, None, None, None)
         else:
             e2e = measure_e2e(filt, seq, args.steps)
             imu = measure_imu(seq, images, ranges, min(args.steps, 100), evict_l2)
             remap = measure_remap(seq, images, ranges, min(args.steps, 100), evict_l2)
             surrogate = measure_surrogate(min(args.steps, 30), dev)
+            frame1024 = measure_1024(min(args.steps, 100), evict_l2, dev)
             mean_epe, max_epe = epe_vs_oracle(seq, frames=3)
             cpu = cpu_baseline(seq)
             filt.close()
@@ -415,6 +416,7 @@ def run_ours(args):
             "imu": imu,
             "remap": remap,
             "surrogate": surrogate,
+            "frame1024": frame1024,
             "batched": batched,
             "gpu_launches": kstep * args.steps,
             "clocks": clocks,
@@ -759,6 +761,45 @@ def measure_surrogate(steps, dev):
                     if out["plain"]["ms_per_step"] > out["surrogate"]["ms_per_step"]
                     else "the surrogate-plus-batched form is slower than the plain GPU form"),
     }
+
+
+PAPER_HZ_1024 = 172.149   # the paper's rate at 1024x1024, 2 levels, max flow 8 px (same table, GTX-780)
+
+
+def measure_1024(steps, evict_l2, dev):
+    """The paper's second configuration: 1024 x 1024, 2 levels, N = [8, 4],
+    smoothing [2, 4] (the 512 x 512 scene tiled 2 x 2 with a 90-degree field
+    of view), autotuned, cold L2 before each timed frame."""
+    import torch
+    from paper_2406_18031_b300 import sf
+    seq = make_sequence(1001, 8, 1024)
+    H, W = seq.shape
+    images = torch.from_numpy(seq.image).to(dev)
+    ranges = torch.from_numpy(seq.range).to(dev)
+    flow = torch.empty((3, H, W), device=dev)
+    inv = torch.empty((H, W), device=dev)
+    params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
+                       flags=sf.CHECK_CFL | sf.AUTOTUNE)
+    filt = sf.Filter(H, W, seq.levels, params)
+    stream = torch.cuda.current_stream()
+    for k in range(4):
+        filt.step(images[k % 8], ranges[k % 8], seq.dt, flow, inv, stream=stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        evict_l2(k)
+        ev[k][0].record(stream)
+        filt.step(images[1 + k % 7], ranges[1 + k % 7], seq.dt, flow, inv, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    out = {"workload": "1024x1024, 2 levels, N=[8,4], smooth=[2,4] (scene512 tiled 2x2), cold L2",
+           "frames_per_s": 1e3 / ms, "ms_per_step": ms, "nf_max": filt.nf_max(),
+           "update_mode": filt.update_mode(), "vs_paper": 1e3 / ms / PAPER_HZ_1024,
+           "hbm_gbs_algorithmic": algorithmic_bytes_per_frame(H, W, seq.levels) / (ms / 1e3) / 1e9,
+           "status": sf.strerror(filt.status())}
+    out["hbm_frac_of_peak"] = out["hbm_gbs_algorithmic"] / measured_peaks()[0]["hbm_gbs"]
+    filt.close()
+    return out
 
 
 def measure_e2e(filt, seq, steps):
