@@ -91,23 +91,6 @@ __device__ __forceinline__ PixGeo pix_geo(float x, float y, float a)
     return o;
 }
 
-// One explicit Euler step of an axis pass (Eqs. 59-66) for the four channels
-// of a float4: f - dt [s D + f src] with D the upwind difference (Eqs. 57-58)
-// is A f - |c| (f - f_up) = (A - |c|) f + |c| f_up, c = dt s, A = 1 - sdt src;
-// at an image border the replicated neighbour gives D = 0 (kself = A, knb = 0).
-__device__ __forceinline__ float4 step4(float4 f, float4 up, float kself, float knb)
-{
-    return make_float4(fmaf(kself, f.x, knb * up.x), fmaf(kself, f.y, knb * up.y),
-                       fmaf(kself, f.z, knb * up.z), fmaf(kself, f.w, knb * up.w));
-}
-
-// the same for (dw, Y): Y carries no source term (Eq. 62): (1 - |c|) Y + |c| Y_up
-__device__ __forceinline__ float4 step4y(float4 f, float4 up, float kself, float knb, float kselfy)
-{
-    return make_float4(fmaf(kself, f.x, knb * up.x), fmaf(kself, f.y, knb * up.y),
-                       fmaf(kself, f.z, knb * up.z), fmaf(kselfy, f.w, knb * up.w));
-}
-
 __device__ __forceinline__ float4 shfl_up4(float4 v)
 {
     return make_float4(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1),
@@ -120,10 +103,13 @@ __device__ __forceinline__ float4 shfl_down4(float4 v)
                        __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
 }
 
-// The same step without selecting the upwind neighbour: with km = c on the
-// minus side and kp = c on the plus side (the other one 0),
-// f' = ks f + km f_minus + kp f_plus, two channels per packed FP32x2
-// instruction; ksw is the self weight of the fourth channel (Y: no source).
+// One explicit Euler step of an axis pass (Eqs. 59-66) for the four channels
+// of a float4: f - dt [s D + f src] with D the upwind difference (Eqs. 57-58)
+// is A f - c (f - f_up) with c = dt |s| and A = 1 - sdt src.  Written without
+// selecting the upwind neighbour: with km = c on the minus side and kp = c on
+// the plus side (the other one 0), f' = ks f + km f_minus + kp f_plus,
+// ks = A - c, two channels per packed FP32x2 instruction; ksw is the self
+// weight of the fourth channel (Y: no source, ksw = 1 - c).
 __device__ __forceinline__ float4 upwind4(float4 f, float4 fm, float4 fp, float km, float kp, float ks, float ksw)
 {
     const float2 km2 = make_float2(km, km), kp2 = make_float2(kp, kp);
@@ -136,32 +122,29 @@ __device__ __forceinline__ float4 upwind4(float4 f, float4 fm, float4 fp, float 
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-__device__ __forceinline__ float4 sel4(bool c, float4 a, float4 b)
-{
-    return make_float4(c ? a.x : b.x, c ? a.y : b.y, c ? a.z : b.z, c ? a.w : b.w);
-}
-
-// Coefficients of one pixel for one pass: upwind side (true = minus side),
-// weights on itself and on the upwind neighbour, and on itself for Y.
+// Coefficients of one pixel for one pass: weights on the minus and plus
+// neighbours (one of them zero: the upwind side of Eqs. 57-58), on itself,
+// and on itself for Y.  v = dt s-hat (s-hat the dominant speed of Eqs.
+// 55-56): km = max(v, 0) on the minus side, kp = max(-v, 0) on the plus side;
+// hm, hp (1 or 0) drop the neighbour beyond the image border (replicated
+// border: D = 0).  kself = A - km - kp with A = 1 - sdt src.
 struct Coef {
-    bool minus;
-    float kself, knb, kselfy;
+    float km, kp, kself, kselfy;
 };
 
 template <bool LITERAL>
-__device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, bool has_minus, bool has_plus,
-                                             float src, float dt, float sdt, bool& bad, bool count)
+__device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, float hm, float hp, float src, float dt,
+                                             float sdt, bool& bad, bool count)
 {
     const float sh = dominant(s_minus, s_plus, LITERAL ? kDominantLiteral : 0);   // Eqs. 55-56
-    const float c = fabsf(dt * sh);
-    bad |= count && (c > 1.0f);                          // Eq. 67
+    const float v = dt * sh;
+    bad |= count && (fabsf(v) > 1.0f);                                          // Eq. 67
     Coef k;
-    k.minus = sh > 0.0f;                                 // Eqs. 57-58: backward difference
-    const bool has = k.minus ? has_minus : has_plus;     // replicated border: D = 0
-    const float A = fmaf(-sdt, src, 1.0f);
-    k.knb = has ? c : 0.0f;
-    k.kself = A - k.knb;
-    k.kselfy = 1.0f - k.knb;
+    k.km = hm * fmaxf(v, 0.0f);                                                 // Eqs. 57-58: backward difference
+    k.kp = hp * fmaxf(-v, 0.0f);
+    const float knb = k.km + k.kp;
+    k.kself = fmaf(-sdt, src, 1.0f) - knb;
+    k.kselfy = 1.0f - knb;
     return k;
 }
 
@@ -291,17 +274,17 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             const bool m0 = j0 > 0, p0 = j0 < g.W - 1, m1 = j1 > 0, p1 = j1 < g.W - 1;
             const float sm0 = m0 ? uL : sp[k][0], spp0 = p0 ? sp[k][1] : sp[k][0];
             const float sm1 = m1 ? sp[k][0] : sp[k][1], spp1 = p1 ? uR : sp[k][1];
-            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0, p0, src0, dt, sdt, bad, row_in && col_in[0]);
-            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1, p1, src1, dt, sdt, bad, row_in && col_in[1]);
+            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0 ? 1.0f : 0.0f, p0 ? 1.0f : 0.0f, src0, dt, sdt, bad,
+                                                  row_in && col_in[0]);
+            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1 ? 1.0f : 0.0f, p1 ? 1.0f : 0.0f, src1, dt, sdt, bad,
+                                                  row_in && col_in[1]);
             const float4 aL = shfl_up4(a[k][1]), aR = shfl_down4(a[k][0]);
-            const float km0 = k0.minus ? k0.knb : 0.0f, kp0 = k0.minus ? 0.0f : k0.knb;
-            const float km1 = k1.minus ? k1.knb : 0.0f, kp1 = k1.minus ? 0.0f : k1.knb;
-            const float4 na0 = upwind4(a[k][0], aL, a[k][1], km0, kp0, k0.kself, k0.kself);
-            const float4 na1 = upwind4(a[k][1], a[k][0], aR, km1, kp1, k1.kself, k1.kself);
+            const float4 na0 = upwind4(a[k][0], aL, a[k][1], k0.km, k0.kp, k0.kself, k0.kself);
+            const float4 na1 = upwind4(a[k][1], a[k][0], aR, k1.km, k1.kp, k1.kself, k1.kself);
             if (has1) {
                 const float4 bL = shfl_up4(b[k][1]), bR = shfl_down4(b[k][0]);
-                const float4 nb0 = upwind4(b[k][0], bL, b[k][1], km0, kp0, k0.kself, k0.kselfy);
-                const float4 nb1 = upwind4(b[k][1], b[k][0], bR, km1, kp1, k1.kself, k1.kselfy);
+                const float4 nb0 = upwind4(b[k][0], bL, b[k][1], k0.km, k0.kp, k0.kself, k0.kselfy);
+                const float4 nb1 = upwind4(b[k][1], b[k][0], bR, k1.km, k1.kp, k1.kself, k1.kselfy);
                 b[k][0] = nb0; b[k][1] = nb1;
             }
             a[k][0] = na0; a[k][1] = na1;
@@ -356,10 +339,10 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 const float4 G = geo[r * kPrW + q * 32 + lane];
                 const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
                 const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
-                const Coef kk = coefficients<LITERAL>(vm, vp, mi, pi, src, dt, sdt, bad, row_in && col_in[q]);
-                const float km = kk.minus ? kk.knb : 0.0f, kp = kk.minus ? 0.0f : kk.knb;
-                na[q] = upwind4(a[k][q], prev_a[q], next_a[q], km, kp, kk.kself, kk.kself);
-                if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], km, kp, kk.kself, kk.kselfy);
+                const Coef kk = coefficients<LITERAL>(vm, vp, mi ? 1.0f : 0.0f, pi ? 1.0f : 0.0f, src, dt, sdt, bad,
+                                                      row_in && col_in[q]);
+                na[q] = upwind4(a[k][q], prev_a[q], next_a[q], kk.km, kk.kp, kk.kself, kk.kself);
+                if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], kk.km, kk.kp, kk.kself, kk.kselfy);
                 if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
                 prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
                 a[k][q] = na[q];
