@@ -11,7 +11,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 LIB = PKG / "libsf.so"
 SOURCES = [CSRC / "sf_api.cu"]
-DEPS = SOURCES + [CSRC / "sf_kernels.cuh", CSRC / "sf_device.cuh", ROOT / "include" / "sf.h"]
+DEPS = SOURCES + sorted(CSRC.glob("*.cuh")) + [ROOT / "include" / "sf.h"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -29,7 +29,9 @@ def _t(a):
 
 # ------------------------------------------------------------------ propagation
 
-@pytest.mark.parametrize("H,W", [(80, 72), (33, 47), (8, 8)])
+# 200 x 184 has regions clear of the image border on every side (the
+# kernel's interior copy); the others are border regions only
+@pytest.mark.parametrize("H,W", [(80, 72), (33, 47), (8, 8), (200, 184)])
 @pytest.mark.parametrize("N", [1, 3, 8, 12, 20])
 @pytest.mark.parametrize("top", [True, False])
 @pytest.mark.parametrize("flags", [0, oracle.SOURCE_SPLIT])
@@ -66,7 +68,7 @@ def test_propagate_matches_oracle(H, W, N, top, flags):
         assert bool(int(status.item()) & 1) == (cfl > 1.0), cfl
 
 
-@pytest.mark.parametrize("H,W", [(80, 72), (33, 47)])
+@pytest.mark.parametrize("H,W", [(80, 72), (33, 47), (200, 184)])
 @pytest.mark.parametrize("N", [1, 3, 12])
 @pytest.mark.parametrize("top", [True, False])
 def test_propagate_inertial_terms_match_oracle(H, W, N, top):
