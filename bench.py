@@ -49,9 +49,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "898c4945ea6a7e8c",
-    "scene512_k_propagate_bytes": 9_487_104 + 3_840,
-    "batch_k_propagate_bytes": 1_070_515_200 + 1_020_592_896,
+    "kernel_sources_sha256_16": "d9ce8842592997e1",
+    "scene512_k_propagate_bytes": 9_483_776 + 1_792,
+    "batch_k_propagate_bytes": 1_069_955_840 + 1_019_135_488,
 }
 
 
@@ -803,26 +803,39 @@ def measure_1024(steps, evict_l2, dev):
 
 
 def measure_e2e(filt, seq, steps):
-    """Same metric through sf_step_host: pinned host inputs copied in, the step,
-    the flow and inverse depth copied out, every step."""
+    """Same metric through the host-buffer API, every step copying its pinned
+    host inputs in and its flow and inverse depth out: sf_submit_host (input
+    copy, step and output copy of consecutive frames overlap; a ring of 4 host
+    output buffers, each reused after its frame's sf_wait_host), and, for
+    comparison, the synchronous sf_step_host."""
     import torch
     H, W = seq.shape
     imgs = torch.from_numpy(seq.image).pin_memory()
     rngs = torch.from_numpy(seq.range).pin_memory()
-    flow = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
-    inv = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    fa, ia = flow.numpy(), inv.numpy()
     ims, rgs = imgs.numpy(), rngs.numpy()
+    ring = 4
+    outs = [(torch.empty((3, H, W), dtype=torch.float32).pin_memory().numpy(),
+             torch.empty((H, W), dtype=torch.float32).pin_memory().numpy()) for _ in range(ring)]
+    st = torch.cuda.Stream()
     for k in range(3):
-        filt.step_host(ims[k], rgs[k], seq.dt, fa, ia)
+        filt.wait_host(filt.submit_host(ims[k], rgs[k], seq.dt, *outs[0], stream=st))
     torch.cuda.synchronize()
+    tickets = []
     t0 = time.perf_counter()
     for k in range(steps):
-        kk = k % seq.frames
-        filt.step_host(ims[kk], rgs[kk], seq.dt, fa, ia)
+        if k >= ring:
+            filt.wait_host(tickets[k - ring])
+        tickets.append(filt.submit_host(ims[k % seq.frames], rgs[k % seq.frames], seq.dt, *outs[k % ring], stream=st))
+    filt.wait_host()
     el = time.perf_counter() - t0
+    fa, ia = outs[0]
+    t1 = time.perf_counter()
+    for k in range(steps):
+        filt.step_host(ims[k % seq.frames], rgs[k % seq.frames], seq.dt, fa, ia)
+    el_sync = time.perf_counter() - t1
     return {"value": steps / el, "unit": "frames/s", "h2d_bytes_per_step": 2 * H * W * 4,
-            "d2h_bytes_per_step": 4 * H * W * 4}
+            "d2h_bytes_per_step": 4 * H * W * 4, "api": "sf_submit_host / sf_wait_host (pipelined, pinned)",
+            "sync_step_host_value": steps / el_sync}
 
 
 def main():

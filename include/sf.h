@@ -139,9 +139,34 @@ int sf_step(sf_ctx* c, const float* image, const float* range, float dt,
 
 /* sf_step on HOST buffers: copies image and range to the device, runs the
  * step and copies the outputs back, all on `stream`, then waits for the
- * stream.  Pinned host buffers make the copies run at full speed. */
+ * stream.  Pinned host buffers make the copies run at full speed.  image and
+ * range hold H x W floats each. */
 int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt,
                  float* flow_out, float* invdepth_out, void* stream);
+
+/* Pipelined sf_step on HOST buffers, for a stream of frames: enqueues the
+ * copy of image and range to a device staging slot (on a copy stream of the
+ * context), the step (on `stream`) and the copy of the outputs back to
+ * flow_out / invdepth_out (on a second copy stream), then returns without
+ * waiting.  Frame k's input copy, frame k-1's step and frame k-2's output
+ * copy can so run at the same time; three staging slots, reused in turn
+ * (about 72 bytes per level-1 pixel, allocated by the first call).  Same
+ * arguments and meaning as sf_step_host (host pointers; dt > 0 and finite,
+ * else SF_EINVAL).  *ticket (if not NULL) receives the frame's number, 0 for
+ * the first call, -1 on error.  The caller keeps image and range unchanged,
+ * and flow_out / invdepth_out unread and alive, until sf_wait_host(c, ticket)
+ * returns.  Pinned host memory (cudaHostAlloc / cudaHostRegister) lets the
+ * call return at once; with pageable memory the CUDA runtime may wait inside
+ * the copies.  Frames are processed in submission order; mixing with sf_step
+ * on the same stream keeps that order. */
+int sf_submit_host(sf_ctx* c, const float* image, const float* range, float dt,
+                   float* flow_out, float* invdepth_out, void* stream, long long* ticket);
+
+/* Wait until the outputs of frame `ticket` (from sf_submit_host; -1 = every
+ * frame submitted so far) are in host memory, and its inputs are no longer
+ * read.  SF_EINVAL for a NULL context or a ticket not yet issued; SF_ECUDA
+ * if the wait failed. */
+int sf_wait_host(sf_ctx* c, long long ticket);
 
 /* Synchronise the device and return the sticky status recorded since the
  * last call (and clear it): SF_ENONFINITE, then SF_WARN_CFL, else SF_OK. */

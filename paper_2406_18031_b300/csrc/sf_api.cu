@@ -754,6 +754,11 @@ int engine_status(Engine& E)
 
 }  // namespace
 
+// staging slots of the pipelined host-buffer steps: frame k uses slot k % kRing;
+// frame k's completion is marked by event k % kDone (host waits)
+constexpr int kRing = 3;
+constexpr int kDone = 64;
+
 struct sf_ctx {
     Engine E;
     // staging for sf_step_host
@@ -761,6 +766,14 @@ struct sf_ctx {
     float* stage_range = nullptr;
     float* stage_flow = nullptr;
     float* stage_inv = nullptr;
+    // sf_submit_host: per slot image, range, flow (3 planes), inverse depth on
+    // the device; input copies on pipe_in, output copies on pipe_out, the step
+    // on the caller's stream; events order the three and guard slot reuse
+    float* ring[kRing] = {};
+    cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaEvent_t ev_in[kRing] = {}, ev_run[kRing] = {}, ev_out[kRing] = {};
+    cudaEvent_t ev_done[kDone] = {};
+    long long submitted = 0;
 };
 
 struct sf_batch {
@@ -772,12 +785,45 @@ namespace {
 void destroy_ctx(sf_ctx* c)
 {
     if (!c) return;
+    if (c->pipe_in) cudaStreamSynchronize(c->pipe_in);
+    if (c->pipe_out) cudaStreamSynchronize(c->pipe_out);
     engine_free(c->E);
     cudaFree(c->stage_image);
     cudaFree(c->stage_range);
     cudaFree(c->stage_flow);
     cudaFree(c->stage_inv);
+    for (int k = 0; k < kRing; ++k) {
+        cudaFree(c->ring[k]);
+        if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+        if (c->ev_run[k]) cudaEventDestroy(c->ev_run[k]);
+        if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+    }
+    for (int k = 0; k < kDone; ++k)
+        if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+    if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
+    if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
     delete c;
+}
+
+// first sf_submit_host: the staging ring, the two copy streams (non-blocking,
+// so that they never wait on the legacy default stream implicitly) and the
+// events (no timing)
+int pipe_init(sf_ctx* c)
+{
+    const size_t n = (size_t)c->E.st[0].H * c->E.st[0].W;
+    for (int k = 0; k < kRing; ++k) {
+        if (cudaMalloc(&c->ring[k], 6 * n * sizeof(float)) != cudaSuccess) return SF_ENOMEM;
+        if (cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_run[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming) != cudaSuccess)
+            return SF_ECUDA;
+    }
+    for (int k = 0; k < kDone; ++k)
+        if (cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming) != cudaSuccess) return SF_ECUDA;
+    if (cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking) != cudaSuccess)
+        return SF_ECUDA;
+    return SF_OK;
 }
 
 void destroy_batch(sf_batch* b)
@@ -886,6 +932,64 @@ int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, fl
         cudaMemcpyAsync(invdepth_out, c->stage_inv, n * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SF_ECUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+int sf_submit_host(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out,
+                   float* invdepth_out, void* stream, long long* ticket)
+{
+    if (ticket) *ticket = -1;
+    if (!c || !image || !range || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
+    if (!c->pipe_in) {
+        const int r = pipe_init(c);
+        if (r) return r;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->E.st[0].H * c->E.st[0].W;
+    const long long k = c->submitted;
+    const int s = (int)(k % kRing);
+    float* img = c->ring[s];
+    float* rng = img + n;
+    float* flow = rng + n;
+    float* inv = flow + 3 * n;
+    // inputs: the slot was last read by the step of frame k - kRing
+    if (k >= kRing && cudaStreamWaitEvent(c->pipe_in, c->ev_run[s], 0) != cudaSuccess) return SF_ECUDA;
+    if (cudaMemcpyAsync(img, image, n * sizeof(float), cudaMemcpyHostToDevice, c->pipe_in) != cudaSuccess ||
+        cudaMemcpyAsync(rng, range, n * sizeof(float), cudaMemcpyHostToDevice, c->pipe_in) != cudaSuccess ||
+        cudaEventRecord(c->ev_in[s], c->pipe_in) != cudaSuccess)
+        return SF_ECUDA;
+    // the step: after its inputs, and after the slot's previous outputs left
+    if (cudaStreamWaitEvent(st, c->ev_in[s], 0) != cudaSuccess ||
+        (k >= kRing && cudaStreamWaitEvent(st, c->ev_out[s], 0) != cudaSuccess))
+        return SF_ECUDA;
+    const int r = sf_step(c, img, rng, dt, flow_out ? flow : nullptr, invdepth_out ? inv : nullptr, stream);
+    if (r) return r;
+    if (cudaEventRecord(c->ev_run[s], st) != cudaSuccess) return SF_ECUDA;
+    // outputs
+    if (cudaStreamWaitEvent(c->pipe_out, c->ev_run[s], 0) != cudaSuccess) return SF_ECUDA;
+    if (flow_out && cudaMemcpyAsync(flow_out, flow, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, c->pipe_out) !=
+                        cudaSuccess)
+        return SF_ECUDA;
+    if (invdepth_out &&
+        cudaMemcpyAsync(invdepth_out, inv, n * sizeof(float), cudaMemcpyDeviceToHost, c->pipe_out) != cudaSuccess)
+        return SF_ECUDA;
+    if (cudaEventRecord(c->ev_out[s], c->pipe_out) != cudaSuccess ||
+        cudaEventRecord(c->ev_done[k % kDone], c->pipe_out) != cudaSuccess)
+        return SF_ECUDA;
+    c->submitted = k + 1;
+    if (ticket) *ticket = k;
+    return SF_OK;
+}
+
+int sf_wait_host(sf_ctx* c, long long ticket)
+{
+    if (!c || ticket >= c->submitted || ticket < -1) return SF_EINVAL;
+    if (ticket == -1) ticket = c->submitted - 1;
+    if (ticket < 0) return SF_OK;   // nothing submitted
+    // event ticket % kDone marks frame ticket while it is one of the last
+    // kDone frames; an older ticket waits for the oldest of those instead
+    // (output copies complete in submission order, so that implies its own)
+    const long long w = std::max(ticket, c->submitted - kDone);
+    return cudaEventSynchronize(c->ev_done[w % kDone]) == cudaSuccess ? SF_OK : SF_ECUDA;
 }
 
 int sf_status(sf_ctx* c)

@@ -42,7 +42,7 @@ class CGrid(ctypes.Structure):
 
 _lib = None
 
-EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_status", "sf_get_state",
+EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_submit_host", "sf_wait_host", "sf_status", "sf_get_state",
            "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_update_mode", "sf_set_motion", "sf_propagate_imu", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_update_mode", "sf_batch_motion", "sf_batch_profile",
@@ -67,6 +67,8 @@ def lib():
         L.sf_reset.argtypes = [vp]
         L.sf_step.argtypes = [vp, vp, vp, f, vp, vp, vp]
         L.sf_step_host.argtypes = [vp, vp, vp, f, vp, vp, vp]
+        L.sf_submit_host.argtypes = [vp, vp, vp, f, vp, vp, vp, P(ctypes.c_longlong)]
+        L.sf_wait_host.argtypes = [vp, ctypes.c_longlong]
         L.sf_status.argtypes = [vp]
         L.sf_get_state.argtypes = [vp, i, vp, P(f), vp]
         L.sf_set_state.argtypes = [vp, i, vp, f, vp]
@@ -213,6 +215,25 @@ class Filter:
             return ctypes.c_void_p(a.ctypes.data)
         return _check(lib().sf_step_host(self._h, hp(image), hp(rng), float(dt), hp(flow_out), hp(invdepth_out),
                                          _stream(stream)), "sf_step_host")
+
+    def submit_host(self, image: np.ndarray, rng: np.ndarray, dt, flow_out: np.ndarray | None = None,
+                    invdepth_out: np.ndarray | None = None, stream=None) -> int:
+        """Pipelined frame on host float32 arrays: enqueues the copies and the
+        step and returns the frame's ticket at once.  The arrays must stay
+        alive and unchanged (outputs unread) until ``wait_host(ticket)``."""
+        def hp(a):
+            if a is None:
+                return None
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+            return ctypes.c_void_p(a.ctypes.data)
+        t = ctypes.c_longlong(-1)
+        _check(lib().sf_submit_host(self._h, hp(image), hp(rng), float(dt), hp(flow_out), hp(invdepth_out),
+                                    _stream(stream), ctypes.byref(t)), "sf_submit_host")
+        return t.value
+
+    def wait_host(self, ticket: int = -1):
+        """Wait for frame ``ticket``'s outputs (-1: every submitted frame)."""
+        _check(lib().sf_wait_host(self._h, int(ticket)), "sf_wait_host")
 
     def kernels_per_step(self) -> int:
         return _check(lib().sf_kernels_per_step(self._h), "sf_kernels_per_step")

@@ -97,6 +97,10 @@ def test_calls_on_null_context_fail_cleanly(lib):
     assert lib.sf_reset(None) == sf.EINVAL
     assert lib.sf_step(None, None, None, ctypes.c_float(0.01), None, None, None) == sf.EINVAL
     assert lib.sf_status(None) == sf.EINVAL
+    t = ctypes.c_longlong(7)
+    assert lib.sf_submit_host(None, None, None, ctypes.c_float(0.01), None, None, None, ctypes.byref(t)) == sf.EINVAL
+    assert t.value == -1
+    assert lib.sf_wait_host(None, -1) == sf.EINVAL
     lib.sf_destroy(None)
 
 

@@ -258,6 +258,74 @@ def test_host_buffer_step_matches_device_step():
     assert np.array_equal(fa.cpu().numpy(), fb) and np.array_equal(ia.cpu().numpy(), ib)
 
 
+@pytest.mark.parametrize("memory", ["pinned", "pinned_slices", "pageable"])
+def test_pipelined_host_steps_match_device_steps(memory):
+    """sf_submit_host: every frame's outputs equal those of sf_step on device
+    buffers (the same kernels in the same order), with more frames in flight
+    than staging slots and output buffers reused only after their ticket;
+    pinned, pinned at offsets inside one allocation, and pageable inputs."""
+    seq = scenes.plane64(frames=9)
+    H, W = seq.shape
+    a, _ = _pair(seq)
+    b, _ = _pair(seq)
+    fa = torch.empty((3, H, W), device="cuda"); ia = torch.empty((H, W), device="cuda")
+    ring = 5
+
+    def host(shape):
+        t = torch.empty(shape, dtype=torch.float32)
+        return (t if memory == "pageable" else t.pin_memory()).numpy()
+    if memory == "pinned_slices":
+        block = host((2, seq.frames + 1, H, W))
+        images, ranges = list(block[0, 1:]), list(block[1, 1:])
+    else:
+        images = [host((H, W)) for _ in range(seq.frames)]
+        ranges = [host((H, W)) for _ in range(seq.frames)]
+    for k in range(seq.frames):
+        images[k][:] = seq.image[k]; ranges[k][:] = seq.range[k]
+    outs = [(host((3, H, W)), host((H, W))) for _ in range(ring)]
+    st = torch.cuda.Stream()
+    tickets, want = [], []
+    for k in range(seq.frames):
+        a.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, fa, ia)
+        want.append((fa.cpu().numpy(), ia.cpu().numpy()))
+        if k >= ring:
+            b.wait_host(tickets[k - ring])
+            fo, io = outs[(k - ring) % ring]
+            assert np.array_equal(fo, want[k - ring][0]) and np.array_equal(io, want[k - ring][1]), k - ring
+        fo, io = outs[k % ring]
+        tickets.append(b.submit_host(images[k], ranges[k], seq.dt, fo, io, stream=st))
+    assert tickets == list(range(seq.frames))
+    b.wait_host()
+    for k in range(seq.frames - ring, seq.frames):
+        fo, io = outs[k % ring]
+        assert np.array_equal(fo, want[k][0]) and np.array_equal(io, want[k][1]), k
+    assert b.status() == sf.OK
+
+
+def test_pipelined_host_step_tickets():
+    seq = scenes.plane64(frames=2)
+    H, W = seq.shape
+    g, _ = _pair(seq)
+    g.wait_host()                                  # nothing submitted yet
+    with pytest.raises(RuntimeError):
+        g.wait_host(0)                             # not issued
+    fo = np.empty((3, H, W), np.float32)
+    t = g.submit_host(seq.image[0], seq.range[0], seq.dt, fo, None)
+    assert t == 0
+    with pytest.raises(RuntimeError):
+        g.submit_host(seq.image[1], seq.range[1], 0.0, fo, None)   # dt must be > 0
+    g.wait_host(t)
+    assert np.isfinite(fo).all()
+    # more frames in flight than the library keeps completion events for:
+    # a ticket that old still waits correctly (for a later frame)
+    io = np.empty((H, W), np.float32)
+    tickets = [g.submit_host(seq.image[k % 2], seq.range[k % 2], seq.dt, fo, io) for k in range(70)]
+    assert tickets == list(range(1, 71))
+    g.wait_host(tickets[0])
+    g.wait_host(tickets[-1])
+    assert np.isfinite(fo).all() and np.isfinite(io).all()
+
+
 @pytest.mark.parametrize("H,W,levels", [(8, 8, 1), (16, 24, 2), (32, 40, 3), (40, 56, 2)])
 def test_small_and_ragged_grids(H, W, levels):
     seq = scenes.plane64(frames=4, H=H, W=W, levels=levels, iters=[2] * levels)
