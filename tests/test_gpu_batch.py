@@ -107,3 +107,52 @@ def test_batch_matches_single_stream_filters_and_oracle(nf_max, update_mode):
     assert batch.update_mode() == (update_mode or 1)
     assert batch.nf_max() == (nf_max or 8)
     assert batch.status() in (sf.OK, sf.WARN_CFL)
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled_streams():
+    """The benchmark's batch as it is timed: 64 streams (16 x 256^2 with 2
+    levels, 32 x 512^2 and 16 x 1024^2 with 3), the autotuner on, steady-state
+    steps replayed from CUDA graphs.  Sampled streams (the first and last of
+    each size) against their own single-stream filters every frame, and the
+    first 256^2 stream against the FP64 oracle."""
+    import bench
+    frames = 5
+    seqs = scenes.batch(frames=frames, sizes=bench.BATCH_SIZES, period=bench.BATCH_FRAMES)
+    assert len(seqs) == 64 and sum(q.shape[0] * q.shape[1] for q in seqs) == 26_214_400
+    dt = seqs[0].dt
+    flags = sf.CHECK_CFL | sf.CHECK_FINITE | sf.AUTOTUNE
+    P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth, flags=flags) for q in seqs]
+    batch = sf.Batch([q.shape for q in seqs], [q.levels for q in seqs], P)
+    bounds = np.cumsum([0] + [n for _, n in bench.BATCH_SIZES])
+    sample = sorted({int(b) for b in bounds[:-1]} | {int(b) - 1 for b in bounds[1:]})
+    singles = {s: sf.Filter(*seqs[s].shape, seqs[s].levels, P[s]) for s in sample}
+    q0 = seqs[0]
+    ref = oracle.Filter(*q0.shape, q0.levels, oracle.Params(q0.fx, q0.fy, q0.cx, q0.cy, iters=q0.iters,
+                                                            smooth=q0.smooth))
+    _, _, dmu0 = ref.geometry(0)
+    outs = {s: (torch.empty((3, *seqs[s].shape), device="cuda"), torch.empty(seqs[s].shape, device="cuda"))
+            for s in sample}
+    stream = torch.cuda.Stream()
+    for k in range(frames):
+        with torch.cuda.stream(stream):
+            for s, q in enumerate(seqs):
+                img, rng, _, _ = batch.slots[s]
+                img.copy_(torch.from_numpy(q.image[k]).cuda())
+                rng.copy_(torch.from_numpy(q.range[k]).cuda())
+            batch.step(dt, stream=stream)
+            for s in sample:
+                singles[s].step(torch.from_numpy(seqs[s].image[k]).cuda(), torch.from_numpy(seqs[s].range[k]).cuda(),
+                                dt, outs[s][0], outs[s][1], stream=stream)
+        stream.synchronize()
+        for s in sample:
+            q = seqs[s]
+            _, _, dmu = oracle.geometry(*q.shape, q.fx, q.fy, q.cx, q.cy)
+            e = np.abs(batch.slots[s][2].cpu().numpy().astype(np.float64) - outs[s][0].cpu().numpy()) * dt / dmu[None]
+            assert e.max() <= gu.FLOW_TOL_PX, (k, s, e.max())
+            assert np.abs(batch.slots[s][3].cpu().numpy() - outs[s][1].cpu().numpy()).max() <= gu.RHO_TOL, (k, s)
+        rf, ri = ref.step(q0.image[k], q0.range[k], dt)
+        e = np.abs(batch.slots[0][2].cpu().numpy().astype(np.float64) - rf) * dt / dmu0[None]
+        assert e.max() <= gu.FLOW_TOL_PX, (k, e.max())
+        assert np.abs(batch.slots[0][3].cpu().numpy() - ri).max() <= gu.RHO_TOL, k
+    assert batch.status() in (sf.OK, sf.WARN_CFL)
