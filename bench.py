@@ -49,18 +49,25 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "d9ce8842592997e1",
+    "kernel_sources_sha256_16": "656709a058fc42e0",
     "scene512_k_propagate_bytes": 9_483_776 + 1_792,
     "batch_k_propagate_bytes": 1_069_955_840 + 1_019_135_488,
 }
 
 
 def kernel_sources_hash():
+    """sha256[:16] of the sources the stored k_propagate traffic depends on: the
+    propagation section of sf_kernels.cuh (up to the update section) and
+    sf_device.cuh."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2406_18031_b300", "csrc")
+    with open(os.path.join(csrc, "sf_kernels.cuh"), "rb") as fh:
+        kern = fh.read()
+    a, b = kern.index(b"\n// propagation\n"), kern.index(b"\n// update\n")
     h = hashlib.sha256()
-    for f in ("sf_kernels.cuh", "sf_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2406_18031_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(kern[a:b])
+    with open(os.path.join(csrc, "sf_device.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -407,7 +407,7 @@ struct LevelData {
             }
         }
         Y = ys * 0.25f;
-        rho = nv ? rs / (float)nv : 0.0f;
+        rho = nv ? __fdividef(rs, (float)nv) : 0.0f;
     }
 };
 
@@ -418,7 +418,8 @@ struct LevelData<1> {
         const size_t q = (size_t)i * a.W1 + j;
         Y = __ldg(a.image + q);
         const float lam = __ldg(a.range + q);
-        rho = (lam > 0.0f && isfinite(lam)) ? a.lambda_ref / lam : 0.0f;  // Eq. 8
+        // Eq. 8; the fast divide (2 ulp) is far inside the inverse-depth tolerance
+        rho = (lam > 0.0f && isfinite(lam)) ? __fdividef(a.lambda_ref, lam) : 0.0f;
     }
 };
 
@@ -623,7 +624,7 @@ k_solve(const SolveJob* __restrict__ jobs, const int4* __restrict__ work, UpdArg
             const float cx_ = fmaf(gy, qZ, -gz * qY), cy_ = fmaf(gz, qX, -gx * qZ), cz_ = fmaf(gx, qY, -gy * qX);
             const float cross2 = fmaf(cx_, cx_, fmaf(cy_, cy_, cz_ * cz_));
             const float det = fmaf(G3, G3, fmaf(G3, fmaf(G1, rr2, G2 * qq2), G1 * G2 * cross2));
-            const float inv = 1.0f / det;
+            const float inv = __fdividef(1.0f, det);   // det >= g3^2 > 0
             const float k11 = G1 * fmaf(G2, qq2, G3) * inv;
             const float k22 = G2 * fmaf(G1, rr2, G3) * inv;
             const float k12 = -G1 * G2 * rq * inv;
