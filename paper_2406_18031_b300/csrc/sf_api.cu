@@ -34,6 +34,10 @@ namespace {
 // square output tile is 64 - 2 nf pixels wide); an engine may use fewer
 constexpr int kNfLimit = 8;
 
+// streaming multiprocessors of a B300 (two dies of 74): grid sizes of the
+// grid-stride kernels and the launch-form thresholds are multiples of it
+constexpr int kSmCount = 148;
+
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 Grid make_grid(const sf_grid& s)
@@ -172,8 +176,10 @@ int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* sta
                   cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
-    if (set_smem_attr((const void*)k_smooth_recon, p.smem)) return SF_ECUDA;
-    return launch_pdl(k_smooth_recon, dim3(p.nwork), dim3(kSmoothThreads), p.smem, st, (const SmoothJob*)p.jobs,
+    // more than four CTAs per SM of work: the 4-CTA-per-SM form (see k_smooth_recon)
+    auto* kern = p.nwork > 4 * kSmCount ? k_smooth_recon<4> : k_smooth_recon<3>;
+    if (set_smem_attr((const void*)kern, p.smem)) return SF_ECUDA;
+    return launch_pdl(kern, dim3(p.nwork), dim3(kSmoothThreads), p.smem, st, (const SmoothJob*)p.jobs,
                       (const int4*)p.work, q, inv_dt, check_finite, status, flow, inv);
 }
 
@@ -188,7 +194,7 @@ int launch_recon(const Plan& p, int q, float inv_dt, int check_finite, int* stat
 int launch_reconstruct(const ReconArgs& a, cudaStream_t st)
 {
     const int n = a.H * a.W;
-    const int blocks = std::min(ceil_div(n, kThreads), 148 * 8);
+    const int blocks = std::min(ceil_div(n, kThreads), kSmCount * 8);
     k_reconstruct<<<blocks, kThreads, 0, st>>>(a);
     return last_error();
 }
@@ -726,7 +732,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
                 sf_level_state& lv = s.lv[s.L - 1];
                 const size_t n = (size_t)lv.grid.H * lv.grid.W;
                 if (wscale != 1.0f) {
-                    k_scale_w<<<(int)std::min<size_t>((n + 255) / 256, 148 * 8), 256, 0, st>>>(lv.s0[E.parity], n,
+                    k_scale_w<<<(int)std::min<size_t>((n + 255) / 256, kSmCount * 8), 256, 0, st>>>(lv.s0[E.parity], n,
                                                                                               wscale);
                     if (last_error()) return SF_ECUDA;
                 }
@@ -1457,9 +1463,9 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
     // strips of up to 32 rows, shorter when that leaves fewer than 4 per SM
     const int columns = N * a.tiles_x;
-    a.strip = std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(148 * 4, columns)))));
+    a.strip = std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(kSmCount * 4, columns)))));
     const int strips = columns * ceil_div(H, a.strip);
-    const int grid = std::min(strips, 148 * 4);
+    const int grid = std::min(strips, kSmCount * 4);
     k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
     return last_error();
 }
@@ -1531,7 +1537,7 @@ int conv_launch(const sf_surrogate* s, int N, int H, int W, int cin, int cout, c
     return sf_conv3x3(N, H, W, cin, cout, x, w, b, relu, y, y32, s->status, st);
 }
 
-inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 148 * 8); }
+inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, kSmCount * 8); }
 
 // features, the four layers (the three hidden activations kept for the
 // backward pass), FP32 output in y32
@@ -1698,7 +1704,7 @@ int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const floa
     // backward: dy of layer l is `d`, its input activation `in`
     const __nv_bfloat16* d = s->dy;
     __nv_bfloat16* bufs[2] = {s->dA, s->dB};
-    const int wg_blocks = std::min(n * g->H * ((g->W + 127) / 128), 148 * 2);
+    const int wg_blocks = std::min(n * g->H * ((g->W + 127) / 128), kSmCount * 2);
     for (int l = sf_surrogate::kL - 1; l >= 0 && !r; --l) {
         const __nv_bfloat16* in = l == 0 ? s->x0 : s->a[l - 1];
         const size_t wsm = wgrad_smem_bytes(s->cin[l], s->cout[l]);

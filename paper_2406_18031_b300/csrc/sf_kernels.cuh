@@ -711,7 +711,12 @@ __device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, in
 // tile columns.  A line is one thread's work: no barrier between passes.
 // At the image border the line ends are the image's; inside the image the
 // region's halo of 2S pixels absorbs the effect of the cut.
-__global__ void __launch_bounds__(kSmoothThreads)
+// MINB: the CTAs per SM the register allocation must allow -- 3 for launches
+// of about one wave, where a CTA's latency sets the launch time; 4 (64
+// registers, a few bytes spilled) for many-wave launches, where a fourth CTA
+// per SM overlaps its loads with the others' passes
+template <int MINB>
+__global__ void __launch_bounds__(kSmoothThreads, MINB)
 k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work, int q, float inv_dt,
                int check_finite, int* __restrict__ status, float* frame_flow, float* frame_inv)
 {
