@@ -995,7 +995,7 @@ struct ReconJob {
     int frame_outputs;         // level 1 of a single-stream filter: the launch's output pointers
 };
 
-constexpr int kReconChunk = 1024;        // four pixels per thread
+constexpr int kReconChunk = kThreads;    // one pixel per thread: short CTAs that start as SMs free up
 
 __global__ void __launch_bounds__(kThreads) k_recon_jobs(const ReconJob* __restrict__ jobs,
                                                         const int4* __restrict__ work, int q, float inv_dt,
