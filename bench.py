@@ -310,13 +310,14 @@ def run_ours(args):
     ranges = torch.from_numpy(seq.range).to(dev)
     flow = torch.empty((3, H, W), device=dev)
     inv = torch.empty((H, W), device=dev)
-    tuned = not (args.nf_max or args.update_mode)
+    tuned = not (args.nf_max or args.update_mode or args.solve_tile)
     params = sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
                        flags=sf.CHECK_CFL | (sf.AUTOTUNE if tuned else 0), nf_max=args.nf_max or None,
-                       update_mode=args.update_mode or None)
+                       update_mode=args.update_mode or None, solve_tile=args.solve_tile or None)
     filt = sf.Filter(H, W, seq.levels, params)
     nf_max = filt.nf_max()       # the autotuner's choices: sub-iterations per propagation launch,
-    update_mode = filt.update_mode()   # and the form of the update
+    update_mode = filt.update_mode()   # the form of the update
+    solve_tile = filt.solve_tile()     # and the solve's tile edge
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -403,7 +404,8 @@ def run_ours(args):
                        + ("" if args.size == 512 else f", tiled to {args.size}x{args.size} (profiling case)"),
                        "global_batch": ws, "streams_per_gpu": 1, "parallelism": f"replicas x{ws}",
                        "l2": "evicted between timed steps (256 MiB write, then 256 MiB read)",
-                       "nf_max": nf_max, "update_mode": update_mode, "autotune": tuned},
+                       "nf_max": nf_max, "update_mode": update_mode, "solve_tile": solve_tile,
+                       "autotune": tuned},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
@@ -497,7 +499,7 @@ def measure_batch(steps, warmup, dev):
         "workload": "64 streams: 16x256^2 (2 levels), 32x512^2 and 16x1024^2 (3 levels), peak flow < 4 px/frame, "
                     "cameras oscillating with a 16-frame period, "
                     "N=[4,2(,1)], smooth=[2,4(,4)], plane scenes, 600 Hz",
-        "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(),
+        "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(), "solve_tile": batch.solve_tile(),
         "update_mode": batch.update_mode(), "autotune": True,
         "frames_per_s_per_stream": 1.0 / step_s, "ms_per_step": step_s * 1e3,
         "stream_frames_per_s": len(seqs) / step_s, "mpx_per_s": px / step_s / 1e6,
@@ -801,7 +803,7 @@ def measure_1024(steps, evict_l2, dev):
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     out = {"workload": "1024x1024, 2 levels, N=[8,4], smooth=[2,4] (scene512 tiled 2x2), cold L2",
            "frames_per_s": 1e3 / ms, "ms_per_step": ms, "nf_max": filt.nf_max(),
-           "update_mode": filt.update_mode(), "vs_paper": 1e3 / ms / PAPER_HZ_1024,
+           "update_mode": filt.update_mode(), "solve_tile": filt.solve_tile(), "vs_paper": 1e3 / ms / PAPER_HZ_1024,
            "hbm_gbs_algorithmic": algorithmic_bytes_per_frame(H, W, seq.levels) / (ms / 1e3) / 1e9,
            "status": sf.strerror(filt.status())}
     out["hbm_frac_of_peak"] = out["hbm_gbs_algorithmic"] / measured_peaks()[0]["hbm_gbs"]
@@ -857,6 +859,8 @@ def main():
                     help="sub-iterations per propagation launch (skips the autotuner; for profiling)")
     ap.add_argument("--update-mode", type=int, default=0, choices=[0, 1, 2],
                     help="form of the update (skips the autotuner; for profiling)")
+    ap.add_argument("--solve-tile", type=int, default=0, choices=[0, 16, 32],
+                    help="tile edge of the solve launch (skips the autotuner; for profiling)")
     ap.add_argument("--workload", choices=["scene512", "batch", "surrogate", "conv"], default="scene512",
                     help="batch / surrogate: only that configuration, as its own line")
     args = ap.parse_args()

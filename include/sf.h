@@ -73,8 +73,10 @@ extern "C" {
                                  frame for each nf_max in {8, 6, 4, 3, 2} that
                                  splits the N_h differently and keep the fastest
                                  (overrides sf_params.nf_max; see sf_nf_max);
-                                 with update_mode 0, also time both update modes
-                                 and keep the faster (see sf_update_mode)     */
+                                 then, with update_mode 0 and/or solve_tile 0,
+                                 time whole frames for every update mode and
+                                 solve tile edge left open and keep the fastest
+                                 (see sf_update_mode, sf_solve_tile)          */
 
 typedef struct sf_params {
     float fx, fy, cx, cy;          /* level-1 pinhole intrinsics, pixels              */
@@ -100,6 +102,13 @@ typedef struct sf_params {
                                       then one light reconstruction launch per lower
                                       depth (fewer dependent launches, more traffic);
                                       0 = 1, or the autotuner's choice under SF_AUTOTUNE */
+    int solve_tile;                /* edge of the square pixel tiles of the solve launch
+                                      (Eqs. 30-52 per pixel): 16 or 32; 0 = 16 when the
+                                      levels' 32-pixel tiles number at most 5 per SM
+                                      (about one wave: short CTAs overlap the
+                                      propagation launch before them), else 32, or the
+                                      autotuner's choice under SF_AUTOTUNE.  Results
+                                      are the same up to rounding order            */
 } sf_params;
 
 typedef struct sf_ctx sf_ctx;      /* opaque; owns all device state of one stream     */
@@ -205,6 +214,9 @@ int sf_nf_max(const sf_ctx* c);
 /* The update_mode the context runs with (1 or 2; see sf_params). */
 int sf_update_mode(const sf_ctx* c);
 
+/* The solve tile edge the context runs with (16 or 32; see sf_params). */
+int sf_solve_tile(const sf_ctx* c);
+
 /* Per-launch device timing.  sf_profile(c, 1) makes every following sf_step
  * record a CUDA event pair around each of its kernel launches, on the
  * step's stream; sf_profile(c, 0) stops it.  sf_profile_read waits for the
@@ -235,8 +247,8 @@ typedef struct sf_batch sf_batch;
 
 /* Create n streams: stream s is H[s] x W[s] with levels[s] levels and the
  * parameters params[s] (validated as in sf_create; all streams must use the
- * same SF_DOMINANT_LITERAL / SF_SOURCE_SPLIT choice; nf_max and SF_AUTOTUNE
- * are taken from params[0]).  The batch owns one
+ * same SF_DOMINANT_LITERAL / SF_SOURCE_SPLIT choice; nf_max, update_mode,
+ * solve_tile and SF_AUTOTUNE are taken from params[0]).  The batch owns one
  * device input slot (image, range) and one output slot (flow 3 x H x W,
  * inverse depth) per stream, zero-filled; see sf_batch_buffers. */
 int sf_batch_create(int n, const int* H, const int* W, const int* levels, const sf_params* params,
@@ -262,6 +274,7 @@ int sf_batch_launches_per_step(const sf_batch* b);
  * params[0].flags' SF_AUTOTUNE). */
 int sf_batch_nf_max(const sf_batch* b);
 int sf_batch_update_mode(const sf_batch* b);
+int sf_batch_solve_tile(const sf_batch* b);
 
 /* Stream s's motion slot for SF_IMU (the batch takes SF_IMU from
  * params[0].flags): *motion receives a device pointer to 6 floats, Omega

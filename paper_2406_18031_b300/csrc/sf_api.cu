@@ -103,6 +103,7 @@ struct Plan {
     int nwork = 0;
     size_t smem = 0;
     bool c8 = false;     // propagation: some job transports 8 channels
+    int tile = 0;        // solve: tile edge (kSolveTSmall, else kSolveT)
 };
 
 template <class Job>
@@ -168,8 +169,8 @@ int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* st
 int launch_solve(const Plan& p, const UpdArgs& a, cudaStream_t st)
 {
     if (p.nwork == 0) return SF_OK;
-    return launch_pdl(k_solve, dim3(p.nwork), dim3(kSolveThreads), 0, st, (const SolveJob*)p.jobs,
-                      (const int4*)p.work, a);
+    auto* kern = p.tile == kSolveTSmall ? k_solve<kSolveTSmall> : k_solve<kSolveT>;
+    return launch_pdl(kern, dim3(p.nwork), dim3(kSolveThreads), 0, st, (const SolveJob*)p.jobs, (const int4*)p.work, a);
 }
 
 int launch_smooth(const Plan& p, int q, float inv_dt, int check_finite, int* status, float* flow, float* inv,
@@ -217,6 +218,7 @@ int check_params(int H, int W, int L, const sf_params* p)
     if (!(p->max_flow >= 0) || !std::isfinite(p->max_flow)) return SF_EINVAL;
     if (p->nf_max < 0 || p->nf_max > kNfLimit) return SF_EINVAL;
     if (p->update_mode < 0 || p->update_mode > 2) return SF_EINVAL;
+    if (p->solve_tile != 0 && p->solve_tile != kSolveTSmall && p->solve_tile != kSolveT) return SF_EINVAL;
     for (int h = 0; h < L; ++h) {
         const int N = p->iters[h] > 0 ? p->iters[h] : std::max(1, (int)std::ceil(p->max_flow / (float)(1 << h)));
         if (N > 4096 || p->smooth_iters[h] < 0 || p->smooth_iters[h] > 16) return SF_EINVAL;
@@ -322,6 +324,8 @@ struct Engine {
     std::vector<Plan> recon;    // parallel: reconstruction of depth 1, 2, ... (coarse first)
     int update_mode = 1;        // 1: smoothing + reconstruction cascade; 2: all smoothing, then reconstruction
     int update_auto = 0;        // the tuner chooses update_mode
+    int solve_t = kSolveT;      // tile edge of the solve launch
+    int solve_auto = 0;         // the tuner chooses solve_t
     void* io = nullptr;         // slots of a batch
     float* motion = nullptr;    // every stream's motion slot (8 floats each), zeroed
     Profiler prof;
@@ -340,6 +344,23 @@ struct Engine {
 };
 
 namespace {
+
+// the solve's tile edge: the parameter, else 16 when the levels' 32-pixel
+// tiles fit in one wave (k_solve keeps 5 CTAs per SM resident), else 32; the
+// autotuner times both when the parameter is 0
+void engine_solve_tile(Engine& E, int param)
+{
+    if (param) {
+        E.solve_t = param;
+        return;
+    }
+    long tiles = 0;
+    for (auto& s : E.st)
+        for (int h = 0; h < s.L; ++h)
+            tiles += (long)ceil_div(s.H >> h, kSolveT) * ceil_div(s.W >> h, kSolveT);
+    E.solve_t = tiles <= 5L * kSmCount ? kSolveTSmall : kSolveT;
+    E.solve_auto = (E.flags & SF_AUTOTUNE) != 0;
+}
 
 void engine_free(Engine& E)
 {
@@ -448,8 +469,9 @@ int engine_smooth_plans(Engine& E, cudaStream_t st);
 
 int engine_update_plans(Engine& E, cudaStream_t st)
 {
-    // ---- solve: every level of every stream, one 32 x 32 tile per CTA
+    // ---- solve: every level of every stream, one solve_t x solve_t tile per CTA
     {
+        free_plan(E.solve);
         std::vector<SolveJob> jobs;
         std::vector<int4> work;
         for (auto& s : E.st) {
@@ -473,13 +495,14 @@ int engine_update_plans(Engine& E, cudaStream_t st)
                 j.H1 = s.H;
                 j.W1 = s.W;
                 j.lambda_ref = s.p.lambda_ref;
-                j.tiles_x = ceil_div(lv.grid.W, kSolveT);
+                j.tiles_x = ceil_div(lv.grid.W, E.solve_t);
                 jobs.push_back(j);
-                add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, kSolveT, kSolveT);
+                add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, E.solve_t, E.solve_t);
             }
         }
         int r = upload_plan(jobs, work, E.solve, st);
         if (r) return r;
+        E.solve.tile = E.solve_t;
     }
     return engine_smooth_plans(E, st);
 }
@@ -611,14 +634,21 @@ int engine_tune(Engine& E, cudaStream_t st)
     if (r) { if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); return r; }
     E.nf_max = best;
     r = engine_prop_plans(E, st);
-    // the update's form, when the parameters leave it open and a stream has a
-    // level below the top: time the solve + smoothing (+ reconstruction) of one
-    // frame in both forms on the zero state (zero inputs and outputs kept in
-    // scratch buffers; the state stays zero) and keep the faster
+    // the update's form and the solve's tile edge, where the parameters leave
+    // them open: time whole frames (the propagation launches just chosen, then
+    // solve + smoothing (+ reconstruction)) for every combination on the zero
+    // state (zero inputs and outputs kept in scratch buffers; the state stays
+    // zero) and keep the fastest.  Whole frames, because a solve launch of
+    // about one wave overlaps the propagation launch before it.
     int maxL = 0;
     size_t npx = 0;
     for (auto& es : E.st) { maxL = std::max(maxL, es.L); npx = std::max(npx, (size_t)es.H * es.W); }
-    if (!r && E.update_auto && maxL >= 2) {
+    std::vector<int> modes, tiles;
+    if (E.update_auto && maxL >= 2) modes = {1, 2};
+    else modes = {E.update_mode};
+    if (E.solve_auto) tiles = {kSolveT, kSolveTSmall};
+    else tiles = {E.solve_t};
+    if (!r && modes.size() * tiles.size() > 1) {
         float* scratch = nullptr;
         if (cudaMalloc(&scratch, 6 * npx * sizeof(float)) != cudaSuccess) scratch = nullptr, r = SF_ENOMEM;
         if (!r) r = cudaMemsetAsync(scratch, 0, 6 * npx * sizeof(float), st) == cudaSuccess ? SF_OK : SF_ECUDA;
@@ -630,26 +660,33 @@ int engine_tune(Engine& E, cudaStream_t st)
         a.W1 = E.st[0].W;
         a.lambda_ref = E.st[0].p.lambda_ref;
         float best_u = -1.0f;
-        int best_mode = 1;
-        for (int mode = 1; mode <= 2 && !r; ++mode) {
-            E.update_mode = mode;
-            r = engine_smooth_plans(E, st);
-            for (int it = 0; it < 14 && !r; ++it) {
-                if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
-                a.parity = it & 1;
-                if (!r) r = engine_update_launches(E, a, 1.0f, scratch + 2 * npx, scratch + 5 * npx, 0, st);
+        int best_mode = modes[0], best_tile = tiles[0];
+        for (int mode : modes) {
+            for (int tile : tiles) {
+                if (r) break;
+                E.update_mode = mode;
+                E.solve_t = tile;
+                r = engine_update_plans(E, st);
+                for (int it = 0; it < 14 && !r; ++it) {
+                    if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
+                    for (auto& pl : E.prop)
+                        if (!r) r = launch_propagate(pl, 0, 1.0f, flags, nullptr, st);
+                    a.parity = it & 1;
+                    if (!r) r = engine_update_launches(E, a, 1.0f, scratch + 2 * npx, scratch + 5 * npx, 0, st);
+                }
+                if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
+                if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
+                float ms = 0.0f;
+                if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
+                if (!r && (best_u < 0.0f || ms < best_u)) { best_u = ms; best_mode = mode; best_tile = tile; }
             }
-            if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
-            if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
-            float ms = 0.0f;
-            if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
-            if (!r && (best_u < 0.0f || ms < best_u)) { best_u = ms; best_mode = mode; }
         }
         if (!r && cudaStreamSynchronize(st) != cudaSuccess) r = SF_ECUDA;
         cudaFree(scratch);
         if (!r) {
             E.update_mode = best_mode;
-            r = engine_smooth_plans(E, st);
+            E.solve_t = best_tile;
+            r = engine_update_plans(E, st);
         }
         if (!r && cudaMemsetAsync(E.status, 0, sizeof(int), st) != cudaSuccess) r = SF_ECUDA;
     }
@@ -885,6 +922,7 @@ int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out)
     c->E.nf_max = p->nf_max ? p->nf_max : kNfLimit;
     c->E.update_mode = p->update_mode ? p->update_mode : 1;
     c->E.update_auto = p->update_mode == 0 && (p->flags & SF_AUTOTUNE);
+    engine_solve_tile(c->E, p->solve_tile);
     r = engine_init(c->E);
     if (r) { destroy_ctx(c); return r; }
     *out = c;
@@ -1054,6 +1092,12 @@ int sf_nf_max(const sf_ctx* c)
     return c->E.nf_max;
 }
 
+int sf_solve_tile(const sf_ctx* c)
+{
+    if (!c) return SF_EINVAL;
+    return c->E.solve_t;
+}
+
 int sf_update_mode(const sf_ctx* c)
 {
     if (!c) return SF_EINVAL;
@@ -1128,6 +1172,7 @@ int sf_batch_create(int n, const int* H, const int* W, const int* levels, const 
         es.image = base; es.range = base + np; es.flow = base + 2 * np; es.inv = base + 5 * np;
         off += 6 * np;
     }
+    if (!r) engine_solve_tile(E, params[0].solve_tile);
     if (!r) r = engine_init(E);
     if (r) { destroy_batch(b); return r; }
     *out = b;
@@ -1201,6 +1246,12 @@ int sf_batch_nf_max(const sf_batch* b)
 {
     if (!b) return SF_EINVAL;
     return b->E.nf_max;
+}
+
+int sf_batch_solve_tile(const sf_batch* b)
+{
+    if (!b) return SF_EINVAL;
+    return b->E.solve_t;
 }
 
 int sf_batch_update_mode(const sf_batch* b)

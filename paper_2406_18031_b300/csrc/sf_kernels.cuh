@@ -476,15 +476,19 @@ struct SolveJob {
     int tiles_x;
 };
 
-constexpr int kSolveT = 32;          // output tile edge
+// Output tile edges of the solve: 32 (the throughput form), or 16 for frames
+// whose 32-pixel tiles fill about one wave, where a CTA's latency sets the
+// launch time and shorter CTAs overlap the propagation launch before them.
+constexpr int kSolveT = 32;
+constexpr int kSolveTSmall = 16;
 constexpr int kSolveThreads = 256;
 
 // Level data of the (T + 4)^2 region around a solve tile into shared memory;
 // on levels 1 and 2 every load of the thread is issued before the first store.
-template <int L>
+template <int L, int T>
 __device__ __forceinline__ void solve_region(const UpdArgs& a, const Grid& g, int y0, int x0, float* Yd, float* Rd)
 {
-    constexpr int T = kSolveT, DX = T + 4, RXd = T + 2, N = DX * DX;
+    constexpr int DX = T + 4, RXd = T + 2, N = DX * DX;
     constexpr int K = (N + kSolveThreads - 1) / kSolveThreads;
     if constexpr (L > 2) {
         // 16 or 64 level-1 pixels per value: the loads of one value are enough in flight
@@ -521,16 +525,17 @@ __device__ __forceinline__ void solve_region(const UpdArgs& a, const Grid& g, in
 
 // Image model (Eqs. 30-31, separable 5-tap g and g*d filters), inverse-depth
 // model (Eqs. 32-34), the closed-form minimiser of Eq. 42 and the blend of
-// Eq. 52 for every pixel of a 32 x 32 tile.  The 3x3 normal equations of
+// Eq. 52 for every pixel of a T x T tile.  The 3x3 normal equations of
 // Eq. 46, A = g1 r r^T + g2 q q^T + g3 I with r = P gradY and q = P gradR +
 // dmu^2 rho-hat eta, are solved in Woodbury form around the prior:
 // x = prior - R K e, R = [r q], e the two residuals at the prior and
 // K = (g3 I + Gamma R^T R)^-1 Gamma, whose 2x2 determinant
 // g3^2 + g3 (g1 |r|^2 + g2 |q|^2) + g1 g2 |r x q|^2 has no cancellation.
+template <int T>
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve(const SolveJob* __restrict__ jobs, const int4* __restrict__ work, UpdArgs args)
 {
-    constexpr int T = kSolveT, DX = T + 4, RXd = T + 2;
+    constexpr int DX = T + 4, RXd = T + 2;
     __shared__ float Yd[DX * DX];          // level image, replicated border
     __shared__ float Rd[RXd * RXd];        // level inverse depth (0: no measurement)
     __shared__ float H0[DX * T];           // sum g Y   (rows of the image region, columns of the tile)
@@ -545,10 +550,10 @@ k_solve(const SolveJob* __restrict__ jobs, const int4* __restrict__ work, UpdArg
     pdl_trigger();
     pdl_wait();   // the input frame, the prediction and the state come from earlier work on the stream
     switch (J.level) {
-    case 1: solve_region<1>(args, g, y0, x0, Yd, Rd); break;
-    case 2: solve_region<2>(args, g, y0, x0, Yd, Rd); break;
-    case 3: solve_region<3>(args, g, y0, x0, Yd, Rd); break;
-    default: solve_region<4>(args, g, y0, x0, Yd, Rd); break;
+    case 1: solve_region<1, T>(args, g, y0, x0, Yd, Rd); break;
+    case 2: solve_region<2, T>(args, g, y0, x0, Yd, Rd); break;
+    case 3: solve_region<3, T>(args, g, y0, x0, Yd, Rd); break;
+    default: solve_region<4, T>(args, g, y0, x0, Yd, Rd); break;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < DX * T; idx += blockDim.x) {

@@ -32,7 +32,7 @@ class CParams(ctypes.Structure):
                 ("iters", ctypes.c_int * MAX_LEVELS), ("max_flow", ctypes.c_float),
                 ("smooth_iters", ctypes.c_int * MAX_LEVELS), ("gamma", ctypes.c_float * 5),
                 ("lambda_ref", ctypes.c_float), ("flags", ctypes.c_int), ("nf_max", ctypes.c_int),
-                ("update_mode", ctypes.c_int)]
+                ("update_mode", ctypes.c_int), ("solve_tile", ctypes.c_int)]
 
 
 class CGrid(ctypes.Structure):
@@ -43,9 +43,9 @@ class CGrid(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_host", "sf_submit_host", "sf_wait_host", "sf_status", "sf_get_state",
-           "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_update_mode", "sf_set_motion", "sf_propagate_imu", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
+           "sf_set_state", "sf_kernels_per_step", "sf_nf_max", "sf_update_mode", "sf_solve_tile", "sf_set_motion", "sf_propagate_imu", "sf_profile", "sf_profile_read", "sf_destroy", "sf_strerror", "sf_propagate", "sf_propagate_noalloc",
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
-           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_update_mode", "sf_batch_motion", "sf_batch_profile",
+           "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_update_mode", "sf_batch_solve_tile", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
            "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_selftest_conv_timeout", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
@@ -75,6 +75,7 @@ def lib():
         L.sf_kernels_per_step.argtypes = [vp]
         L.sf_nf_max.argtypes = [vp]
         L.sf_update_mode.argtypes = [vp]
+        L.sf_solve_tile.argtypes = [vp]
         L.sf_profile.argtypes = [vp, i]
         L.sf_profile_read.argtypes = [vp, P(f), P(i), i]
         L.sf_destroy.argtypes = [vp]
@@ -107,6 +108,7 @@ def lib():
         L.sf_batch_launches_per_step.argtypes = [vp]
         L.sf_batch_nf_max.argtypes = [vp]
         L.sf_batch_update_mode.argtypes = [vp]
+        L.sf_batch_solve_tile.argtypes = [vp]
         L.sf_batch_profile.argtypes = [vp, i]
         L.sf_batch_profile_read.argtypes = [vp, P(f), P(i), i]
         L.sf_batch_destroy.argtypes = [vp]
@@ -160,11 +162,12 @@ class Params:
     flags: int | None = None
     nf_max: int | None = None
     update_mode: int | None = None
+    solve_tile: int | None = None
 
     def to_c(self, H, W, levels) -> CParams:
         c = CParams()
         _check(lib().sf_params_default(ctypes.byref(c), H, W, levels), "sf_params_default")
-        for name in ("fx", "fy", "cx", "cy", "max_flow", "lambda_ref", "flags", "nf_max", "update_mode"):
+        for name in ("fx", "fy", "cx", "cy", "max_flow", "lambda_ref", "flags", "nf_max", "update_mode", "solve_tile"):
             v = getattr(self, name)
             if v is not None:
                 setattr(c, name, v)
@@ -245,6 +248,10 @@ class Filter:
     def update_mode(self) -> int:
         """1: smoothing + reconstruction cascade; 2: all smoothing, then reconstruction."""
         return _check(lib().sf_update_mode(self._h), "sf_update_mode")
+
+    def solve_tile(self) -> int:
+        """Edge of the solve launch's pixel tiles (16 or 32; set, default or AUTOTUNE)."""
+        return _check(lib().sf_solve_tile(self._h), "sf_solve_tile")
 
     def set_surrogate(self, net):
         """Predict the top level with a trained Surrogate (None: the plain propagation)."""
@@ -472,6 +479,9 @@ class Batch:
 
     def update_mode(self) -> int:
         return _check(lib().sf_batch_update_mode(self._h), "sf_batch_update_mode")
+
+    def solve_tile(self) -> int:
+        return _check(lib().sf_batch_solve_tile(self._h), "sf_batch_solve_tile")
 
     def profile(self, enable: bool):
         _check(lib().sf_batch_profile(self._h, int(bool(enable))), "sf_batch_profile")

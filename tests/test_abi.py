@@ -39,8 +39,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layout_matches_header(lib, tmp_path):
-    # sf_params: 4 floats, 4 ints, float, 4 ints, 5 floats, float, int, int, int
-    assert ctypes.sizeof(sf.CParams) == 4 * (4 + 4 + 1 + 4 + 5 + 1 + 1 + 1 + 1)
+    # sf_params: 4 floats, 4 ints, float, 4 ints, 5 floats, float, int, int, int, int
+    assert ctypes.sizeof(sf.CParams) == 4 * (4 + 4 + 1 + 4 + 5 + 1 + 1 + 1 + 1 + 1)
     assert ctypes.sizeof(sf.CGrid) == 24
     # the C compiler's view of the header: sizes and every field's offset
     fields = [f for f, _ in sf.CParams._fields_]
@@ -77,7 +77,8 @@ def test_create_rejects_bad_shapes_without_touching_the_device(lib, H, W, L):
 
 @pytest.mark.parametrize("field,value", [("fx", 0.0), ("lambda_ref", -1.0), ("gamma2", 0.0), ("gamma0", -1.0),
                                          ("gamma4", 0.0), ("iters0", 5000), ("smooth0", 17), ("nf_max", 9),
-                                         ("nf_max", -1), ("update_mode", 3)])
+                                         ("nf_max", -1), ("update_mode", 3), ("solve_tile", 8),
+                                         ("solve_tile", 24), ("solve_tile", 64)])
 def test_create_rejects_bad_parameters(lib, field, value):
     p = sf.CParams()
     lib.sf_params_default(ctypes.byref(p), 64, 64, 1)

@@ -106,6 +106,7 @@ def test_batch_matches_single_stream_filters_and_oracle(nf_max, update_mode):
     assert batch.launches_per_step() == (2 if nf_max is None else 3) + 1 + 3
     assert batch.update_mode() == (update_mode or 1)
     assert batch.nf_max() == (nf_max or 8)
+    assert batch.solve_tile() == 16        # 49 tiles of 32 pixels: one wave
     assert batch.status() in (sf.OK, sf.WARN_CFL)
 
 

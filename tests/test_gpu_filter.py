@@ -19,22 +19,23 @@ def _cuda():
     oracle.set_threads(8)
 
 
-def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None, update_mode=None):
+def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None, update_mode=None, solve_tile=None):
     H, W = seq.shape
     kw = dict(iters=seq.iters, smooth=seq.smooth)
     if gamma is not None:
         kw["gamma"] = gamma
     g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, nf_max=nf_max,
-                                               update_mode=update_mode,
+                                               update_mode=update_mode, solve_tile=solve_tile,
                                                flags=flags | gpu_flags | sf.CHECK_CFL | sf.CHECK_FINITE, **kw))
     r = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, flags=flags, **kw))
     return g, r
 
 
 def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX, gpu_flags=0, nf_max=None,
-         filt=None, update_mode=None):
+         filt=None, update_mode=None, solve_tile=None):
     """Run both filters; returns per-frame (max px error, max rho error) and the final outputs."""
-    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max, update_mode=update_mode)
+    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max, update_mode=update_mode,
+                 solve_tile=solve_tile)
     if filt is not None:
         filt.append(g)
     H, W = seq.shape
@@ -85,6 +86,28 @@ def test_propagation_split_into_launches(nf_max):
     assert filt[0].kernels_per_step() == -(-10 // nf_max) + 1 + 2
 
 
+@pytest.mark.parametrize("solve_tile", [16, 32])
+@pytest.mark.parametrize("H,W,levels", [(128, 160, 2), (96, 312, 3), (40, 56, 2)])
+def test_solve_tile_edges_match_oracle(solve_tile, H, W, levels):
+    # the solve launch on 16- and 32-pixel tiles, ragged tails included
+    if levels == 2:
+        seq = scenes.scene512(frames=5, H=H, W=W, max_flow=3.0, levels=2, iters=(3, 2), smooth=(2, 4))
+    else:
+        seq = scenes.drive(frames=4, H=H, W=W, levels=3, iters=(8, 4, 2), smooth=(2, 4, 4))
+    filt = []
+    errs, _, _, st = _run(seq, seq.frames, solve_tile=solve_tile, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert filt[0].solve_tile() == solve_tile
+
+
+def test_solve_tile_default_follows_the_wave_size():
+    # 0: 16 when the levels' 32-pixel tiles fit in one wave (5 per SM), else 32
+    small = sf.Filter(512, 512, 2, sf.Params(iters=[8, 4]))
+    large = sf.Filter(2048, 2048, 2, sf.Params(iters=[8, 4]))
+    assert small.solve_tile() == 16 and large.solve_tile() == 32
+
+
 @pytest.mark.parametrize("levels", [2, 3])
 def test_parallel_update_mode_matches_oracle(levels):
     # update_mode 2: every level smoothed in one launch, the lower levels then
@@ -109,6 +132,7 @@ def test_autotune_keeps_a_candidate_and_the_results():
     assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
     assert filt[0].nf_max() in (8, 6, 4, 3, 2)
     assert filt[0].update_mode() in (1, 2)
+    assert filt[0].solve_tile() in (16, 32)
     assert st == sf.OK
 
 
