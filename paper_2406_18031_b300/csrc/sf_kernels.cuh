@@ -75,7 +75,8 @@ struct PixGeo {
 };
 
 // eta and cu = |m'| / (a (1 - eta_x^2)) of the pixel at (x, y) (closed forms
-// at the top of sf_device.cuh)
+// at the top of sf_device.cuh); |m'| n2 / (a y2p1) with the fast reciprocal
+// square root and divide (a few ulp, once per pixel and launch)
 __device__ __forceinline__ PixGeo pix_geo(float x, float y, float a)
 {
     const float y2p1 = fmaf(y, y, 1.0f);
@@ -87,7 +88,7 @@ __device__ __forceinline__ PixGeo pix_geo(float x, float y, float a)
     o.ex = x * r;
     o.ey = y * r;
     o.ez = r;
-    o.cu = sqrtf(n2p) * n2 / (a * y2p1);
+    o.cu = __fdividef(n2p * rsqrtf(n2p) * n2, a * y2p1);
     return o;
 }
 
