@@ -685,20 +685,26 @@ __host__ __device__ inline size_t smooth_smem_bytes(int S)
 
 // S passes of the 5-tap mean with replicated ends over p[lo..hi] (stride
 // `st`), in place.  A pass keeps its 5-wide window in registers and reads
-// four values ahead, all still unwritten.
-__device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, int S)
+// four values ahead, all still unwritten.  An end that is a region edge
+// rather than the image border (shl, shr) is not replicated: pass s (from 0)
+// then skips its 2 (s + 1) outermost positions there, whose results no later
+// pass reads on the way to the tile (S passes leave the 2S outermost
+// positions of each such side unneeded; the region holds exactly that halo).
+__device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, int S, bool shl, bool shr)
 {
     for (int s = 0; s < S; ++s) {
-        float w0 = p[lo * st], w1 = w0, w2 = w0;
-        float w3 = p[min(lo + 1, hi) * st], w4 = p[min(lo + 2, hi) * st];
+        const int a = shl ? lo + 2 * (s + 1) : lo, b = shr ? hi - 2 * (s + 1) : hi;
+        const float w0i = p[(shl ? a - 2 : lo) * st], w1i = p[(shl ? a - 1 : lo) * st];
+        float w0 = w0i, w1 = w1i, w2 = p[a * st];
+        float w3 = p[min(a + 1, hi) * st], w4 = p[min(a + 2, hi) * st];
         float sum = (w0 + w1) + (w2 + w3) + w4;
-        for (int e = lo; e <= hi; e += 5) {
+        for (int e = a; e <= b; e += 5) {
             float n[5];
 #pragma unroll
             for (int u = 0; u < 5; ++u) n[u] = p[min(e + 3 + u, hi) * st];
 #pragma unroll
             for (int u = 0; u < 5; ++u) {
-                if (e + u <= hi) p[(e + u) * st] = sum * 0.2f;
+                if (e + u <= b) p[(e + u) * st] = sum * 0.2f;
                 sum += n[u] - w0;
                 w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = n[u];
             }
@@ -793,13 +799,13 @@ k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work
         const int nrow = wy1 - wy0;
         for (int t = tid; t < 3 * nrow; t += kSmoothThreads) {
             const int ch = t / nrow, r = wy0 + (t - ch * nrow);
-            box5_passes(Pl + ch * PL + r * SP, 1, wx0, wx1 - 1, S);
+            box5_passes(Pl + ch * PL + r * SP, 1, wx0, wx1 - 1, S, wx0 == 0, wx1 == SX);
         }
         __syncthreads();
         // column passes on the tile's columns, one (column, channel) per thread
         for (int t = tid; t < 3 * T; t += kSmoothThreads) {
             const int ch = t / T, c = 2 * S + (t - ch * T);
-            if (c < wx1) box5_passes(Pl + ch * PL + c, SP, wy0, wy1 - 1, S);
+            if (c < wx1) box5_passes(Pl + ch * PL + c, SP, wy0, wy1 - 1, S, wy0 == 0, wy1 == SX);
         }
         __syncthreads();
     }
