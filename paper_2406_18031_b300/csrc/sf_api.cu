@@ -596,11 +596,13 @@ int engine_smooth_plans(Engine& E, cudaStream_t st)
 
 // The autotuner: time one frame's propagation launches for every nf_max in
 // {8, 6, 4, 3, 2} that splits the levels' N_h into a different set of launches
-// (12 frames after 2 warm-up frames, CUDA events on the engine's stream) and
-// keep the fastest.  It runs on the engine's zero state: the kernel has no
+// (12 frames after 2 warm-up frames, CUDA events on the engine's stream; two
+// interleaved rounds, each candidate keeping its faster) and keep the fastest.  It runs on the engine's zero state: the kernel has no
 // data-dependent branches, so the timing is that of any state, and the
 // propagation of zeros writes zeros, so the engine is left as created.
 int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, float* inv, int slot, cudaStream_t st);
+
+constexpr int kTuneRounds = 2;
 
 int engine_tune(Engine& E, cudaStream_t st)
 {
@@ -611,26 +613,36 @@ int engine_tune(Engine& E, cudaStream_t st)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = SF_ECUDA;
     const int flags = E.flags & ~(SF_CHECK_CFL | SF_CHECK_FINITE);
+    // every candidate is timed in kTuneRounds interleaved rounds and keeps its
+    // fastest, so that one disturbed measurement cannot decide the choice
+    std::vector<int> nfs;
     for (int nf : cand) {
-        if (r) break;
         std::vector<int> sig;
         for (auto& s : E.st)
             for (int h = 0; h < s.L; ++h) sig.push_back(ceil_div(s.lv[h].N, nf));
         if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
         seen.push_back(sig);
-        E.nf_max = nf;
-        r = engine_prop_plans(E, st);
-        for (int it = 0; it < 14 && !r; ++it) {
-            if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
-            for (auto& pl : E.prop)
-                if (!r) r = launch_propagate(pl, 0, 1.0f, flags, nullptr, st);
-        }
-        if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
-        if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
-        float ms = 0.0f;
-        if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
-        if (!r && (best_ms < 0.0f || ms < best_ms)) { best_ms = ms; best = nf; }
+        nfs.push_back(nf);
     }
+    std::vector<float> nf_ms(nfs.size(), -1.0f);
+    for (int round = 0; round < kTuneRounds && nfs.size() > 1; ++round) {
+        for (size_t c = 0; c < nfs.size() && !r; ++c) {
+            E.nf_max = nfs[c];
+            r = engine_prop_plans(E, st);
+            for (int it = 0; it < 14 && !r; ++it) {
+                if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
+                for (auto& pl : E.prop)
+                    if (!r) r = launch_propagate(pl, 0, 1.0f, flags, nullptr, st);
+            }
+            if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = SF_ECUDA;
+            if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
+            float ms = 0.0f;
+            if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
+            if (!r && (nf_ms[c] < 0.0f || ms < nf_ms[c])) nf_ms[c] = ms;
+        }
+    }
+    for (size_t c = 0; c < nfs.size(); ++c)
+        if (best_ms < 0.0f || (nf_ms[c] >= 0.0f && nf_ms[c] < best_ms)) { best_ms = nf_ms[c]; best = nfs[c]; }
     if (r) { if (e0) cudaEventDestroy(e0); if (e1) cudaEventDestroy(e1); return r; }
     E.nf_max = best;
     r = engine_prop_plans(E, st);
@@ -659,13 +671,14 @@ int engine_tune(Engine& E, cudaStream_t st)
         a.H1 = E.st[0].H;
         a.W1 = E.st[0].W;
         a.lambda_ref = E.st[0].p.lambda_ref;
-        float best_u = -1.0f;
-        int best_mode = modes[0], best_tile = tiles[0];
-        for (int mode : modes) {
-            for (int tile : tiles) {
-                if (r) break;
-                E.update_mode = mode;
-                E.solve_t = tile;
+        std::vector<std::pair<int, int>> combos;
+        for (int mode : modes)
+            for (int tile : tiles) combos.emplace_back(mode, tile);
+        std::vector<float> combo_ms(combos.size(), -1.0f);
+        for (int round = 0; round < kTuneRounds; ++round) {
+            for (size_t c = 0; c < combos.size() && !r; ++c) {
+                E.update_mode = combos[c].first;
+                E.solve_t = combos[c].second;
                 r = engine_update_plans(E, st);
                 for (int it = 0; it < 14 && !r; ++it) {
                     if (it == 2 && cudaEventRecord(e0, st) != cudaSuccess) r = SF_ECUDA;
@@ -678,9 +691,17 @@ int engine_tune(Engine& E, cudaStream_t st)
                 if (!r && cudaEventSynchronize(e1) != cudaSuccess) r = SF_ECUDA;
                 float ms = 0.0f;
                 if (!r && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = SF_ECUDA;
-                if (!r && (best_u < 0.0f || ms < best_u)) { best_u = ms; best_mode = mode; best_tile = tile; }
+                if (!r && (combo_ms[c] < 0.0f || ms < combo_ms[c])) combo_ms[c] = ms;
             }
         }
+        float best_u = -1.0f;
+        int best_mode = modes[0], best_tile = tiles[0];
+        for (size_t c = 0; c < combos.size(); ++c)
+            if (combo_ms[c] >= 0.0f && (best_u < 0.0f || combo_ms[c] < best_u)) {
+                best_u = combo_ms[c];
+                best_mode = combos[c].first;
+                best_tile = combos[c].second;
+            }
         if (!r && cudaStreamSynchronize(st) != cudaSuccess) r = SF_ECUDA;
         cudaFree(scratch);
         if (!r) {
