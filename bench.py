@@ -109,6 +109,32 @@ def algorithmic_bytes_per_frame(H, W, levels):
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
+def frame_flops(H, W, levels, iters, smooth):
+    """Algorithmic FP32 operations of one frame: per pixel of level h, N_h
+    propagation sub-iterations (94 below the top, 58 at the top; see
+    propagate_flops_per_launch), the models and the 3x3 solve (about 130),
+    S_h smoothing passes (18 each: a row and a column 5-tap mean on 3
+    channels) and, below the top, the reconstruction (12)."""
+    total = 0
+    for h in range(levels):
+        n = (H >> h) * (W >> h)
+        top = h == levels - 1
+        total += n * (iters[h] * (58 if top else 94) + 130 + 18 * smooth[h] + (0 if top else 12))
+    return total
+
+
+def roofline_frame(frames, ms, hbm_gbs):
+    """The frame's roofline fraction: time_min / time with time_min =
+    max(algorithmic bytes / HBM bandwidth, algorithmic FLOPs / FP32 peak);
+    frames: (H, W, levels, iters, smooth) of every stream stepped in ms."""
+    b = sum(algorithmic_bytes_per_frame(H, W, L) for H, W, L, _, _ in frames)
+    f = sum(frame_flops(H, W, L, it, sm) for H, W, L, it, sm in frames)
+    tb, tf = b / (hbm_gbs * 1e9), f / (FP32_PEAK_TFLOPS * 1e12)
+    return {"algorithmic_bytes": b, "algorithmic_flops": f, "time_min_us": max(tb, tf) * 1e6,
+            "bound": "hbm" if tb >= tf else "alu", "frac": max(tb, tf) / (ms / 1e3),
+            "peak_source": "measured hbm_gbs; FP32 peak from SMs x 128 lanes x 2 x 2.032 GHz"}
+
+
 def propagate_flops_per_launch(H, W, levels, iters, nf_max=8):
     """Algorithmic FP32 operations of the first propagation launch: per pixel
     and sub-iteration 94 below the top level (8 channels) and 58 at the top
@@ -408,6 +434,8 @@ def run_ours(args):
                        "autotune": tuned},
             "hbm_gbs_algorithmic": frame_bytes * value / ws / 1e9,
             "hbm_frac_of_peak": frame_bytes * value / ws / 1e9 / peaks["hbm_gbs"],
+            "roofline_frame": roofline_frame([(H, W, seq.levels, seq.iters, seq.smooth)], 1e3 * ws / value,
+                                             peaks["hbm_gbs"]),
             "epe_vs_oracle_px": {"mean": mean_epe, "max": max_epe, "frames": 3},
             "roofline": {"kernel": "k_propagate (first launch of the frame, all levels)", "bound": "hbm",
                          "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -505,6 +533,8 @@ def measure_batch(steps, warmup, dev):
         "stream_frames_per_s": len(seqs) / step_s, "mpx_per_s": px / step_s / 1e6,
         "hbm_gbs_algorithmic": frame_bytes / step_s / 1e9,
         "hbm_frac_of_peak": frame_bytes / step_s / 1e9 / peaks["hbm_gbs"],
+        "roofline_frame": roofline_frame([(q.shape[0], q.shape[1], q.levels, q.iters, q.smooth) for q in seqs],
+                                         step_s * 1e3, peaks["hbm_gbs"]),
         "launches_per_step": batch.launches_per_step(),
         "kernels": {n: {"ms_per_launch": ms / max(c, 1), "launches": c, "share": ms / tot}
                     for n, (ms, c) in zip(names, slots)},
@@ -807,6 +837,8 @@ def measure_1024(steps, evict_l2, dev):
            "hbm_gbs_algorithmic": algorithmic_bytes_per_frame(H, W, seq.levels) / (ms / 1e3) / 1e9,
            "status": sf.strerror(filt.status())}
     out["hbm_frac_of_peak"] = out["hbm_gbs_algorithmic"] / measured_peaks()[0]["hbm_gbs"]
+    out["roofline_frame"] = roofline_frame([(H, W, seq.levels, seq.iters, seq.smooth)], ms,
+                                           measured_peaks()[0]["hbm_gbs"])
     filt.close()
     return out
 
