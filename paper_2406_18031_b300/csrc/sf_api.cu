@@ -1,13 +1,15 @@
 // sf_api.cu -- host side of libsf: filter engines, launch plans and the C ABI
-// of include/sf.h.  All device work is issued on the caller's stream; nothing
-// here synchronises except sf_status / sf_batch_status, sf_step_host and the
-// stage entry points' descriptor uploads.
+// of include/sf.h.  All device work is issued on the caller's stream (and, for
+// sf_submit_host, the context's two copy streams); nothing here synchronises
+// except sf_status / sf_batch_status, sf_step_host, sf_wait_host, creation
+// (and its autotuner) and the stage entry points' descriptor uploads.
 //
 // An engine is a set of independent camera streams, each with its pyramid
 // levels.  Its frame is a fixed sequence of launches whose descriptors are
 // built once: the propagation launches (every level of every stream), one
 // solve launch (every level), then the smoothing + reconstruction cascade
-// (one launch per pyramid depth, top levels first).  sf_ctx is an engine of
+// (one launch per pyramid depth, top levels first; or one smoothing launch and
+// light reconstruction launches, update mode 2).  sf_ctx is an engine of
 // one stream fed through per-frame pointers; sf_batch is an engine of many
 // streams with library-owned input/output slots, replayed from CUDA graphs.
 #include <cuda_runtime.h>
