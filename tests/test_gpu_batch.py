@@ -157,3 +157,33 @@ def test_full_size_batch_sampled_streams():
         assert e.max() <= gu.FLOW_TOL_PX, (k, e.max())
         assert np.abs(batch.slots[0][3].cpu().numpy() - ri).max() <= gu.RHO_TOL, k
     assert batch.status() in (sf.OK, sf.WARN_CFL)
+
+
+def test_batch_with_a_four_level_stream():
+    # streams of 1 to 4 levels in one engine: the deepest sets the number of
+    # smoothing depths; each stream against its own single-stream filter
+    seqs = [scenes.scene512(frames=4, seed=31, H=128, W=160, max_flow=4.0, levels=4, iters=(4, 2, 1, 1),
+                            smooth=(2, 4, 4, 4)),
+            scenes.plane64(frames=4, seed=32, H=64, W=64, levels=1, iters=[2])]
+    dt = seqs[0].dt
+    batch = sf.Batch([q.shape for q in seqs], [q.levels for q in seqs], [_params(q) for q in seqs])
+    singles = [sf.Filter(*q.shape, q.levels, _params(q)) for q in seqs]
+    outs = [(torch.empty((3, *q.shape), device="cuda"), torch.empty(q.shape, device="cuda")) for q in seqs]
+    stream = torch.cuda.Stream()
+    for k in range(4):
+        with torch.cuda.stream(stream):
+            for s, q in enumerate(seqs):
+                img, rng, _, _ = batch.slots[s]
+                img.copy_(torch.from_numpy(q.image[k]).cuda())
+                rng.copy_(torch.from_numpy(q.range[k]).cuda())
+            batch.step(dt, stream=stream)
+            for s, q in enumerate(seqs):
+                singles[s].step(torch.from_numpy(q.image[k]).cuda(), torch.from_numpy(q.range[k]).cuda(), dt,
+                                outs[s][0], outs[s][1], stream=stream)
+        stream.synchronize()
+        for s, q in enumerate(seqs):
+            _, _, dmu = oracle.geometry(*q.shape, q.fx, q.fy, q.cx, q.cy)
+            e = np.abs(batch.slots[s][2].cpu().numpy().astype(np.float64) - outs[s][0].cpu().numpy()) * dt / dmu[None]
+            assert e.max() <= gu.FLOW_TOL_PX, (k, s, e.max())
+            assert np.abs(batch.slots[s][3].cpu().numpy() - outs[s][1].cpu().numpy()).max() <= gu.RHO_TOL
+    assert batch.status() in (sf.OK, sf.WARN_CFL)

@@ -101,6 +101,18 @@ def test_solve_tile_edges_match_oracle(solve_tile, H, W, levels):
     assert filt[0].solve_tile() == solve_tile
 
 
+@pytest.mark.parametrize("update_mode,solve_tile", [(1, 32), (2, 16)])
+def test_four_levels_match_oracle(update_mode, solve_tile):
+    # the deepest pyramid: level data of level 4 averages 8x8 blocks of the input
+    seq = scenes.scene512(frames=5, H=128, W=160, max_flow=4.0, levels=4, iters=(4, 2, 1, 1),
+                          smooth=(2, 4, 4, 4))
+    filt = []
+    errs, _, _, st = _run(seq, seq.frames, update_mode=update_mode, solve_tile=solve_tile, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert filt[0].update_mode() == update_mode and filt[0].solve_tile() == solve_tile
+
+
 def test_solve_tile_default_follows_the_wave_size():
     # 0: 16 when the levels' 32-pixel tiles fit in one wave (5 per SM), else 32
     small = sf.Filter(512, 512, 2, sf.Params(iters=[8, 4]))

@@ -176,7 +176,7 @@ def _update_case(level, levels, top, S, init, seed=11, H1=128, W1=96, invalid=Tr
     return ref, n0.cpu().numpy(), n1.cpu().numpy(), diag.cpu().numpy()
 
 
-@pytest.mark.parametrize("level,levels", [(1, 1), (1, 2), (2, 2), (1, 3), (2, 3), (3, 3)])
+@pytest.mark.parametrize("level,levels", [(1, 1), (1, 2), (2, 2), (1, 3), (2, 3), (3, 3), (1, 4), (3, 4), (4, 4)])
 @pytest.mark.parametrize("S", [0, 2, 4])
 def test_update_matches_oracle(level, levels, S):
     top = level == levels
@@ -197,7 +197,7 @@ def test_update_matches_oracle(level, levels, S):
         assert (n1[..., :3] == 0).all()
 
 
-@pytest.mark.parametrize("level,levels", [(1, 1), (2, 2), (3, 3), (1, 3)])
+@pytest.mark.parametrize("level,levels", [(1, 1), (2, 2), (3, 3), (1, 3), (4, 4)])
 def test_update_init_frame(level, levels):
     ref, n0, n1, _ = _update_case(level, levels, level == levels, 4, init=True)
     assert (n0[..., :3] == 0).all() and (n1[..., :3] == 0).all()
@@ -208,7 +208,7 @@ def test_update_init_frame(level, levels):
 
 # ------------------------------------------------------------------ reconstruction
 
-@pytest.mark.parametrize("levels", [1, 2, 3])
+@pytest.mark.parametrize("levels", [1, 2, 3, 4])
 def test_reconstruct_matches_oracle(levels):
     rng = np.random.default_rng(21 + levels)
     H1, W1 = 96, 136
