@@ -71,7 +71,8 @@ def test_propagate_matches_oracle(H, W, N, top, flags):
 @pytest.mark.parametrize("H,W", [(80, 72), (33, 47), (200, 184)])
 @pytest.mark.parametrize("N", [1, 3, 12])
 @pytest.mark.parametrize("top", [True, False])
-def test_propagate_inertial_terms_match_oracle(H, W, N, top):
+@pytest.mark.parametrize("flags", [0, oracle.DOMINANT_LITERAL | oracle.SOURCE_SPLIT])
+def test_propagate_inertial_terms_match_oracle(H, W, N, top, flags):
     # SF_IMU: the source step -2 Om x w - Om x (Om x eta) - rho a after each
     # sub-iteration (and -2 Om x dw below the top), Om and a in frame units
     rng = np.random.default_rng(300 + H + N + 7 * top)
@@ -89,9 +90,9 @@ def test_propagate_inertial_terms_match_oracle(H, W, N, top):
     s1 = None if top else np.concatenate([dw, Y[..., None]], -1)
     o0 = torch.empty((H, W, 4), device="cuda")
     o1 = None if top else torch.empty((H, W, 4), device="cuda")
-    sf.propagate_imu(g, N, imu, _t(s0), o0, None if top else _t(s1), o1)
+    sf.propagate_imu(g, N, imu, _t(s0), o0, None if top else _t(s1), o1, flags=flags)
     torch.cuda.synchronize()
-    rw, rdw, rr, ry, _ = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y, flags=oracle.IMU,
+    rw, rdw, rr, ry, _ = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y, flags=oracle.IMU | flags,
                                           imu=imu.astype(np.float64))
     out0 = o0.cpu().numpy()
     assert gu.px_err(out0[..., :3], rw, dmu) <= gu.FLOW_TOL_PX
@@ -101,7 +102,7 @@ def test_propagate_inertial_terms_match_oracle(H, W, N, top):
         assert gu.px_err(out1[..., :3], rdw, dmu) <= gu.FLOW_TOL_PX
         assert np.abs(out1[..., 3] - ry).max() <= gu.Y_TOL
     # and the terms matter at this size: without them the flow differs
-    rw0 = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y)[0]
+    rw0 = oracle.propagate(w, rho, eta, B, dmu, N, dw=dw, Y=Y, flags=flags)[0]
     assert gu.px_err(out0[..., :3], rw0, dmu) > 100 * gu.FLOW_TOL_PX
 
 
