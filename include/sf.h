@@ -123,7 +123,7 @@ int sf_params_default(sf_params* p, int H, int W, int levels);
 /* Create a filter for H x W frames with `levels` levels (1..SF_MAX_LEVELS = 4;
  * the coarse levels are built on the fly, 4^(h-1) input reads per pixel).
  * H and W must be divisible by 2^(levels-1); every level must be at least
- * 8 x 8.  Allocates all device state on the current device (about 128 bytes
+ * 8 x 8; H x W at most 2^30.  Allocates all device state on the current device (about 128 bytes
  * per level-1 pixel, the coarser levels adding a third).  *out receives the
  * context; on error *out is NULL. */
 int sf_create(int H, int W, int levels, const sf_params* p, sf_ctx** out);

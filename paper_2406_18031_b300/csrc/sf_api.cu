@@ -36,6 +36,10 @@ namespace {
 // square output tile is 64 - 2 nf pixels wide); an engine may use fewer
 constexpr int kNfLimit = 8;
 
+// the largest frame (pixels): plane offsets of the kernels are 32-bit, and a
+// frame of this size already needs 137 GB of state
+constexpr long long kMaxPixels = 1LL << 30;
+
 // streaming multiprocessors of a B300 (two dies of 74): grid sizes of the
 // grid-stride kernels and the launch-form thresholds are multiples of it
 constexpr int kSmCount = 148;
@@ -210,6 +214,7 @@ int check_params(int H, int W, int L, const sf_params* p)
     if (!p || L < 1 || L > SF_MAX_LEVELS || L > kMaxLevelsDev) return SF_EINVAL;
     const int m = 1 << (L - 1);
     if (H <= 0 || W <= 0 || H % m || W % m || H / m < 8 || W / m < 8) return SF_EINVAL;
+    if ((long long)H * W > kMaxPixels) return SF_EINVAL;
     if (!(p->fx > 0 && p->fy > 0) || !std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->cx) ||
         !std::isfinite(p->cy))
         return SF_EINVAL;

@@ -66,7 +66,8 @@ def test_params_default(lib):
     assert lib.sf_params_default(ctypes.byref(p), 4, 4, 5) == sf.EINVAL
 
 
-@pytest.mark.parametrize("H,W,L", [(30, 30, 3), (64, 64, 0), (64, 64, 5), (0, 64, 1), (24, 24, 3), (64, 60, 4)])
+@pytest.mark.parametrize("H,W,L", [(30, 30, 3), (64, 64, 0), (64, 64, 5), (0, 64, 1), (24, 24, 3), (64, 60, 4),
+                                   (32768, 32776, 1), (65536, 65536, 2)])
 def test_create_rejects_bad_shapes_without_touching_the_device(lib, H, W, L):
     p = sf.CParams()
     lib.sf_params_default(ctypes.byref(p), 64, 64, 1)

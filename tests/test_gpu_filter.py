@@ -210,6 +210,18 @@ def test_full_size_512_two_levels():
 
 
 @pytest.mark.slow
+def test_largest_frame_tested_4096_two_levels():
+    # the benchmark's scene tiled to 4096 x 4096 (16.8 Mpx, 2.2 GB of state):
+    # every pixel of two frames against the FP64 oracle
+    import bench
+    seq = bench.make_sequence(1001, 2, 4096)
+    errs, _, _, st = _run(seq, 2)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert st >= 0
+
+
+@pytest.mark.slow
 def test_full_size_driving_three_levels():
     seq = scenes.drive(frames=2)
     errs, _, _, _ = _run(seq, 2)
