@@ -141,6 +141,30 @@ def _ptr(t, itemsize=4):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _fptr(t, n, what):
+    """Device pointer of a contiguous float32 CUDA tensor of exactly n elements
+    (or None -> NULL): the library reads and writes n floats there."""
+    import torch
+    if t is None:
+        return None
+    if t.dtype != torch.float32:
+        raise ValueError(f"{what}: expected float32, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{what}: expected {n} elements, got {t.numel()}")
+    return _ptr(t)
+
+
+def _hptr(a, n, what):
+    """Address of a C-contiguous float32 host array of exactly n elements (or None)."""
+    if a is None:
+        return None
+    if a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise ValueError(f"{what}: expected a C-contiguous float32 array")
+    if a.size != n:
+        raise ValueError(f"{what}: expected {n} elements, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -205,18 +229,17 @@ class Filter:
 
     def step(self, image, rng, dt, flow_out=None, invdepth_out=None, stream=None):
         """Asynchronous frame on CUDA tensors; returns the status code (>= 0)."""
-        return _check(lib().sf_step(self._h, _ptr(image), _ptr(rng), float(dt), _ptr(flow_out),
-                                    _ptr(invdepth_out), _stream(stream)), "sf_step")
+        n = self.H * self.W
+        return _check(lib().sf_step(self._h, _fptr(image, n, "image"), _fptr(rng, n, "range"), float(dt),
+                                    _fptr(flow_out, 3 * n, "flow_out"), _fptr(invdepth_out, n, "invdepth_out"),
+                                    _stream(stream)), "sf_step")
 
     def step_host(self, image: np.ndarray, rng: np.ndarray, dt, flow_out: np.ndarray | None = None,
                   invdepth_out: np.ndarray | None = None, stream=None):
         """Frame on host float32 arrays (copies included); waits for completion."""
-        def hp(a):
-            if a is None:
-                return None
-            assert a.dtype == np.float32 and a.flags.c_contiguous
-            return ctypes.c_void_p(a.ctypes.data)
-        return _check(lib().sf_step_host(self._h, hp(image), hp(rng), float(dt), hp(flow_out), hp(invdepth_out),
+        n = self.H * self.W
+        return _check(lib().sf_step_host(self._h, _hptr(image, n, "image"), _hptr(rng, n, "range"), float(dt),
+                                         _hptr(flow_out, 3 * n, "flow_out"), _hptr(invdepth_out, n, "invdepth_out"),
                                          _stream(stream)), "sf_step_host")
 
     def submit_host(self, image: np.ndarray, rng: np.ndarray, dt, flow_out: np.ndarray | None = None,
@@ -224,13 +247,10 @@ class Filter:
         """Pipelined frame on host float32 arrays: enqueues the copies and the
         step and returns the frame's ticket at once.  The arrays must stay
         alive and unchanged (outputs unread) until ``wait_host(ticket)``."""
-        def hp(a):
-            if a is None:
-                return None
-            assert a.dtype == np.float32 and a.flags.c_contiguous
-            return ctypes.c_void_p(a.ctypes.data)
+        n = self.H * self.W
         t = ctypes.c_longlong(-1)
-        _check(lib().sf_submit_host(self._h, hp(image), hp(rng), float(dt), hp(flow_out), hp(invdepth_out),
+        _check(lib().sf_submit_host(self._h, _hptr(image, n, "image"), _hptr(rng, n, "range"), float(dt),
+                                    _hptr(flow_out, 3 * n, "flow_out"), _hptr(invdepth_out, n, "invdepth_out"),
                                     _stream(stream), ctypes.byref(t)), "sf_submit_host")
         return t.value
 
@@ -294,8 +314,9 @@ class Filter:
         return dst, dtp.value
 
     def set_state(self, h, planes, dt_prev, stream=None):
-        _check(lib().sf_set_state(self._h, h, _ptr(planes.contiguous()), float(dt_prev), _stream(stream)),
-               "sf_set_state")
+        Hh, Wh = self.level_shape(h)
+        _check(lib().sf_set_state(self._h, h, _fptr(planes.contiguous(), 8 * Hh * Wh, "planes"), float(dt_prev),
+                                  _stream(stream)), "sf_set_state")
 
 
 def grid(H, W, fx, fy, cx, cy) -> CGrid:

@@ -350,6 +350,31 @@ def test_pipelined_host_steps_match_device_steps(memory):
     assert b.status() == sf.OK
 
 
+def test_binding_rejects_wrong_buffers_before_the_call():
+    # the library reads and writes exactly H x W (3 H x W) floats: the binding
+    # refuses other sizes, dtypes and devices instead of passing them on
+    seq = scenes.plane64(frames=2)
+    H, W = seq.shape
+    g, _ = _pair(seq)
+    img = torch.from_numpy(seq.image[0]).cuda(); rg = torch.from_numpy(seq.range[0]).cuda()
+    with pytest.raises(ValueError):
+        g.step(img[:-1], rg, seq.dt)                                  # too few pixels
+    with pytest.raises(ValueError):
+        g.step(img, rg.double(), seq.dt)                              # wrong dtype
+    with pytest.raises(ValueError):
+        g.step(img, rg, seq.dt, torch.empty((3, H, W - 1), device="cuda"))
+    with pytest.raises(ValueError):
+        g.step(img.cpu(), rg, seq.dt)                                 # host tensor to the device call
+    with pytest.raises(ValueError):
+        g.step_host(seq.image[0][:, :-2].copy(), seq.range[0], seq.dt)
+    with pytest.raises(ValueError):
+        g.submit_host(seq.image[0], seq.range[0], seq.dt, np.empty((2, H, W), np.float32))
+    with pytest.raises(ValueError):
+        g.set_state(0, torch.zeros((7, H, W), device="cuda"), seq.dt)
+    g.step(img, rg, seq.dt)                                           # the right ones still work
+    assert g.status() == sf.OK
+
+
 def test_pipelined_host_step_tickets():
     seq = scenes.plane64(frames=2)
     H, W = seq.shape
