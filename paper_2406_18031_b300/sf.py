@@ -326,25 +326,31 @@ def grid(H, W, fx, fy, cx, cy) -> CGrid:
 def propagate(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
               stream=None):
     """Stage entry point ``sf_propagate`` on [H, W, 4] float32 CUDA tensors."""
-    return _check(lib().sf_propagate(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in), _ptr(s1_in),
-                                     _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)), "sf_propagate")
+    n = 4 * g.H * g.W
+    return _check(lib().sf_propagate(ctypes.byref(g), int(N), int(flags), float(wscale), _fptr(s0_in, n, "s0_in"),
+                                     _fptr(s1_in, n, "s1_in"), _fptr(s0_out, n, "s0_out"), _fptr(s1_out, n, "s1_out"),
+                                     _ptr(status), _stream(stream)), "sf_propagate")
 
 
 def propagate_imu(g: CGrid, N, imu, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
                   stream=None):
     """``sf_propagate_imu``: imu = (Omega, a) in frame units, six numbers."""
     m = (ctypes.c_float * 6)(*[float(x) for x in np.asarray(imu, dtype=np.float64).reshape(6)])
-    return _check(lib().sf_propagate_imu(ctypes.byref(g), int(N), int(flags), float(wscale), m, _ptr(s0_in),
-                                         _ptr(s1_in), _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)),
-                  "sf_propagate_imu")
+    n = 4 * g.H * g.W
+    return _check(lib().sf_propagate_imu(ctypes.byref(g), int(N), int(flags), float(wscale), m,
+                                         _fptr(s0_in, n, "s0_in"), _fptr(s1_in, n, "s1_in"),
+                                         _fptr(s0_out, n, "s0_out"), _fptr(s1_out, n, "s1_out"), _ptr(status),
+                                         _stream(stream)), "sf_propagate_imu")
 
 
 def propagate_noalloc(g: CGrid, N, s0_in, s0_out, s1_in=None, s1_out=None, flags=0, wscale=1.0, status=None,
                       stream=None):
     """``sf_propagate_noalloc``: sf_propagate without allocating (frames up to 1024 x 1024 pixels)."""
-    return _check(lib().sf_propagate_noalloc(ctypes.byref(g), int(N), int(flags), float(wscale), _ptr(s0_in),
-                                             _ptr(s1_in), _ptr(s0_out), _ptr(s1_out), _ptr(status), _stream(stream)),
-                  "sf_propagate_noalloc")
+    n = 4 * g.H * g.W
+    return _check(lib().sf_propagate_noalloc(ctypes.byref(g), int(N), int(flags), float(wscale),
+                                             _fptr(s0_in, n, "s0_in"), _fptr(s1_in, n, "s1_in"),
+                                             _fptr(s0_out, n, "s0_out"), _fptr(s1_out, n, "s1_out"), _ptr(status),
+                                             _stream(stream)), "sf_propagate_noalloc")
 
 
 def update(g: CGrid, level, top, S, init, gamma, lambda_ref, image, rng, s0_new, s1_new, s0_cur=None, s1_cur=None,
@@ -352,19 +358,24 @@ def update(g: CGrid, level, top, S, init, gamma, lambda_ref, image, rng, s0_new,
     """Stage entry point ``sf_update``; image/rng are the level-1 [H1, W1] inputs."""
     gm = (ctypes.c_float * 5)(*gamma)
     H1, W1 = image.shape
+    n1, n = H1 * W1, 4 * g.H * g.W
     return _check(lib().sf_update(ctypes.byref(g), int(level), int(top), int(S), int(init), gm, float(lambda_ref),
-                                  _ptr(image), _ptr(rng), H1, W1, _ptr(s0_cur), _ptr(s1_cur), _ptr(p0), _ptr(p1),
-                                  _ptr(s0_new), _ptr(s1_new), _ptr(diag), _stream(stream)), "sf_update")
+                                  _fptr(image, n1, "image"), _fptr(rng, n1, "range"), H1, W1,
+                                  _fptr(s0_cur, n, "s0_cur"), _fptr(s1_cur, n, "s1_cur"), _fptr(p0, n, "p0"),
+                                  _fptr(p1, n, "p1"), _fptr(s0_new, n, "s0_new"), _fptr(s1_new, n, "s1_new"),
+                                  _fptr(diag, 3 * n, "diag"), _stream(stream)), "sf_update")
 
 
 def reconstruct(grids, s0, s1, dt, flow_out=None, invdepth_out=None, check_finite=False, status=None, stream=None):
     """Stage entry point ``sf_reconstruct`` over per-level [H, W, 4] tensors."""
     L = len(grids)
     ga = (CGrid * L)(*grids)
-    p0 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s0])
-    p1 = (ctypes.c_void_p * L)(*[t.data_ptr() for t in s1])
-    return _check(lib().sf_reconstruct(L, ga, p0, p1, float(dt), _ptr(flow_out), _ptr(invdepth_out),
-                                       int(bool(check_finite)), _ptr(status), _stream(stream)), "sf_reconstruct")
+    p0 = (ctypes.c_void_p * L)(*[_fptr(t, 4 * gr.H * gr.W, "s0").value for t, gr in zip(s0, grids)])
+    p1 = (ctypes.c_void_p * L)(*[_fptr(t, 4 * gr.H * gr.W, "s1").value for t, gr in zip(s1, grids)])
+    n = grids[0].H * grids[0].W
+    return _check(lib().sf_reconstruct(L, ga, p0, p1, float(dt), _fptr(flow_out, 3 * n, "flow_out"),
+                                       _fptr(invdepth_out, n, "invdepth_out"), int(bool(check_finite)), _ptr(status),
+                                       _stream(stream)), "sf_reconstruct")
 
 
 def remap_pinhole(dst: CGrid, R, cam, image, out_image, rng=None, out_range=None, stream=None):
