@@ -141,17 +141,22 @@ def _ptr(t, itemsize=4):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _fptr(t, n, what):
-    """Device pointer of a contiguous float32 CUDA tensor of exactly n elements
-    (or None -> NULL): the library reads and writes n floats there."""
-    import torch
+def _tptr(t, dtype, n, what):
+    """Device pointer of a contiguous CUDA tensor of the given dtype and exactly
+    n elements (or None -> NULL): the library reads or writes n elements there."""
     if t is None:
         return None
-    if t.dtype != torch.float32:
-        raise ValueError(f"{what}: expected float32, got {t.dtype}")
+    if t.dtype != dtype:
+        raise ValueError(f"{what}: expected {dtype}, got {t.dtype}")
     if t.numel() != n:
         raise ValueError(f"{what}: expected {n} elements, got {t.numel()}")
-    return _ptr(t)
+    return _ptr(t, dtype.itemsize)
+
+
+def _fptr(t, n, what):
+    """Device pointer of a contiguous float32 CUDA tensor of exactly n elements (or None)."""
+    import torch
+    return _tptr(t, torch.float32, n, what)
 
 
 def _hptr(a, n, what):
@@ -383,25 +388,36 @@ def remap_pinhole(dst: CGrid, R, cam, image, out_image, rng=None, out_range=None
     Rm = (ctypes.c_float * 9)(*[float(x) for x in np.asarray(R, dtype=np.float64).reshape(9)])
     K = (ctypes.c_float * 4)(*[float(x) for x in cam])
     Hs, Ws = image.shape
-    return _check(lib().sf_remap_pinhole(ctypes.byref(dst), Rm, Hs, Ws, K, _ptr(image), _ptr(rng), _ptr(out_image),
-                                         _ptr(out_range), _stream(stream)), "sf_remap_pinhole")
+    n, nd = Hs * Ws, dst.H * dst.W
+    return _check(lib().sf_remap_pinhole(ctypes.byref(dst), Rm, Hs, Ws, K, _fptr(image, n, "image"),
+                                         _fptr(rng, n, "rng"), _fptr(out_image, nd, "out_image"),
+                                         _fptr(out_range, nd, "out_range"), _stream(stream)), "sf_remap_pinhole")
 
 
 def remap_equirect(dst: CGrid, R, image, out_image, rng=None, out_range=None, stream=None):
     """``sf_remap_equirect``: an equirectangular panorama (device [Hs, Ws]) onto the grid ``dst``."""
     Rm = (ctypes.c_float * 9)(*[float(x) for x in np.asarray(R, dtype=np.float64).reshape(9)])
     Hs, Ws = image.shape
-    return _check(lib().sf_remap_equirect(ctypes.byref(dst), Rm, Hs, Ws, _ptr(image), _ptr(rng), _ptr(out_image),
-                                          _ptr(out_range), _stream(stream)), "sf_remap_equirect")
+    n, nd = Hs * Ws, dst.H * dst.W
+    return _check(lib().sf_remap_equirect(ctypes.byref(dst), Rm, Hs, Ws, _fptr(image, n, "image"),
+                                          _fptr(rng, n, "rng"), _fptr(out_image, nd, "out_image"),
+                                          _fptr(out_range, nd, "out_range"), _stream(stream)), "sf_remap_equirect")
 
 
 def conv3x3(x, w, bias=None, relu=False, y=None, y32=None, status=None, stream=None):
     """``sf_conv3x3``: x [N, H, W, Cin] and w [9, Cout, Cin] bfloat16 CUDA tensors; writes y
     (bfloat16) and/or y32 (float32), [N, H, W, Cout]."""
+    import torch
     N, H, W, Cin = x.shape
+    if w.dim() != 3 or w.shape[0] != 9 or w.shape[2] != Cin:
+        raise ValueError(f"w: expected [9, Cout, {Cin}], got {list(w.shape)}")
     Cout = w.shape[1]
-    return _check(lib().sf_conv3x3(N, H, W, Cin, Cout, _ptr(x, 2), _ptr(w, 2), _ptr(bias), int(bool(relu)),
-                                   _ptr(y, 2), _ptr(y32), _ptr(status), _stream(stream)), "sf_conv3x3")
+    bf, f32 = torch.bfloat16, torch.float32
+    m = N * H * W * Cout
+    return _check(lib().sf_conv3x3(N, H, W, Cin, Cout, _tptr(x, bf, x.numel(), "x"), _tptr(w, bf, w.numel(), "w"),
+                                   _tptr(bias, f32, Cout, "bias"), int(bool(relu)), _tptr(y, bf, m, "y"),
+                                   _tptr(y32, f32, m, "y32"), _tptr(status, torch.int32, 1, "status"),
+                                   _stream(stream)), "sf_conv3x3")
 
 
 class Surrogate:

@@ -70,3 +70,22 @@ def test_bounded_wait_gives_up_and_leaves_the_device_usable():
     # the kernel must report the timeout, free its tensor memory and return
     assert sf.lib().sf_selftest_conv_timeout(None) == sf.ETIMEOUT
     _case(1, 3, 130, 16, 16, True, seed=5)       # and the next convolution still works
+
+
+def test_binding_rejects_wrong_buffers_before_the_call():
+    x = torch.zeros((1, 8, 8, 16), dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros((9, 32, 16), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty((1, 8, 8, 32), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(ValueError, match="w: expected"):
+        sf.conv3x3(x, w[:, :, :8].contiguous(), y=y)                   # Cin of w differs from x's
+    with pytest.raises(ValueError, match="y: expected"):
+        sf.conv3x3(x, w, y=y.float())                                  # float32 tensor as the bf16 output
+    with pytest.raises(ValueError, match="y32: expected 2048"):
+        sf.conv3x3(x, w, y32=torch.empty((1, 8, 7, 32), device="cuda"))
+    with pytest.raises(ValueError, match="bias: expected"):
+        sf.conv3x3(x, w, torch.zeros(16, device="cuda"), y=y)
+    with pytest.raises(ValueError, match="status: expected"):
+        sf.conv3x3(x, w, y=y, status=torch.zeros(1, dtype=torch.int64, device="cuda"))
+    sf.conv3x3(x, w, y=y)                                              # the right ones still work
+    torch.cuda.synchronize()
+    assert float(y.float().abs().max()) == 0.0

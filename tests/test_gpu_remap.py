@@ -136,3 +136,21 @@ def test_equirect_full_size_panorama_onto_512_grid():
     # the paper's rendering path: a 360-degree panorama onto a front-facing
     # 512 x 512 grid (90 degree field of view)
     _equirect_case(1024, sf.grid(512, 512, 256.0, 256.0, 256.0, 256.0), _R(0.0, 0.0, 0.0), seed=10)
+
+
+def test_binding_rejects_wrong_buffers_before_the_call():
+    g = sf.CGrid(16, 24, 20.0, 20.0, 11.5, 7.5)
+    R = np.eye(3)
+    img = torch.zeros((10, 12), device="cuda")
+    oi = torch.empty((16, 24), device="cuda")
+    with pytest.raises(ValueError, match="out_image: expected 384"):
+        sf.remap_pinhole(g, R, (10.0, 10.0, 6.0, 5.0), img, oi[:, :-1])
+    with pytest.raises(ValueError, match="rng: expected 120"):
+        sf.remap_pinhole(g, R, (10.0, 10.0, 6.0, 5.0), img, oi, torch.zeros((10, 11), device="cuda"), oi.clone())
+    with pytest.raises(ValueError, match="image: expected"):
+        sf.remap_equirect(g, R, img.double(), oi)
+    with pytest.raises(ValueError, match="out_range: expected 384"):
+        sf.remap_equirect(g, R, img, oi, img.clone(), torch.empty(383, device="cuda"))
+    sf.remap_equirect(g, R, img, oi)                                   # the right ones still work
+    torch.cuda.synchronize()
+    assert float(oi.abs().max()) == 0.0
