@@ -332,6 +332,7 @@ def run_ours(args):
     seq = make_sequence(1001 + rank, 8 if args.quick else SEQ_FRAMES, args.size)
     H, W = seq.shape
     dev = torch.device("cuda", local)
+    host_io = None if args.quick else pin_host_io(seq)
     images = torch.from_numpy(seq.image).to(dev)
     ranges = torch.from_numpy(seq.range).to(dev)
     flow = torch.empty((3, H, W), device=dev)
@@ -409,7 +410,7 @@ def run_ours(args):
             e2e, (mean_epe, max_epe), cpu, batched, imu, remap, surrogate, frame1024 = (
                 None, (None, None), None, None, None, None, None, None)
         else:
-            e2e = measure_e2e(filt, seq, args.steps)
+            e2e = measure_e2e(filt, seq, args.steps, host_io)
             imu = measure_imu(seq, images, ranges, min(args.steps, 100), evict_l2)
             remap = measure_remap(seq, images, ranges, min(args.steps, 100), evict_l2)
             surrogate = measure_surrogate(min(args.steps, 30), dev)
@@ -843,20 +844,39 @@ def measure_1024(steps, evict_l2, dev):
     return out
 
 
-def measure_e2e(filt, seq, steps):
-    """Same metric through the host-buffer API, every step copying its pinned
-    host inputs in and its flow and inverse depth out: sf_submit_host (input
-    copy, step and output copy of consecutive frames overlap; a ring of 4 host
-    output buffers, each reused after its frame's sf_wait_host), and, for
-    comparison, the synchronous sf_step_host."""
+PIN_AGE_S = 1.0   # minimum age of the pinned host buffers when the e2e loop is timed
+
+
+def pin_host_io(seq, ring=4):
+    """Pinned host buffers of the e2e measurement: every frame's inputs and a
+    ring of output buffers.  Made when the run starts and reused, as a
+    long-running application pins its buffers once: a freshly pinned buffer
+    was measured copying several times slower in its first second (a 2 MB
+    host-to-device copy 190 us at first, 45-55 us from about 1 s on, whether
+    the buffer was idle or copied meanwhile)."""
     import torch
     H, W = seq.shape
     imgs = torch.from_numpy(seq.image).pin_memory()
     rngs = torch.from_numpy(seq.range).pin_memory()
-    ims, rgs = imgs.numpy(), rngs.numpy()
-    ring = 4
     outs = [(torch.empty((3, H, W), dtype=torch.float32).pin_memory().numpy(),
              torch.empty((H, W), dtype=torch.float32).pin_memory().numpy()) for _ in range(ring)]
+    return {"ims": imgs.numpy(), "rgs": rngs.numpy(), "outs": outs, "keep": (imgs, rngs), "t": time.perf_counter()}
+
+
+def measure_e2e(filt, seq, steps, io):
+    """Same metric through the host-buffer API, every step copying its pinned
+    host inputs in and its flow and inverse depth out: sf_submit_host (input
+    copy, step and output copy of consecutive frames overlap; a ring of 4 host
+    output buffers, each reused after its frame's sf_wait_host), and, for
+    comparison, the synchronous sf_step_host.  io: pin_host_io's buffers,
+    at least PIN_AGE_S old when the timing starts."""
+    import torch
+    H, W = seq.shape
+    ims, rgs, outs = io["ims"], io["rgs"], io["outs"]
+    ring = len(outs)
+    age = time.perf_counter() - io["t"]
+    if age < PIN_AGE_S:
+        time.sleep(PIN_AGE_S - age)
     st = torch.cuda.Stream()
     for k in range(3):
         filt.wait_host(filt.submit_host(ims[k], rgs[k], seq.dt, *outs[0], stream=st))
@@ -876,7 +896,8 @@ def measure_e2e(filt, seq, steps):
     el_sync = time.perf_counter() - t1
     return {"value": steps / el, "unit": "frames/s", "h2d_bytes_per_step": 2 * H * W * 4,
             "d2h_bytes_per_step": 4 * H * W * 4, "api": "sf_submit_host / sf_wait_host (pipelined, pinned)",
-            "sync_step_host_value": steps / el_sync}
+            "sync_step_host_value": steps / el_sync,
+            "host_buffers": f"pinned when the run starts, {max(age, PIN_AGE_S):.1f} s old when timed"}
 
 
 def main():
