@@ -238,49 +238,55 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def cpu_baseline(seq, budget_s=12.0, max_frames=40):
+def gpu_first_flows(seq, frames=3):
+    """The CUDA filter's flow (host copies) over the first frames of seq, from
+    a fresh filter: what the cpu_baseline leg compares its oracle frames with."""
+    import torch
+    from paper_2406_18031_b300 import sf
+    H, W = seq.shape
+    g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters,
+                                               smooth=seq.smooth))
+    flow = torch.empty((3, H, W), device="cuda")
+    out = []
+    for k in range(frames):
+        g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, flow)
+        out.append(flow.cpu().numpy().astype(np.float64))
+    g.close()
+    return out
+
+
+def cpu_baseline(seq, gpu_flows=(), budget_s=12.0, max_frames=40):
     """The FP64 oracle, as it stands, on the host cores: frames/s on a bounded
-    sample (the first frames of the same sequence)."""
+    sample (the first frames of the same sequence).  The oracle's flow of the
+    first len(gpu_flows) frames is kept and, after the timing, compared with
+    the CUDA filter's (end-point difference in px/frame, 3-D, Eq. 68 style)."""
     import oracle
     oracle.build()
     threads = oracle.set_threads(os.cpu_count() or 1)
     H, W = seq.shape
     f = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, iters=seq.iters,
                                                       smooth=seq.smooth))
-    f.step(seq.image[0], seq.range[0], seq.dt)  # initialisation frame, untimed
+    rf, _ = f.step(seq.image[0], seq.range[0], seq.dt)  # initialisation frame, untimed
+    kept = [np.array(rf, dtype=np.float64)]
     t0 = time.perf_counter()
     n = 0
     while n < max_frames and (time.perf_counter() - t0) < budget_s:
         k = 1 + n % (seq.frames - 1)
-        f.step(seq.image[k], seq.range[k], seq.dt)
+        rf, _ = f.step(seq.image[k], seq.range[k], seq.dt)
+        if len(kept) < len(gpu_flows) and k == len(kept):
+            kept.append(np.array(rf, dtype=np.float64))
         n += 1
     el = time.perf_counter() - t0
+    epe = None
+    m = min(len(kept), len(gpu_flows))
+    if m:
+        _, _, dmu = f.geometry(0)
+        d = [np.linalg.norm(gpu_flows[k] - kept[k], axis=0) * seq.dt / dmu for k in range(m)]
+        epe = {"mean": float(d[-1].mean()), "max": max(float(x.max()) for x in d), "frames": m}
     return {"value": n / el, "unit": "frames/s", "cores": threads, "kind": "oracle",
             "sample": f"{n} frames of the {H}x{W} {seq.levels}-level sequence after the initialisation frame, "
-                      f"FP64 oracle with {threads} OpenMP threads"}
-
-
-def epe_vs_oracle(seq, frames=3):
-    """Mean and max end-point difference (px/frame, 3-D, Eq. 68 style) between
-    the CUDA filter and the FP64 oracle over the first frames."""
-    import torch
-    import oracle
-    from paper_2406_18031_b300 import sf
-    H, W = seq.shape
-    g = sf.Filter(H, W, seq.levels, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters,
-                                               smooth=seq.smooth))
-    r = oracle.Filter(H, W, seq.levels, oracle.Params(seq.fx, seq.fy, seq.cx, seq.cy, iters=seq.iters,
-                                                      smooth=seq.smooth))
-    _, _, dmu = r.geometry(0)
-    flow = torch.empty((3, H, W), device="cuda")
-    mean = mx = 0.0
-    for k in range(frames):
-        g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, flow)
-        rf, _ = r.step(seq.image[k], seq.range[k], seq.dt)
-        d = np.linalg.norm(flow.cpu().numpy().astype(np.float64) - rf, axis=0) * seq.dt / dmu
-        mean, mx = float(d.mean()), max(mx, float(d.max()))
-    g.close()
-    return mean, mx
+                      f"FP64 oracle with {threads} OpenMP threads",
+            "epe_vs_gpu_px": epe}
 
 
 def run_reference(args):
@@ -415,8 +421,9 @@ def run_ours(args):
             remap = measure_remap(seq, images, ranges, min(args.steps, 100), evict_l2)
             surrogate = measure_surrogate(min(args.steps, 30), dev)
             frame1024 = measure_1024(min(args.steps, 100), evict_l2, dev)
-            mean_epe, max_epe = epe_vs_oracle(seq, frames=3)
-            cpu = cpu_baseline(seq)
+            cpu = cpu_baseline(seq, gpu_first_flows(seq, frames=3))
+            epe = cpu.pop("epe_vs_gpu_px") or {}
+            mean_epe, max_epe = epe.get("mean"), epe.get("max")
             filt.close()
             del images, ranges
             torch.cuda.empty_cache()
