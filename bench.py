@@ -49,9 +49,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "1e203acaadc2a8f2",
-    "scene512_k_propagate_bytes": 9_479_168 + 1_536,
-    "batch_k_propagate_bytes": 1_069_932_544 + 1_019_518_976,
+    "kernel_sources_sha256_16": "5eecf7fcdbead5ba",
+    "scene512_k_propagate_bytes": 9_480_960 + 3_072,
+    "batch_k_propagate_bytes": 1_070_113_280 + 1_019_235_072,
 }
 
 
