@@ -692,6 +692,9 @@ __host__ __device__ inline size_t smooth_smem_bytes(int S)
 // then skips its 2 (s + 1) outermost positions there, whose results no later
 // pass reads on the way to the tile (S passes leave the 2S outermost
 // positions of each such side unneeded; the region holds exactly that halo).
+// The clamp of the read index and the test of the write index (ALU work on
+// every element) are needed only near the line's end: the main loop runs
+// without them, the same operations in the same order otherwise.
 __device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, int S, bool shl, bool shr)
 {
     for (int s = 0; s < S; ++s) {
@@ -700,7 +703,20 @@ __device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, in
         float w0 = w0i, w1 = w1i, w2 = p[a * st];
         float w3 = p[min(a + 1, hi) * st], w4 = p[min(a + 2, hi) * st];
         float sum = (w0 + w1) + (w2 + w3) + w4;
-        for (int e = a; e <= b; e += 5) {
+        int e = a;
+        // away from the line's end: no clamped reads, no skipped writes
+        for (; e + 7 <= hi && e + 4 <= b; e += 5) {
+            float n[5];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) n[u] = p[(e + 3 + u) * st];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+                p[(e + u) * st] = sum * 0.2f;
+                sum += n[u] - w0;
+                w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = n[u];
+            }
+        }
+        for (; e <= b; e += 5) {
             float n[5];
 #pragma unroll
             for (int u = 0; u < 5; ++u) n[u] = p[min(e + 3 + u, hi) * st];
