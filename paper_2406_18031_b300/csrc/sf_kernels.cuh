@@ -695,8 +695,10 @@ __host__ __device__ inline size_t smooth_smem_bytes(int S)
 // The clamp of the read index and the test of the write index (ALU work on
 // every element) are needed only near the line's end: the main loop runs
 // without them, the same operations in the same order otherwise.
-__device__ __forceinline__ void box5_passes(float* p, int st, int lo, int hi, int S, bool shl, bool shr)
+template <int ST>
+__device__ __forceinline__ void box5_passes(float* p, int st_rt, int lo, int hi, int S, bool shl, bool shr)
 {
+    const int st = ST ? ST : st_rt;   // ST: a stride known at compile time (0: st_rt)
     for (int s = 0; s < S; ++s) {
         const int a = shl ? lo + 2 * (s + 1) : lo, b = shr ? hi - 2 * (s + 1) : hi;
         const float w0i = p[(shl ? a - 2 : lo) * st], w1i = p[(shl ? a - 1 : lo) * st];
@@ -817,13 +819,20 @@ k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work
         const int nrow = wy1 - wy0;
         for (int t = tid; t < 3 * nrow; t += kSmoothThreads) {
             const int ch = t / nrow, r = wy0 + (t - ch * nrow);
-            box5_passes(Pl + ch * PL + r * SP, 1, wx0, wx1 - 1, S, wx0 == 0, wx1 == SX);
+            box5_passes<1>(Pl + ch * PL + r * SP, 1, wx0, wx1 - 1, S, wx0 == 0, wx1 == SX);
         }
         __syncthreads();
-        // column passes on the tile's columns, one (column, channel) per thread
+        // column passes on the tile's columns, one (column, channel) per thread; the
+        // 3-CTA form takes the default counts' strides (S = 2, 4) as constants (shared
+        // memory offsets instead of address adds), the 4-CTA form has no registers to spare
         for (int t = tid; t < 3 * T; t += kSmoothThreads) {
             const int ch = t / T, c = 2 * S + (t - ch * T);
-            if (c < wx1) box5_passes(Pl + ch * PL + c, SP, wy0, wy1 - 1, S, wy0 == 0, wy1 == SX);
+            if (c >= wx1) continue;
+            float* const line = Pl + ch * PL + c;
+            const bool shl = wy0 == 0, shr = wy1 == SX;
+            if (MINB == 3 && S == 2) box5_passes<kSmoothT + 9>(line, SP, wy0, wy1 - 1, S, shl, shr);        // SP = 41
+            else if (MINB == 3 && S == 4) box5_passes<kSmoothT + 17>(line, SP, wy0, wy1 - 1, S, shl, shr);  // SP = 49
+            else box5_passes<0>(line, SP, wy0, wy1 - 1, S, shl, shr);
         }
         __syncthreads();
     }
