@@ -49,9 +49,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "5eecf7fcdbead5ba",
-    "scene512_k_propagate_bytes": 9_480_960 + 3_072,
-    "batch_k_propagate_bytes": 1_070_113_280 + 1_019_235_072,
+    "kernel_sources_sha256_16": "66a9c9e0cee28323",
+    "scene512_k_propagate_bytes": 9_480_704 + 2_560,
+    "batch_k_propagate_bytes": 1_070_017_024 + 1_019_224_832,
 }
 
 

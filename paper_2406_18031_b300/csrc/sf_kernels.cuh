@@ -222,14 +222,16 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
         }
     }
     pdl_wait();
-    float om[3] = {0.f, 0.f, 0.f}, ac[3] = {0.f, 0.f, 0.f};   // frame units
-    if (IMU && J.motion) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            om[c] = J.motion[c] * mscale;
-            ac[c] = J.motion[3 + c] * (mscale * mscale);
-        }
+    // Omega and a in frame units, in shared memory: read where used rather than
+    // held in six registers across the passes (visible after the first barrier,
+    // which precedes the first inertial step)
+    __shared__ float s_motion[6];
+    if (IMU && threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        s_motion[c] = J.motion ? J.motion[c] * (c < 3 ? mscale : mscale * mscale) : 0.0f;
     }
+    const float* const om = s_motion;
+    const float* const ac = s_motion + 3;
 
     // load (replicated coordinates outside the image: those pixels are never
     // read by an in-image pixel, whose border neighbours are itself)
