@@ -178,7 +178,7 @@ def _update_case(level, levels, top, S, init, seed=11, H1=128, W1=96, invalid=Tr
 
 
 @pytest.mark.parametrize("level,levels", [(1, 1), (1, 2), (2, 2), (1, 3), (2, 3), (3, 3), (1, 4), (3, 4), (4, 4)])
-@pytest.mark.parametrize("S", [0, 2, 4])
+@pytest.mark.parametrize("S", [0, 1, 2, 3, 4, 16])   # 2 and 4 take constant strides; 16 the largest region
 def test_update_matches_oracle(level, levels, S):
     top = level == levels
     ref, n0, n1, diag = _update_case(level, levels, top, S, init=False)
