@@ -109,6 +109,7 @@ struct Plan {
     int nwork = 0;
     size_t smem = 0;
     bool c8 = false;     // propagation: some job transports 8 channels
+    int nf = 0;          // propagation: sub-iterations of the launch's longest job
     int tile = 0;        // solve: tile edge (kSolveTSmall, else kSolveT)
 };
 
@@ -143,19 +144,27 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
 // need 16-byte alignment whatever the size of the job struct
 inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
-template <bool C8, bool LIT, bool IMU>
+template <bool C8, bool LIT, bool IMU, bool PE>
 int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
 {
-    if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU>, p.smem)) return SF_ECUDA;
-    return launch_pdl(k_propagate<C8, LIT, IMU>, dim3(p.nwork), dim3(kPrThreads), p.smem, st, (const PropJob*)p.jobs,
-                      (const int4*)p.work, parity, wscale, flags, status, mscale);
+    if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU, PE>, p.smem)) return SF_ECUDA;
+    return launch_pdl(k_propagate<C8, LIT, IMU, PE>, dim3(p.nwork), dim3(kPrThreads), p.smem, st,
+                      (const PropJob*)p.jobs, (const int4*)p.work, parity, wscale, flags, status, mscale);
+}
+
+template <bool C8, bool LIT, bool IMU>
+int launch_propagate_i(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
+{
+    // the padded form for launches of many sub-iterations (see kPrPaddedNf)
+    if (p.nf >= kPrPaddedNf) return launch_propagate_t<C8, LIT, IMU, true>(p, parity, wscale, flags, status, mscale, st);
+    return launch_propagate_t<C8, LIT, IMU, false>(p, parity, wscale, flags, status, mscale, st);
 }
 
 template <bool C8, bool LIT>
 int launch_propagate_l(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
 {
-    if (flags & SF_IMU) return launch_propagate_t<C8, LIT, true>(p, parity, wscale, flags, status, mscale, st);
-    return launch_propagate_t<C8, LIT, false>(p, parity, wscale, flags, status, mscale, st);
+    if (flags & SF_IMU) return launch_propagate_i<C8, LIT, true>(p, parity, wscale, flags, status, mscale, st);
+    return launch_propagate_i<C8, LIT, false>(p, parity, wscale, flags, status, mscale, st);
 }
 
 // one propagation launch; with SF_IMU in flags the jobs' motion slots hold
@@ -424,6 +433,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
         std::vector<PropJob> jobs;
         std::vector<int4> work;
         bool c8 = false;
+        int nfl = 0;   // the longest job's sub-iterations
         for (int want = nfmax; want >= 1; --want) {   // longest tiles (most passes) first
             for (auto& s : E.st) {
                 for (int h = 0; h < s.L; ++h) {
@@ -461,10 +471,12 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
                     jobs.push_back(j);
                     add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
                     c8 |= !top;
+                    nfl = std::max(nfl, nf);
                 }
             }
         }
         E.prop[k].c8 = c8;
+        E.prop[k].nf = nfl;
         E.prop[k].smem = prop_smem_bytes();
         int r = upload_plan(jobs, work, E.prop[k], st);
         if (r) return r;
@@ -1355,6 +1367,7 @@ int stage_propagate(const sf_grid* g, int N, int flags, float wscale, const floa
         add_tiles(work, 0, g->H, g->W, prop_tile(j.nf), prop_tile(j.nf));
         Plan pl;
         pl.c8 = c8;
+        pl.nf = j.nf;
         pl.smem = prop_smem_bytes();
         // the job, its work list and the motion travel through stream-ordered scratch
         void* mem = nullptr;
@@ -2058,6 +2071,7 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
         if (r) break;
         Plan pl;
         pl.c8 = c8;
+        pl.nf = j.nf;
         pl.smem = prop_smem_bytes();
         pl.jobs = djob;
         pl.work = dwork;

@@ -63,11 +63,22 @@ constexpr int kPrThreads = 32 * kPrWarps;
 
 __host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // square output tile edge
 
+// Published rows: slot 1 + 2w holds warp w's first row, slot 2 + 2w its last.
+// In the padded form (PE) slot 0 and the last slot repeat the region's first
+// and last rows (the row beyond a region edge is the edge row itself), so every
+// warp reads the rows above and below its own from fixed slots without a
+// select; the plain form selects the warp's own row at the region edges.  The
+// padded form saves ALU work in every sub-iteration but holds more registers
+// (spills around the load and store phases): launches whose longest job runs
+// at least kPrPaddedNf sub-iterations take it.
+constexpr int kPubSlots = 2 * kPrWarps + 2;
+constexpr int kPrPaddedNf = 6;
+
 __host__ __device__ inline size_t prop_smem_bytes()
 {
     return (size_t)kPrH * kPrW * sizeof(float4)                 // geometry
-           + 2 * (size_t)kPrWarps * 2 * kPrW * sizeof(float4)   // published rows: s0, s1
-           + (size_t)kPrWarps * 2 * kPrW * sizeof(float);       // published row speeds
+           + 2 * (size_t)kPubSlots * kPrW * sizeof(float4)      // published rows: s0, s1
+           + (size_t)kPubSlots * kPrW * sizeof(float);          // published row speeds
 }
 
 struct PixGeo {
@@ -176,16 +187,16 @@ __device__ __forceinline__ void inertial_step(float4& w, float4& d, bool has1, f
     }
 }
 
-template <bool C8, bool LITERAL, bool IMU>
+template <bool C8, bool LITERAL, bool IMU, bool PE>
 __global__ void __launch_bounds__(kPrThreads, 1)
 k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int parity, float wscale,
             int flags, int* __restrict__ status, float mscale)
 {
     extern __shared__ float4 smem4[];
     float4* geo = smem4;                                   // [kPrH][kPrW]
-    float4* pub0 = geo + kPrH * kPrW;                      // [kPrWarps][2][kPrW]
-    float4* pub1 = pub0 + kPrWarps * 2 * kPrW;
-    float* pubv = reinterpret_cast<float*>(pub1 + kPrWarps * 2 * kPrW);
+    float4* pub0 = geo + kPrH * kPrW;                      // [kPubSlots][kPrW]
+    float4* pub1 = pub0 + kPubSlots * kPrW;
+    float* pubv = reinterpret_cast<float*>(pub1 + kPubSlots * kPrW);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 wk = work[blockIdx.x];
@@ -296,21 +307,36 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             sp[k][0] = G0.w * fmaf(G0.z, na0.y, -G0.y * na0.z);   // v of Eq. 54 for the row pass
             sp[k][1] = G1.w * fmaf(G1.z, na1.y, -G1.y * na1.z);
         }
-        // publish my first and last rows for the neighbouring warps
+        // publish my first and last rows for the neighbouring warps (padded form:
+        // the first and the last warp also fill the edge slots)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int k = e ? kPrRows - 1 : 0;
-            const int base = (warp * 2 + e) * kPrW + lane;
-            pub0[base] = a[k][0]; pub0[base + 32] = a[k][1];
-            if (has1) { pub1[base] = b[k][0]; pub1[base + 32] = b[k][1]; }
-            pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
+            const int edge = !PE ? -1 : e == 0 ? (warp == 0 ? 0 : -1) : (warp == kPrWarps - 1 ? kPubSlots - 1 : -1);
+#pragma unroll
+            for (int m = 0; m < (PE ? 2 : 1); ++m) {
+                const int slot = m ? edge : 1 + warp * 2 + e;
+                if (slot < 0) continue;                    // warp-uniform
+                const int base = slot * kPrW + lane;
+                pub0[base] = a[k][0]; pub0[base + 32] = a[k][1];
+                if (PE ? C8 : has1) { pub1[base] = b[k][0]; pub1[base + 32] = b[k][1]; }   // zeros at the top level
+                pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
+            }
         }
         __syncthreads();
         // ---------------- row pass (Eqs. 63-66, reading R2), neighbours in rows k -+ 1
         float4 prev_a[2], prev_b[2];
         float prev_v[2];
-        {   // the row above my first row: the last row of the warp above (or myself at the region edge)
-            const int base = ((warp > 0 ? warp - 1 : warp) * 2 + (warp > 0 ? 1 : 0)) * kPrW + lane;
+        if constexpr (PE) {   // the row above my first row: slot 2w (the warp above's last, or mine at the edge)
+            const int base = (2 * warp) * kPrW + lane;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                prev_a[q] = pub0[base + 32 * q];
+                prev_b[q] = C8 ? pub1[base + 32 * q] : b[0][q];
+                prev_v[q] = pubv[base + 32 * q];
+            }
+        } else {   // the last row of the warp above (or myself at the region edge)
+            const int base = (warp > 0 ? 2 * warp : 1) * kPrW + lane;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 prev_a[q] = warp > 0 ? pub0[base + 32 * q] : a[0][q];
@@ -327,9 +353,17 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             if (k + 1 < kPrRows) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q) { next_a[q] = a[k + 1][q]; next_b[q] = b[k + 1][q]; next_v[q] = sp[k + 1][q]; }
-            } else {
+            } else if constexpr (PE) {   // slot 2w + 3: the warp below's first row, or mine at the edge
+                const int base = (2 * warp + 3) * kPrW + lane;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    next_a[q] = pub0[base + 32 * q];
+                    next_b[q] = C8 ? pub1[base + 32 * q] : b[k][q];
+                    next_v[q] = pubv[base + 32 * q];
+                }
+            } else {   // the first row of the warp below (or myself at the region edge)
                 const bool below = warp + 1 < kPrWarps;
-                const int base = ((below ? warp + 1 : warp) * 2 + (below ? 0 : 1)) * kPrW + lane;
+                const int base = (below ? 2 * warp + 3 : 2 * warp + 2) * kPrW + lane;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     next_a[q] = below ? pub0[base + 32 * q] : a[k][q];
