@@ -147,9 +147,13 @@ int sf_step(sf_ctx* c, const float* image, const float* range, float dt,
             float* flow_out, float* invdepth_out, void* stream);
 
 /* sf_step on HOST buffers: copies image and range to the device, runs the
- * step and copies the outputs back, all on `stream`, then waits for the
- * stream.  Pinned host buffers make the copies run at full speed.  image and
- * range hold H x W floats each. */
+ * step and copies the outputs back, then waits for `stream` and for the
+ * library's own copy stream.  The input copies run on that internal stream,
+ * after the work already queued on `stream`, beside the propagation (which
+ * reads only the state); the update waits for them, and the output copies run
+ * on `stream`.  Pinned host buffers make the copies run at full speed.  image
+ * and range hold H x W floats each.  SF_EINVAL for a null context, image or
+ * range, or a dt that is not finite and positive (before any copy). */
 int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt,
                  float* flow_out, float* invdepth_out, void* stream);
 

@@ -784,8 +784,10 @@ int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, f
 }
 
 // the launches of one frame (no host synchronisation; capturable)
+// inputs: an event the update waits for (inputs still being copied in while
+// the propagation, which reads only the state, runs), or null
 int engine_launches(Engine& E, const float* image, const float* range, float dt, float wscale, float* flow,
-                    float* inv, cudaStream_t st)
+                    float* inv, cudaStream_t st, cudaEvent_t inputs = nullptr)
 {
     UpdArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -820,6 +822,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
     } else {
         slot = (int)E.prop.size() + (E.surr ? 1 : 0);
     }
+    if (inputs && cudaStreamWaitEvent(st, inputs, 0) != cudaSuccess) return SF_ECUDA;
     return engine_update_launches(E, a, dt, flow, inv, slot, st);
 }
 
@@ -849,6 +852,8 @@ struct sf_ctx {
     float* stage_range = nullptr;
     float* stage_flow = nullptr;
     float* stage_inv = nullptr;
+    cudaStream_t stage_copy = nullptr;                      // input copies, beside the propagation
+    cudaEvent_t stage_free = nullptr, stage_in = nullptr;   // staging free / inputs copied
     // sf_submit_host: per slot image, range, flow (3 planes), inverse depth on
     // the device; input copies on pipe_in, output copies on pipe_out, the step
     // on the caller's stream; events order the three and guard slot reuse
@@ -875,6 +880,12 @@ void destroy_ctx(sf_ctx* c)
     cudaFree(c->stage_range);
     cudaFree(c->stage_flow);
     cudaFree(c->stage_inv);
+    if (c->stage_copy) {
+        cudaStreamSynchronize(c->stage_copy);
+        cudaStreamDestroy(c->stage_copy);
+    }
+    if (c->stage_free) cudaEventDestroy(c->stage_free);
+    if (c->stage_in) cudaEventDestroy(c->stage_in);
     for (int k = 0; k < kRing; ++k) {
         cudaFree(c->ring[k]);
         if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
@@ -976,13 +987,15 @@ int sf_reset(sf_ctx* c)
     return SF_OK;
 }
 
-int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
-            void* stream)
+namespace {
+
+int step_impl(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
+              cudaStream_t st, cudaEvent_t inputs)
 {
     if (!c || !image || !range || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
     Engine& E = c->E;
     const float wscale = E.initialised ? dt / E.dt_prev : 1.0f;   // reading R9
-    const int r = engine_launches(E, image, range, dt, wscale, flow_out, invdepth_out, (cudaStream_t)stream);
+    const int r = engine_launches(E, image, range, dt, wscale, flow_out, invdepth_out, st, inputs);
     if (r) return r;
     E.parity ^= 1;
     E.initialised = 1;
@@ -990,10 +1003,18 @@ int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* 
     return SF_OK;
 }
 
+}  // namespace
+
+int sf_step(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
+            void* stream)
+{
+    return step_impl(c, image, range, dt, flow_out, invdepth_out, (cudaStream_t)stream, nullptr);
+}
+
 int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, float* flow_out, float* invdepth_out,
                  void* stream)
 {
-    if (!c || !image || !range) return SF_EINVAL;
+    if (!c || !image || !range || !(dt > 0.0f) || !std::isfinite(dt)) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)c->E.st[0].H * c->E.st[0].W;
     if (!c->stage_image) {
@@ -1003,12 +1024,29 @@ int sf_step_host(sf_ctx* c, const float* image, const float* range, float dt, fl
             cudaMalloc(&c->stage_inv, n * sizeof(float)) != cudaSuccess)
             return SF_ENOMEM;
     }
-    if (cudaMemcpyAsync(c->stage_image, image, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(c->stage_range, range, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (!c->stage_copy) {
+        if (cudaStreamCreateWithFlags(&c->stage_copy, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->stage_in, cudaEventDisableTiming) != cudaSuccess)
+            return SF_ECUDA;
+    }
+    // the inputs go in on a side stream once the staging is free (earlier work
+    // on the caller's stream done with it), beside the propagation, which reads
+    // only the state; the update waits for them
+    if (cudaEventRecord(c->stage_free, st) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stage_copy, c->stage_free, 0) != cudaSuccess ||
+        cudaMemcpyAsync(c->stage_image, image, n * sizeof(float), cudaMemcpyHostToDevice, c->stage_copy) != cudaSuccess ||
+        cudaMemcpyAsync(c->stage_range, range, n * sizeof(float), cudaMemcpyHostToDevice, c->stage_copy) != cudaSuccess ||
+        cudaEventRecord(c->stage_in, c->stage_copy) != cudaSuccess) {
+        cudaStreamSynchronize(c->stage_copy);   // no copy from the caller's buffers outlives the call
         return SF_ECUDA;
-    int r = sf_step(c, c->stage_image, c->stage_range, dt, flow_out ? c->stage_flow : nullptr,
-                    invdepth_out ? c->stage_inv : nullptr, stream);
-    if (r) return r;
+    }
+    int r = step_impl(c, c->stage_image, c->stage_range, dt, flow_out ? c->stage_flow : nullptr,
+                      invdepth_out ? c->stage_inv : nullptr, st, c->stage_in);
+    if (r) {
+        cudaStreamSynchronize(c->stage_copy);
+        return r;
+    }
     if (flow_out && cudaMemcpyAsync(flow_out, c->stage_flow, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st) !=
                         cudaSuccess)
         return SF_ECUDA;
