@@ -790,8 +790,8 @@ k_smooth_recon(const SmoothJob* __restrict__ jobs, const int4* __restrict__ work
 {
     extern __shared__ float4 sm4[];
     pdl_trigger();
+    const int4 wk = work[blockIdx.x];   // the plan is written by no kernel: read before the wait
     pdl_wait();   // the solution, Y-hat and the coarser level come from earlier kernels
-    const int4 wk = work[blockIdx.x];
     const SmoothJob& J = jobs[wk.x];
     constexpr int T = kSmoothT, CE = kSmoothC;
     const int S = J.S, SX = T + 4 * S, SP = SX + 1, PL = SX * SP;
@@ -1078,27 +1078,30 @@ __global__ void __launch_bounds__(kThreads) k_recon_jobs(const ReconJob* __restr
                                                         float* frame_flow, float* frame_inv)
 {
     pdl_trigger();
-    pdl_wait();
+    // the plan (work list, jobs) is written by no kernel: read it before the wait,
+    // overlapping the previous kernel's tail
     const int4 wk = work[blockIdx.x];
     const ReconJob& J = jobs[wk.x];
-    const int n = J.H * J.W, p1 = min(n, wk.y + kReconChunk);
+    const int JW = J.W, Hc = J.Hc, Wc = J.Wc;
+    const int n = J.H * JW, p1 = min(n, wk.y + kReconChunk);
     float4* __restrict__ s0 = J.s0[q];
     const float4* __restrict__ c = J.s0c[q];
     float* const flow_out = J.frame_outputs ? frame_flow : J.flow_out;
     float* const inv_out = J.frame_outputs ? frame_inv : J.invdepth_out;
+    pdl_wait();
     bool bad = false;
 #pragma unroll
     for (int u = 0; u < kReconChunk / kThreads; ++u) {
         const int p = wk.y + threadIdx.x + u * kThreads;
         if (p >= p1) break;
-        const int i = p / J.W, j = p - (p / J.W) * J.W;
+        const int i = p / JW, j = p - (p / JW) * JW;
         float4 s = s0[p];
         const int i0 = (i - 1) >> 1, j0 = (j - 1) >> 1;   // bilinear x2 at pixel centres (reading R14)
         const float fy = (i & 1) ? 0.25f : 0.75f, fx = (j & 1) ? 0.25f : 0.75f;
-        const int ia = clampi(i0, 0, J.Hc - 1), ib = clampi(i0 + 1, 0, J.Hc - 1);
-        const int ja = clampi(j0, 0, J.Wc - 1), jb = clampi(j0 + 1, 0, J.Wc - 1);
-        const float4 c00 = c[ia * J.Wc + ja], c01 = c[ia * J.Wc + jb];
-        const float4 c10 = c[ib * J.Wc + ja], c11 = c[ib * J.Wc + jb];
+        const int ia = clampi(i0, 0, Hc - 1), ib = clampi(i0 + 1, 0, Hc - 1);
+        const int ja = clampi(j0, 0, Wc - 1), jb = clampi(j0 + 1, 0, Wc - 1);
+        const float4 c00 = c[ia * Wc + ja], c01 = c[ia * Wc + jb];
+        const float4 c10 = c[ib * Wc + ja], c11 = c[ib * Wc + jb];
         const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
         s.x += wy0 * (wx0 * c00.x + fx * c01.x) + fy * (wx0 * c10.x + fx * c11.x);
         s.y += wy0 * (wx0 * c00.y + fx * c01.y) + fy * (wx0 * c10.y + fx * c11.y);
