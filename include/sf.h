@@ -333,9 +333,10 @@ int sf_propagate_imu(const sf_grid* g, int N, int flags, float wscale, const flo
 
 /* sf_propagate without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory --
- * code running inside a CUDA graph capture or a host callback, real-time
- * loops that must not touch the allocator, hosts whose memory pools belong
- * to another framework.  It computes exactly what sf_propagate computes,
+ * real-time loops that must not touch the allocator (cudaMalloc and
+ * cudaFree can block and synchronise the device), hosts whose memory pools
+ * belong to another framework, code that has been handed a fixed memory
+ * budget.  It computes exactly what sf_propagate computes,
  * with the same arguments, but keeps the fields passed between launches and
  * the launch descriptors in a file-scope device array of 33 MiB that every
  * GPU using this library holds until the process exits; it calls no
@@ -350,7 +351,9 @@ int sf_propagate_imu(const sf_grid* g, int N, int flags, float wscale, const flo
  *     overlaps on the GPU -- on different streams or different host threads
  *     without ordering between them -- race on the array.
  *   - The call enqueues two small descriptor kernels ahead of each
- *     propagation launch and returns without waiting for the stream. */
+ *     propagation launch (which is then an ordinary, fully stream-ordered
+ *     launch, since its descriptors come from those kernels) and returns
+ *     without waiting for the stream. */
 int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float wscale,
                          const float* s0_in, const float* s1_in, float* s0_out, float* s1_out,
                          int* status, void* stream);

@@ -83,10 +83,17 @@ int last_error() { return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA; 
 // each may be scheduled while the previous kernel of the stream finishes, and
 // waits (pdl_wait) before it touches anything that kernel or earlier work
 // produced, so only launch latency and index set-up overlap.
+//
+// Rule for every caller: the kernels read their launch descriptors (jobs and
+// work items) BEFORE pdl_wait, so a programmatic launch is correct only when
+// those descriptors were written by no kernel of the stream (host uploads at
+// plan creation).  A path whose descriptors come from a device kernel just
+// before the launch must pass pdl = false (an ordinary, fully serialised
+// launch), as sf_propagate_noalloc does.
 constexpr bool kUsePdl = true;
 
 template <typename... KArgs, typename... Args>
-int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+int launch_ex(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
 {
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
@@ -98,8 +105,14 @@ int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cud
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = kUsePdl ? 1 : 0;
+    cfg.numAttrs = (kUsePdl && pdl) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+template <typename... KArgs, typename... Args>
+int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    return launch_ex(true, kernel, grid, block, smem, st, args...);
 }
 
 // A launch: device copies of its jobs and of its work list (one item per CTA).
@@ -145,40 +158,46 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
 inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
 template <bool C8, bool LIT, bool IMU, bool PE>
-int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
+int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
+                       bool pdl)
 {
     if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU, PE>, p.smem)) return SF_ECUDA;
-    return launch_pdl(k_propagate<C8, LIT, IMU, PE>, dim3(p.nwork), dim3(kPrThreads), p.smem, st,
-                      (const PropJob*)p.jobs, (const int4*)p.work, parity, wscale, flags, status, mscale);
+    return launch_ex(pdl, k_propagate<C8, LIT, IMU, PE>, dim3(p.nwork), dim3(kPrThreads), p.smem, st,
+                     (const PropJob*)p.jobs, (const int4*)p.work, parity, wscale, flags, status, mscale);
 }
 
 template <bool C8, bool LIT, bool IMU>
-int launch_propagate_i(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
+int launch_propagate_i(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
+                       bool pdl)
 {
     // the padded form for launches of many sub-iterations (see kPrPaddedNf)
-    if (p.nf >= kPrPaddedNf) return launch_propagate_t<C8, LIT, IMU, true>(p, parity, wscale, flags, status, mscale, st);
-    return launch_propagate_t<C8, LIT, IMU, false>(p, parity, wscale, flags, status, mscale, st);
+    if (p.nf >= kPrPaddedNf)
+        return launch_propagate_t<C8, LIT, IMU, true>(p, parity, wscale, flags, status, mscale, st, pdl);
+    return launch_propagate_t<C8, LIT, IMU, false>(p, parity, wscale, flags, status, mscale, st, pdl);
 }
 
 template <bool C8, bool LIT>
-int launch_propagate_l(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st)
+int launch_propagate_l(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
+                       bool pdl)
 {
-    if (flags & SF_IMU) return launch_propagate_i<C8, LIT, true>(p, parity, wscale, flags, status, mscale, st);
-    return launch_propagate_i<C8, LIT, false>(p, parity, wscale, flags, status, mscale, st);
+    if (flags & SF_IMU) return launch_propagate_i<C8, LIT, true>(p, parity, wscale, flags, status, mscale, st, pdl);
+    return launch_propagate_i<C8, LIT, false>(p, parity, wscale, flags, status, mscale, st, pdl);
 }
 
 // one propagation launch; with SF_IMU in flags the jobs' motion slots hold
 // (Omega, a) and mscale converts them to frame units (Omega mscale,
-// a mscale^2): the frame time in seconds, or 1 for values already per frame
+// a mscale^2): the frame time in seconds, or 1 for values already per frame.
+// pdl = false for a plan whose descriptors a kernel has just written (see
+// launch_ex).
 int launch_propagate(const Plan& p, int parity, float wscale, int flags, int* status, cudaStream_t st,
-                     float mscale = 1.0f)
+                     float mscale = 1.0f, bool pdl = true)
 {
     if (p.nwork == 0) return SF_OK;
     const bool lit = (flags & SF_DOMINANT_LITERAL) != 0;
-    if (p.c8) return lit ? launch_propagate_l<true, true>(p, parity, wscale, flags, status, mscale, st)
-                         : launch_propagate_l<true, false>(p, parity, wscale, flags, status, mscale, st);
-    return lit ? launch_propagate_l<false, true>(p, parity, wscale, flags, status, mscale, st)
-               : launch_propagate_l<false, false>(p, parity, wscale, flags, status, mscale, st);
+    if (p.c8) return lit ? launch_propagate_l<true, true>(p, parity, wscale, flags, status, mscale, st, pdl)
+                         : launch_propagate_l<true, false>(p, parity, wscale, flags, status, mscale, st, pdl);
+    return lit ? launch_propagate_l<false, true>(p, parity, wscale, flags, status, mscale, st, pdl)
+               : launch_propagate_l<false, false>(p, parity, wscale, flags, status, mscale, st, pdl);
 }
 
 int launch_solve(const Plan& p, const UpdArgs& a, cudaStream_t st)
@@ -2007,9 +2026,11 @@ int sf_reconstruct(int levels, const sf_grid* grids, float* const* s0, const flo
 // ---------------------------------------------------------------------------
 // allocation-free propagation (sf_propagate_noalloc)
 //
-// Callers that cannot allocate device memory -- code running inside a CUDA
-// graph capture or a host callback, real-time loops that must not touch the
-// allocator, or hosts whose memory pools are owned by another framework --
+// Callers that cannot allocate device memory -- code running in a stream
+// callback (where CUDA calls are not allowed at all), real-time loops that
+// must not touch the allocator (cudaMalloc and cudaFree can block and
+// synchronise the device), or hosts whose memory pools are owned by another
+// framework --
 // get sf_propagate's result without cudaMalloc/cudaMallocAsync/cudaFree: the
 // intermediate fields and the launch descriptors live in one file-scope
 // device array that every GPU using this library holds until exit.
@@ -2021,6 +2042,9 @@ constexpr size_t kNoAllocDescBytes = size_t(1) << 20;                      // jo
 constexpr size_t kNoAllocFieldBytes = 2 * kNoAllocMaxPixels * sizeof(float4);  // (s0, s1) between launches
 constexpr size_t kNoAllocJobBytes = 256;                                   // job slot ahead of the tiles
 constexpr int kNoAllocMaxDevices = 64;
+// the job slot must hold a PropJob and keep the int4 tile list behind it aligned
+static_assert(sizeof(PropJob) <= kNoAllocJobBytes, "PropJob outgrew its slot in the allocation-free array");
+static_assert(kNoAllocJobBytes % alignof(int4) == 0, "tile list behind the job slot must be int4-aligned");
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDescBytes + kNoAllocFieldBytes];
@@ -2114,7 +2138,10 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
         pl.jobs = djob;
         pl.work = dwork;
         pl.nwork = ntiles;
-        r = launch_propagate(pl, 0, wscale, flags, status, st);
+        // an ordinary launch: k_propagate reads its job and work item before
+        // griddepcontrol.wait, so a programmatic launch could read the
+        // descriptors before the two kernels above have written them
+        r = launch_propagate(pl, 0, wscale, flags, status, st, 1.0f, /*pdl=*/false);
         in0 = o0;
         in1 = o1;
     }

@@ -1,9 +1,9 @@
 """sf_propagate_noalloc: the allocation-free propagation entry point.
 
-Some callers cannot allocate device memory while they run the filter: code
-inside a CUDA graph capture or a host callback, real-time loops that must not
-touch the allocator, processes whose memory pools belong to another
-framework.  For them the library offers sf_propagate_noalloc, which keeps its
+Some callers cannot allocate device memory while they run the filter:
+real-time loops that must not touch the allocator (cudaMalloc and cudaFree can
+block and synchronise the device), processes whose memory pools belong to
+another framework, code handed a fixed memory budget.  For them the library offers sf_propagate_noalloc, which keeps its
 scratch in a fixed device array instead of allocating.  This file checks,
 through the C ABI, that it returns what the allocating sf_propagate returns,
 on two calls in a row (the second call sees the array as the first left it).
