@@ -436,6 +436,19 @@ int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const 
 int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w,
                const float* bias, int relu, void* y, float* y32, int* status, void* stream);
 
+/* Weight and bias gradients of one 3x3 layer (the contraction over pixels
+ * of the surrogate's training step):
+ *   dw[3 dy + dx][co][ci] = sum_{n,i,j} g[n,i,j,co] x[n, i+dy-1, j+dx-1, ci]
+ *   db[co] = sum_{n,i,j} g[n,i,j,co]
+ * with x outside the frame read as zero.  x: device N x H x W x Cin
+ * bfloat16 (NHWC); dy = g: device N x H x W x Cout bfloat16; dw: device
+ * 9 x Cout x Cin float32 and db: device Cout float32, both overwritten
+ * (FP32 accumulation).  Cin and Cout are 16 or 32; pointers 16-byte
+ * aligned.  SF_EINVAL for bad shapes or pointers (checked before any device
+ * call).  Asynchronous on `stream`. */
+int sf_conv3x3_wgrad(int N, int H, int W, int Cin, int Cout, const void* x, const void* dy,
+                     float* dw, float* db, void* stream);
+
 /* Self-test of the convolution's bounded wait: runs one tile whose MMAs are
  * never issued, so its mbarrier wait cannot complete; the kernel gives up
  * after a short poll limit, sets the timeout bit, frees its tensor memory and

@@ -1688,6 +1688,18 @@ int conv_launch(const sf_surrogate* s, int N, int H, int W, int cin, int cout, c
 
 inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, kSmCount * 8); }
 
+// weight and bias gradients of one 3x3 layer, ADDED into dw [9][Cout][Cin]
+// and db [Cout] (the caller zeroes them)
+int wgrad_launch(int N, int H, int W, int Cin, int Cout, const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw,
+                 float* db, cudaStream_t st)
+{
+    const int blocks = std::min(N * H * ((W + 127) / 128), kSmCount * 2);
+    const size_t wsm = wgrad_smem_bytes(Cin, Cout);
+    if (set_smem_attr((const void*)k_wgrad, wsm)) return SF_ECUDA;
+    k_wgrad<<<blocks, kWgThreads, wsm, st>>>(N, H, W, Cin, Cout, x, dy, dw, db);
+    return last_error();
+}
+
 // features, the four layers (the three hidden activations kept for the
 // backward pass), FP32 output in y32
 int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, cudaStream_t st)
@@ -1708,6 +1720,21 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
 }
 
 }  // namespace
+
+int sf_conv3x3_wgrad(int N, int H, int W, int Cin, int Cout, const void* x, const void* dy, float* dw, float* db,
+                     void* stream)
+{
+    if (N < 1 || H < 1 || W < 1 || (Cin != 16 && Cin != 32) || (Cout != 16 && Cout != 32) || !x || !dy || !dw ||
+        !db)
+        return SF_EINVAL;
+    if (!aligned16(x) || !aligned16(dy) || !aligned16(dw) || !aligned16(db)) return SF_EINVAL;
+    if ((double)N * H * W * (Cin > Cout ? Cin : Cout) > 2147483647.0) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the kernel adds into its outputs
+    if (cudaMemsetAsync(dw, 0, (size_t)9 * Cin * Cout * sizeof(float), st) != cudaSuccess) return SF_ECUDA;
+    if (cudaMemsetAsync(db, 0, (size_t)Cout * sizeof(float), st) != cudaSuccess) return SF_ECUDA;
+    return wgrad_launch(N, H, W, Cin, Cout, (const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, dw, db, st);
+}
 
 int sf_selftest_conv_timeout(void* stream)
 {
@@ -1853,14 +1880,10 @@ int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const floa
     // backward: dy of layer l is `d`, its input activation `in`
     const __nv_bfloat16* d = s->dy;
     __nv_bfloat16* bufs[2] = {s->dA, s->dB};
-    const int wg_blocks = std::min(n * g->H * ((g->W + 127) / 128), kSmCount * 2);
     for (int l = sf_surrogate::kL - 1; l >= 0 && !r; --l) {
         const __nv_bfloat16* in = l == 0 ? s->x0 : s->a[l - 1];
-        const size_t wsm = wgrad_smem_bytes(s->cin[l], s->cout[l]);
-        if (set_smem_attr((const void*)k_wgrad, wsm)) { r = SF_ECUDA; break; }
-        k_wgrad<<<wg_blocks, kWgThreads, wsm, st>>>(n, g->H, g->W, s->cin[l], s->cout[l], in, d,
-                                                    s->grad + s->off[l], s->grad + s->off[l] + 9 * s->cin[l] * s->cout[l]);
-        r = last_error();
+        r = wgrad_launch(n, g->H, g->W, s->cin[l], s->cout[l], in, d, s->grad + s->off[l],
+                         s->grad + s->off[l] + 9 * s->cin[l] * s->cout[l], st);
         if (r || l == 0) break;
         __nv_bfloat16* dx = bufs[l & 1];
         r = conv_launch(s, n, g->H, g->W, s->cout[l], s->cin[l], d, s->w16t[l], nullptr, 0, dx, nullptr, st);

@@ -203,6 +203,19 @@ def _ray_box(o, d, lo, hi):
     return np.where(hit & (t > 1e-6), t, np.inf)
 
 
+def _map_frames(fn, frames):
+    """[fn(0), ..., fn(frames - 1)] on a pool of threads (numpy releases the
+    interpreter lock inside its array operations, so the frames render in
+    parallel); fn must not draw random numbers."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    workers = max(1, min(frames, os.cpu_count() or 1, 32))
+    if workers == 1:
+        return [fn(k) for k in range(frames)]
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, range(frames)))
+
+
 def _random_walk(rng, F, sigma, vmax, start=None):
     x = np.zeros((F, 3)) if start is None else np.tile(start, (F, 1)).astype(np.float64)
     cur = x[0].copy()
@@ -312,10 +325,9 @@ def scene512(frames=300, seed=1001, H=512, W=512, rate=600.0, max_flow=8.0, leve
     v *= s
     om *= s
     Rs, ps = _integrate(v, om, dt)
-    imgs, rngs = [], []
-    for k in range(frames):
-        y, lam = render(Rs[k], ps[k])
-        imgs.append(y); rngs.append(lam)
+    out = _map_frames(lambda k: render(Rs[k], ps[k]), frames)
+    imgs = [y for y, _ in out]
+    rngs = [lam for _, lam in out]
     return Sequence("scene512", np.array(imgs, np.float32), np.array(rngs, np.float32), dt,
                     fx, fy, cx, cy, levels, list(iters), list(smooth), v, om,
                     meta=dict(velocity_scale=s))
@@ -343,8 +355,8 @@ def drive(frames=500, seed=1002, H=384, W=1248, rate=100.0, levels=3, iters=(32,
     om = np.zeros((frames, 3)); om[:, 1] = yaw
     Rs, ps = _integrate(v, om, dt)
     eta = camera_rays(H, W, fx, fy, cx, cy)
-    imgs, rngs = [], []
-    for k in range(frames):
+
+    def render(k):
         d = eta.reshape(-1, 3) @ Rs[k].T
         o = ps[k]
         best = _ray_plane(o, d, np.array([0.0, -1.0, 0.0]), np.array([0.0, 1.5, 0.0]))
@@ -357,9 +369,14 @@ def drive(frames=500, seed=1002, H=384, W=1248, rate=100.0, levels=3, iters=(32,
             if mm.any():
                 best[mm] = t[mm]
                 val[mm] = tex(o + t[mm, None] * d[mm])
-        lam = best.reshape(H, W)
+        return val.reshape(H, W), best.reshape(H, W)
+
+    out = _map_frames(render, frames)
+    imgs, rngs = [], []
+    for k in range(frames):                              # range noise drawn in frame order
+        val, lam = out[k]
         lam = np.where(np.isfinite(lam), lam * (1.0 + noise * rng.normal(size=lam.shape)), np.inf)
-        imgs.append(val.reshape(H, W)); rngs.append(lam)
+        imgs.append(val); rngs.append(lam)
     return Sequence("drive", np.array(imgs, np.float32), np.array(rngs, np.float32), dt, fx, fy, cx, cy,
                     levels, list(iters), list(smooth), v, om, meta=dict(speed=speed))
 

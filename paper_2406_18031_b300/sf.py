@@ -47,7 +47,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_update_mode", "sf_batch_solve_tile", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
-           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_selftest_conv_timeout", "sf_surrogate_create",
+           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_conv3x3_wgrad", "sf_selftest_conv_timeout", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
            "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
            "sf_batch_set_surrogate"]
@@ -87,6 +87,7 @@ def lib():
         L.sf_set_motion.argtypes = [vp, P(f), P(f), vp]
         L.sf_remap_pinhole.argtypes = [P(CGrid), P(f), i, i, P(f), vp, vp, vp, vp, vp]
         L.sf_conv3x3.argtypes = [i, i, i, i, i, vp, vp, vp, i, vp, vp, vp, vp]
+        L.sf_conv3x3_wgrad.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
         L.sf_selftest_conv_timeout.argtypes = [vp]
         L.sf_surrogate_create.argtypes = [ctypes.c_ulonglong, P(vp)]
         L.sf_surrogate_destroy.argtypes = [vp]
@@ -418,6 +419,20 @@ def conv3x3(x, w, bias=None, relu=False, y=None, y32=None, status=None, stream=N
                                    _tptr(bias, f32, Cout, "bias"), int(bool(relu)), _tptr(y, bf, m, "y"),
                                    _tptr(y32, f32, m, "y32"), _tptr(status, torch.int32, 1, "status"),
                                    _stream(stream)), "sf_conv3x3")
+
+
+def conv3x3_wgrad(x, dy, dw, db, stream=None):
+    """``sf_conv3x3_wgrad``: x [N, H, W, Cin] and dy [N, H, W, Cout] bfloat16 CUDA tensors;
+    overwrites dw [9, Cout, Cin] and db [Cout] (float32)."""
+    import torch
+    N, H, W, Cin = x.shape
+    if dy.dim() != 4 or tuple(dy.shape[:3]) != (N, H, W):
+        raise ValueError(f"dy: expected [{N}, {H}, {W}, Cout], got {list(dy.shape)}")
+    Cout = dy.shape[3]
+    bf, f32 = torch.bfloat16, torch.float32
+    return _check(lib().sf_conv3x3_wgrad(N, H, W, Cin, Cout, _tptr(x, bf, x.numel(), "x"),
+                                         _tptr(dy, bf, dy.numel(), "dy"), _tptr(dw, f32, 9 * Cout * Cin, "dw"),
+                                         _tptr(db, f32, Cout, "db"), _stream(stream)), "sf_conv3x3_wgrad")
 
 
 class Surrogate:

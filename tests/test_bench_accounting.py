@@ -3,6 +3,7 @@ the roofline figures, the launch-slot names and the whole-job rate, each
 checked against a count made by hand from the state layout (Sec. 4: w, rho,
 dw, Y-hat per pixel of a lower level; w, rho, Y-hat at the top) rather than
 against the helper's own formula."""
+import numpy as np
 import pytest
 
 import bench
@@ -75,3 +76,29 @@ def test_stored_traffic_follows_the_kernel_source(monkeypatch):
     assert bench.measured_traffic(key) == bench.TRAFFIC[key]
     monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "0" * 16)   # the kernel changed since the capture
     assert bench.measured_traffic(key) is None
+
+
+def test_pixel_spacing_matches_the_oracle_geometry():
+    import oracle
+    oracle.build()
+    H, W, fx, fy, cx, cy = 24, 40, 30.0, 28.0, 19.0, 13.0
+    _, _, dmu = oracle.geometry(H, W, fx, fy, cx, cy)
+    np.testing.assert_allclose(bench.pixel_spacing(H, W, fx, fy, cx, cy), dmu, rtol=1e-12)
+
+
+def test_flow_errors_of_known_differences():
+    H, W, dt = 3, 4, 0.01
+    dmu = np.full((H, W), 0.002)
+    truth = np.zeros((3, H, W))
+    truth[0] = 0.4                                   # 0.4 rad/s x 0.01 s / 0.002 = 2 px/frame along x
+    epe, aae = bench.flow_errors(truth, truth, dt, dmu)
+    assert epe == 0.0 and aae < 1e-6
+    flow = truth.copy()
+    flow[1] = 0.3                                    # + 1.5 px/frame along y
+    epe, aae = bench.flow_errors(flow, truth, dt, dmu)
+    assert abs(epe - 1.5) < 1e-12
+    # a = (2, 1.5, 0), b = (2, 0, 0): arccos(5 / sqrt(7.25 x 5))
+    assert abs(aae - np.degrees(np.arccos(5.0 / np.sqrt(7.25 * 5.0)))) < 1e-9
+    mask = np.zeros((H, W), bool)
+    mask[0, 0] = True
+    assert bench.flow_errors(flow, truth, dt, dmu, mask)[0] == epe

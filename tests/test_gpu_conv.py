@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import surrogate as oracle_surrogate
 from paper_2406_18031_b300 import sf
 from tests import gpu_util as gu
 
@@ -89,3 +90,44 @@ def test_binding_rejects_wrong_buffers_before_the_call():
     sf.conv3x3(x, w, y=y)                                              # the right ones still work
     torch.cuda.synchronize()
     assert float(y.float().abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("Cin,Cout", [(16, 32), (32, 32), (32, 16)])
+def test_weight_gradient_element_by_element(Cin, Cout):
+    # sf_conv3x3_wgrad: dW[tap, co, ci] = sum_p dy[p, co] x[p + tap, ci] over
+    # N x H x W pixels (two frames, rows of two tiles, the second ragged).
+    # The bf16 x bf16 products are exact in float32; float32 accumulation
+    # over n pixels is within n 2^-23 of the sum of |products|.  Channel
+    # means that differ per channel make every (co, ci) entry distinct, so
+    # a transposed block or a shifted tap cannot hide under the tolerance.
+    N, H, W = 2, 7, 200
+    rng = np.random.default_rng(Cin * 3 + Cout)
+    x = gu.bf16_round((rng.normal(size=(N, H, W, Cin)) + 0.2 * np.arange(Cin) - 1.0).astype(np.float32))
+    dy = gu.bf16_round((rng.normal(size=(N, H, W, Cout)) * 0.5 + 0.1 * (np.arange(Cout) - 8)).astype(np.float32))
+    dw = torch.full((9, Cout, Cin), float("nan"), device="cuda")
+    db = torch.full((Cout,), float("nan"), device="cuda")
+    sf.conv3x3_wgrad(_bf16_tensor(x), _bf16_tensor(dy), dw, db)
+    torch.cuda.synchronize()
+    ref_w, ref_b = oracle_surrogate.conv3x3_wgrad(x, dy)
+    mag_w, mag_b = oracle_surrogate.conv3x3_wgrad(np.abs(x), np.abs(dy))
+    gam = N * H * W * 2.0 ** -23
+    got_w, got_b = dw.cpu().numpy(), db.cpu().numpy()
+    assert np.all(np.abs(got_w - ref_w) <= gam * mag_w)
+    assert np.all(np.abs(got_b - ref_b) <= gam * mag_b)
+    # the tolerance separates neighbouring taps and swapped channels
+    assert (np.abs(np.roll(ref_w, 1, axis=0) - ref_w) > gam * mag_w).mean() > 0.9
+    assert (np.abs(np.swapaxes(ref_w[:, :16, :16], 1, 2) - ref_w[:, :16, :16]) > gam * mag_w[:, :16, :16]).mean() > 0.8
+
+
+def test_weight_gradient_called_twice_overwrites():
+    # the entry point overwrites its outputs (the kernel adds into zeroed buffers)
+    rng = np.random.default_rng(7)
+    x = gu.bf16_round(rng.normal(size=(1, 3, 130, 16)).astype(np.float32))
+    dy = gu.bf16_round(rng.normal(size=(1, 3, 130, 16)).astype(np.float32))
+    dw = torch.empty((9, 16, 16), device="cuda")
+    db = torch.empty((16,), device="cuda")
+    sf.conv3x3_wgrad(_bf16_tensor(x), _bf16_tensor(dy), dw, db)
+    first = dw.clone(), db.clone()
+    sf.conv3x3_wgrad(_bf16_tensor(x), _bf16_tensor(dy), dw, db)
+    torch.cuda.synchronize()
+    assert torch.allclose(dw, first[0], rtol=1e-6, atol=1e-6) and torch.allclose(db, first[1], rtol=1e-6, atol=1e-6)

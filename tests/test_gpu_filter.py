@@ -199,6 +199,20 @@ def test_hundred_frame_drift(case):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("case", ["scene512", "drive"])
+def test_hundred_frame_drift_full_size(case):
+    # the contract's 1e-3 relative after 100 frames on the benchmark's
+    # workload (512x512, 2 levels, N = [8, 4], S = [2, 4], 8 px/frame) and on
+    # the driving workload (384x1248, 3 levels, N = [32, 16, 8], S = [2, 4, 4]),
+    # both at full size, 100 consecutive frames of their sequences
+    seq = scenes.scene512(frames=100) if case == "scene512" else scenes.drive(frames=100)
+    errs, (gf, gi), (rf, ri), st = _run(seq, 100, check_every=False)
+    assert gu.rel_l2(gf, rf) <= gu.DRIFT_TOL, gu.rel_l2(gf, rf)
+    assert gu.rel_l2(gi, ri) <= gu.DRIFT_TOL, gu.rel_l2(gi, ri)
+    assert st >= 0
+
+
+@pytest.mark.slow
 def test_full_size_512_two_levels():
     # the benchmark's workload (512x512, 2 levels, N = [8, 4], S = [2, 4]) in the
     # same launch configuration, three frames, every pixel

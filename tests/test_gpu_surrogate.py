@@ -5,8 +5,11 @@ bfloat16 at the points where the CUDA path stores bfloat16.
 Forward: the prediction agrees within 2^-7 of the largest output (one
 bfloat16 ulp of a value that may round differently when its float32 and
 float64 sums straddle a rounding boundary) plus 1e-4 (float32 accumulation),
-in the network's units.  Gradients: relative L2 error per layer within 3e-2
-(bfloat16 output and input gradients).  Training: 400 Adam steps on pairs
+in the network's units.  Gradients: every weight and bias within (2^-7 +
+n 2^-23) of the |.|-weighted sum of the products that form it
+(tests/surrogate_bounds.py: one bfloat16 ulp for the isolated stores and ReLU
+decisions that round differently, float32 accumulation over n pixels).
+Training: 400 Adam steps on pairs
 produced by the plain propagation lower the loss at least five-fold."""
 import numpy as np
 import pytest
@@ -15,6 +18,7 @@ import oracle
 from oracle import surrogate as S
 from paper_2406_18031_b300 import sf
 from tests import gpu_util as gu
+from tests import surrogate_bounds as SB
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -79,11 +83,17 @@ def test_gradients_match_oracle():
                                                                     np.full((H, W, 1), 0.01)], -1)[None])
     loss = net.train_step(g, torch.from_numpy(s0).cuda(), torch.from_numpy(tgt).cuda(), lr=0.0)
     gg = net.grads()
-    ref_loss, ref_g = S.loss_and_grads(S.features(eta, dmu, s0), p, S.residual_target(eta, dmu, s0, tgt), q=S.bf16)
+    ref_loss, ref_g, tol = SB.oracle_gradients_and_tolerance(S.features(eta, dmu, s0), p,
+                                                             S.residual_target(eta, dmu, s0, tgt))
     assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    # element by element: every weight and bias of every layer
+    bad = np.abs(gg - ref_g) > tol
+    assert not bad.any(), (int(bad.sum()), np.flatnonzero(bad)[:8], (np.abs(gg - ref_g) / np.maximum(tol, 1e-300)).max())
+    # the comparison is not vacuous: the gradients are far from zero and the
+    # tolerance is a small fraction of them
     for sl in _layer_slices():
-        err = np.linalg.norm(gg[sl] - ref_g[sl]) / np.linalg.norm(ref_g[sl])
-        assert err <= 3e-2, err
+        nz = ref_g[sl] != 0
+        assert nz.mean() > 0.3 and np.median(tol[sl][nz] / np.abs(ref_g[sl][nz])) < 0.05
     np.testing.assert_array_equal(net.params(), p)     # lr = 0 leaves the parameters
 
 
