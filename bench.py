@@ -471,7 +471,7 @@ def run_ours(args):
             e2e = measure_e2e(filt, seq, args.steps, host_io)
             imu = measure_imu(seq, images, ranges, min(args.steps, 100), evict_l2)
             remap = measure_remap(seq, images, ranges, min(args.steps, 100), evict_l2)
-            surrogate = measure_surrogate(min(args.steps, 30), dev)
+            surrogate, held = measure_surrogate(min(args.steps, 30), dev, seq)
             frame1024 = measure_1024(min(args.steps, 100), evict_l2, dev)
             plane64 = measure_plane64(max(args.steps, 200), dev)
             drive_seq = scenes.drive(frames=DRIVE_FRAMES)
@@ -481,6 +481,7 @@ def run_ours(args):
                                                         solve_tile=solve_tile), dev)
             p64 = scenes.plane64(frames=20)
             cpu = cpu_baseline(seq, gpu_first_flows(seq, frames=3))
+            surrogate["vs_oracle"] = surrogate_vs_oracle(held)
             otable = oracle_table([("plane64", p64, gpu_first_flows(p64, frames=3)),
                                    ("drive", drive_seq, gpu_first_flows(drive_seq, frames=3))])
             epe = cpu.pop("epe_vs_gpu_px") or {}
@@ -763,6 +764,7 @@ def measure_remap(seq, images, ranges, steps, evict_l2):
 
 
 SURR_TRAIN_STEPS = 1500
+SURR_N = 4               # the plain propagation the surrogate learns: 4 sub-iterations (the evaluation streams' N)
 
 
 def surrogate_flops_per_px():
@@ -770,69 +772,78 @@ def surrogate_flops_per_px():
     return 2 * 9 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16)
 
 
-def measure_surrogate(steps, dev):
-    """The learned propagation surrogate on 16 single-level 1024 x 1024
-    streams (plane scenes, peak flow below 4 px/frame, N = 4): trained here on
-    pairs from the plain propagation (random smooth states of 8 x 256^2
-    pixels, SURR_TRAIN_STEPS Adam steps), then (a) one-frame prediction
-    error against the plain propagation on held-out states, (b) the batch
-    step with the plain propagation against the batch step with the
-    surrogate predicting the top level, (c) the flow difference between the
-    two batches after the timed frames."""
+def top_level_pairs(seq, dev, frames, skip=2):
+    """Training pairs the plain propagation generates: the plain GPU filter
+    runs over `frames` frames of seq; after each frame from `skip` on, its
+    top-level state (w, rho) and that state propagated by the plain scheme
+    with SURR_N sub-iterations.  Returns (grid, states [n, H, W, 4], targets,
+    dmu of the top level)."""
+    import torch
+    from paper_2406_18031_b300 import sf
+    H, W = seq.shape
+    L = seq.levels
+    f = sf.Filter(H, W, L, sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters,
+                                      smooth=seq.smooth))
+    sc = 2.0 ** (L - 1)
+    Hh, Wh = H >> (L - 1), W >> (L - 1)
+    g = sf.grid(Hh, Wh, seq.fx / sc, seq.fy / sc, seq.cx / sc, seq.cy / sc)
+    states = []
+    for k in range(frames):
+        f.step(torch.from_numpy(seq.image[k]).to(dev), torch.from_numpy(seq.range[k]).to(dev), seq.dt)
+        if k >= skip:
+            planes, _ = f.get_state(L - 1)
+            states.append(planes[0:4].permute(1, 2, 0).contiguous())
+    f.close()
+    s0 = torch.stack(states)
+    tgt = torch.empty_like(s0)
+    for k in range(s0.shape[0]):
+        sf.propagate(g, SURR_N, s0[k], tgt[k])
+    dmu = pixel_spacing(Hh, Wh, seq.fx / sc, seq.fy / sc, seq.cx / sc, seq.cy / sc)
+    return g, s0, tgt, dmu
+
+
+def measure_surrogate(steps, dev, seq512):
+    """The learned propagation surrogate (configuration 5).  Training pairs
+    come from the plain propagation itself on the configuration-1 and -2
+    sequences (the top-level state of the plain filter after every frame of
+    plane64 and of the first 40 frames of scene512, each propagated by the
+    plain scheme with N = 4: 2.6 M pixel pairs), SURR_TRAIN_STEPS Adam steps.
+    Then (a) one-frame prediction error against the plain GPU propagation on
+    held-out states (scene512 frames 42..47), (b) the batch step of 16
+    single-level 1024 x 1024 plane streams (peak flow below 4 px/frame, N = 4)
+    with the plain propagation against the batch step with the surrogate
+    predicting the top level and its on-device fallback (default threshold 1
+    px/frame), (c) both batches' flow against the analytic truth and against
+    each other after the timed frames.  Returns the line's dict and the
+    held-out (grid, states, predictions, plain targets) for the CPU leg."""
     import torch
     from paper_2406_18031_b300 import scenes, sf
     rng = np.random.default_rng(17)
-
-    def states(n, H, W, g_eta_dmu, max_px):
-        eta, dmu = g_eta_dmu
-        out = []
-        for _ in range(n):
-            f = np.zeros((H, W, 3))
-            for c in range(3):
-                for _w in range(4):
-                    k = rng.uniform(0.02, 0.2, size=2) * rng.choice([-1, 1], size=2)
-                    i, j = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
-                    f[..., c] += rng.uniform(0.3, 1.0) * np.sin(k[0] * i + k[1] * j + rng.uniform(0, 6.3))
-            f *= max_px / np.abs(f).max()
-            w = f * dmu[..., None] * np.array([1.0, 1.0, 0.3])
-            rho = 0.2 + 0.1 * np.sin(np.arange(H)[:, None] * 0.05 + np.arange(W)[None] * 0.03)
-            out.append(np.concatenate([w, rho[..., None]], -1))
-        return torch.from_numpy(np.stack(out).astype(np.float32)).to(dev)
-
-    def geometry(H, W, f):
-        j = (np.arange(W) + 0.5 - W / 2) / f
-        i = (np.arange(H) + 0.5 - H / 2) / f
-        x, y = np.meshgrid(j, i)
-        d = np.stack([x, y, np.ones_like(x)], -1)
-        eta = d / np.linalg.norm(d, axis=-1, keepdims=True)
-        dmu = (1.0 / f) / np.sqrt((x + 1.0 / f) ** 2 + y ** 2 + 1.0) * np.sqrt(1.0 - eta[..., 0] ** 2)
-        return eta, dmu
-
-    N = 4
-    # training pairs
-    Ht = Wt = 256
-    gt = sf.grid(Ht, Wt, Wt / 2, Wt / 2, Wt / 2, Ht / 2)
-    geo_t = geometry(Ht, Wt, Wt / 2)
-    s_train = states(8, Ht, Wt, geo_t, 3.0)
-    t_train = torch.empty_like(s_train)
-    for k in range(8):
-        sf.propagate(gt, N, s_train[k], t_train[k])
+    p64 = scenes.plane64(frames=20)
+    g1, s1, t1, d1 = top_level_pairs(p64, dev, 20)
+    g2, s2, t2, d2 = top_level_pairs(seq512, dev, 48)
+    s2_train, t2_train = s2[:38].contiguous(), t2[:38].contiguous()     # frames 2..39
+    s2_test, t2_test = s2[-6:].contiguous(), t2[-6:].contiguous()       # frames 42..47, held out
+    pairs = s1.shape[0] * s1.shape[1] * s1.shape[2] + s2_train.shape[0] * s2_train.shape[1] * s2_train.shape[2]
     net = sf.Surrogate(seed=2024)
     t0 = time.perf_counter()
-    losses = [net.train_step(gt, s_train, t_train, lr=2e-3 if k < SURR_TRAIN_STEPS // 2 else 5e-4)
-              for k in range(SURR_TRAIN_STEPS)]
+    losses = []
+    for k in range(SURR_TRAIN_STEPS):
+        lr = 2e-3 if k < SURR_TRAIN_STEPS // 2 else 5e-4
+        if k % 4 == 0:
+            losses.append(net.train_step(g1, s1, t1, lr=lr))
+        else:
+            idx = torch.from_numpy(rng.choice(s2_train.shape[0], size=8, replace=False)).to(dev)
+            losses.append(net.train_step(g2, s2_train[idx].contiguous(), t2_train[idx].contiguous(), lr=lr))
     train_s = time.perf_counter() - t0
-    # held-out prediction error (px/frame)
-    s_test = states(4, Ht, Wt, geo_t, 3.0)
-    t_test = torch.empty_like(s_test); p_test = torch.empty_like(s_test)
-    for k in range(4):
-        sf.propagate(gt, N, s_test[k], t_test[k])
-    net.forward(gt, s_test, p_test)
+    p_test = torch.empty_like(s2_test)
+    net.forward(g2, s2_test, p_test)
     torch.cuda.synchronize()
-    dmu_t = torch.from_numpy(geo_t[1].astype(np.float32)).to(dev)
-    err = torch.linalg.norm(p_test[..., :3] - t_test[..., :3], dim=-1) / dmu_t
+    dmu2 = torch.from_numpy(d2.astype(np.float32)).to(dev)
+    err = torch.linalg.norm(p_test[..., :3] - t2_test[..., :3], dim=-1) / dmu2
     # the batch: plain against surrogate
     H = W = 1024
+    N = SURR_N
     seqs = []
     for k in range(16):
         depth = rng.uniform(3.0, 8.0)
@@ -847,6 +858,7 @@ def measure_surrogate(steps, dev):
     stream = torch.cuda.current_stream()
     out = {}
     flows = {}
+    dmu1 = pixel_spacing(H, W, W / 2, W / 2, W / 2, H / 2)
     for mode in ("plain", "surrogate"):
         P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
         batch = sf.Batch([q.shape for q in seqs], [1] * len(seqs), P)
@@ -869,38 +881,78 @@ def measure_surrogate(steps, dev):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        last = (4 + steps - 1) % BATCH_FRAMES
         flows[mode] = [batch.slots[s_][2].clone() for s_ in range(len(seqs))]
+        truth = [flow_errors(flows[mode][s_].cpu().numpy(), seqs[s_].gt_flow(last), dt, dmu1)
+                 for s_ in range(len(seqs))]
+        res = {"ms_per_step": ms, "frames_per_s_per_stream": 1e3 / ms,
+               "epe_vs_truth_px": float(np.mean([e for e, _ in truth])),
+               "aae_vs_truth_deg": float(np.mean([a for _, a in truth]))}
+        if mode == "surrogate":
+            r, c = batch.surrogate_stats()
+            res["fallback_frames"] = int(c.sum())
+            res["stream_frames"] = int(len(seqs) * (steps + 3))
+            res["residual_px_last_frame"] = {"mean": float(r.mean()), "max": float(r.max())}
+            res["threshold_px"] = 1.0
         batch.profile(True)
         load(4 + steps)
         batch.step(dt, stream=stream)
         torch.cuda.synchronize()
         batch.profile(False)
         slots = batch.profile_read()
-        out[mode] = {"ms_per_step": ms, "frames_per_s_per_stream": 1e3 / ms,
-                     "top_level_prediction_ms": slots[0][0] if slots else None}
+        res["top_level_prediction_ms"] = slots[0][0] if slots else None
+        if mode == "surrogate":
+            res["fallback_check_ms"] = slots[1][0]
+        out[mode] = res
         batch.close()
-    g1 = sf.grid(H, W, W / 2, W / 2, W / 2, H / 2)
-    dmu1 = torch.from_numpy(geometry(H, W, W / 2)[1].astype(np.float32)).to(dev)
-    diffs = [torch.linalg.norm((a - b).permute(1, 2, 0), dim=-1) * dt / dmu1 for a, b in zip(flows["plain"],
-                                                                                              flows["surrogate"])]
+    dm = torch.from_numpy(dmu1.astype(np.float32)).to(dev)
+    diffs = [torch.linalg.norm((a - b).permute(1, 2, 0), dim=-1) * dt / dm for a, b in zip(flows["plain"],
+                                                                                           flows["surrogate"])]
     d = torch.stack(diffs)
     px = 16 * H * W
     surr_ms = out["surrogate"]["top_level_prediction_ms"]
-    return {
+    line = {
         "workload": "16 single-level 1024x1024 streams, plane scenes, peak flow < 4 px/frame, N=4, smooth 2, 600 Hz",
-        "training": {"pairs": "8 random smooth 256x256 states and their plain predictions (N=4)",
+        "training": {"pairs": f"top-level states of the plain filter on plane64 (20 frames) and scene512 (frames "
+                              f"2..39) and their plain propagation (N={N}): {pairs} pixel pairs",
                      "steps": SURR_TRAIN_STEPS, "seconds": train_s, "loss_first": losses[0],
                      "loss_last": float(np.mean(losses[-20:]))},
         "prediction_error_px": {"mean": float(err.mean()), "max": float(err.max()),
-                                "states": "4 held-out random 256x256 states"},
+                                "states": "6 held-out scene512 top-level states (frames 42..47), "
+                                          "against the plain GPU propagation"},
         "plain": out["plain"], "surrogate": out["surrogate"],
         "speedup": out["plain"]["ms_per_step"] / out["surrogate"]["ms_per_step"],
         "flow_difference_px_after_timed_frames": {"mean": float(d.mean()), "max": float(d.max())},
+        "epe_gap_vs_plain_px": out["surrogate"]["epe_vs_truth_px"] - out["plain"]["epe_vs_truth_px"],
         "tensor_tflops_in_surrogate": surrogate_flops_per_px() * px / (surr_ms / 1e3) / 1e12 if surr_ms else None,
         "verdict": ("the surrogate-plus-batched form is faster than the plain GPU form"
                     if out["plain"]["ms_per_step"] > out["surrogate"]["ms_per_step"]
                     else "the surrogate-plus-batched form is slower than the plain GPU form"),
     }
+    held = (seq512, s2_test.cpu().numpy(), p_test.cpu().numpy(), t2_test.cpu().numpy())
+    return line, held
+
+
+def surrogate_vs_oracle(held):
+    """CPU leg: the held-out top-level states propagated by the FP64 oracle
+    (N = 4), against the surrogate's prediction and the plain GPU
+    propagation of the same states: mean and max end-point difference in
+    px/frame (3-D, w / dmu)."""
+    import oracle
+    seq, s0, pred, plain = held
+    L = seq.levels
+    sc = 2.0 ** (L - 1)
+    Hh, Wh = s0.shape[1:3]
+    eta, B, dmu = oracle.geometry(Hh, Wh, seq.fx / sc, seq.fy / sc, seq.cx / sc, seq.cy / sc)
+    e_s, e_p = [], []
+    for k in range(s0.shape[0]):
+        w, _, _, _, _ = oracle.propagate(s0[k, ..., :3], s0[k, ..., 3], eta, B, dmu, SURR_N)
+        e_s.append(np.linalg.norm(pred[k, ..., :3] - w, axis=-1) / dmu)
+        e_p.append(np.linalg.norm(plain[k, ..., :3] - w, axis=-1) / dmu)
+    e_s, e_p = np.array(e_s), np.array(e_p)
+    return {"surrogate_epe_vs_oracle_px": {"mean": float(e_s.mean()), "max": float(e_s.max())},
+            "plain_gpu_epe_vs_oracle_px": {"mean": float(e_p.mean()), "max": float(e_p.max())},
+            "states": f"{s0.shape[0]} held-out scene512 top-level states, one frame (N={SURR_N})"}
 
 
 PAPER_HZ_1024 = 172.149   # the paper's rate at 1024x1024, 2 levels, max flow 8 px (same table, GTX-780)
@@ -1265,8 +1317,9 @@ def run_surrogate_line(args):
     torch.cuda.set_device(local)
     sfbuild.build()
     dev = torch.device("cuda", local)
+    seq = make_sequence(1001, SEQ_FRAMES)
     sampler = ClockSampler(local)
-    r = measure_surrogate(args.steps, dev)
+    r, _ = measure_surrogate(args.steps, dev, seq)
     clocks = sampler.stop()
     line = {"metric": METRIC, "value": r["surrogate"]["frames_per_s_per_stream"],
             "unit": "frames/s per stream (16 streams, surrogate)", "n_gpus": 1, "steps": args.steps,

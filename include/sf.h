@@ -505,9 +505,32 @@ int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, cons
  * surrogate instead of the plain propagation (NULL restores the plain one).
  * The lower levels keep the plain propagation.  The surrogate's buffers are
  * sized here; it serves one filter or batch at a time and must outlive the
- * attachment.  Steady-state batch steps re-capture their graphs. */
+ * attachment.  Steady-state batch steps re-capture their graphs.
+ * Every frame then checks each stream's prediction on the device, with no
+ * host decision (so the frame stays one captured graph): one plain
+ * sub-iteration (N = 1) of the top level, the largest flow difference to the
+ * surrogate's prediction over the stream's pixels (px/frame), and the plain
+ * propagation of the Sec. 4.6 scheme with the level's N sub-iterations
+ * replacing the prediction of every stream whose difference exceeds its
+ * threshold (default 1 px/frame) or is NaN. */
 int sf_set_surrogate(sf_ctx* c, sf_surrogate* s);
 int sf_batch_set_surrogate(sf_batch* b, sf_surrogate* s);
+
+/* Threshold (px/frame, >= 0; +inf: never fall back) of the surrogate's
+ * fallback: for a filter, or for batch stream s (s = -1: every stream, and
+ * the default of later attachments).  Synchronous copy to the device; takes
+ * effect from the next frame, captured graphs included.  SF_EINVAL for a
+ * negative or NaN threshold, a bad s, or s >= 0 before any attachment. */
+int sf_set_surrogate_threshold(sf_ctx* c, float threshold_px);
+int sf_batch_set_surrogate_threshold(sf_batch* b, int s, float threshold_px);
+
+/* Waits for the device, then returns per stream (the first n of a batch; a
+ * filter has one) the last frame's largest difference between the
+ * surrogate's prediction and one plain step (px/frame) and the number of
+ * frames whose prediction fell back to the plain propagation since the
+ * attachment.  Either output may be NULL.  SF_EINVAL before any attachment. */
+int sf_surrogate_stats(sf_ctx* c, float* residual_px, int* fallbacks);
+int sf_batch_surrogate_stats(sf_batch* b, float* residual_px, int* fallbacks, int n);
 
 #ifdef __cplusplus
 }

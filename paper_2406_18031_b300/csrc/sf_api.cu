@@ -367,13 +367,26 @@ struct Engine {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     float graph_dt[2] = {0.0f, 0.0f};
     int steps_plain = 0;
+    // the surrogate's fallback (engine_surr_plans): one plain step of every
+    // top level, the residual of the surrogate's prediction against it, and
+    // the plain propagation gated per stream by residual > threshold
+    float surr_thr_default = 1.0f;   // px/frame, for streams attached later
+    void* surr_block = nullptr;
+    float4* surr_one = nullptr;      // one plain step (N = 1) of every stream's top level
+    unsigned* surr_res = nullptr;    // per stream: the frame's residual (float bits), zeroed every frame
+    float* surr_thr = nullptr;       // per stream: threshold (px/frame)
+    unsigned* surr_cnt = nullptr;    // per stream: frames whose prediction fell back to the plain propagation
+    Plan surr_one_plan;
+    Plan surr_res_plan;
+    std::vector<Plan> surr_fb;       // gated plain propagation of the top levels (one per segment)
 
     int launches_per_step() const
     {
         int n = (int)prop.size() + 1;
         for (auto& p : smooth) n += p.nwork ? 1 : 0;
         for (auto& p : recon) n += p.nwork ? 1 : 0;
-        if (surr) n += 6 * (int)st.size();   // features, four layers, head per stream
+        if (surr) n += 6 * (int)st.size() + 2 + (int)surr_fb.size();   // per stream: features, four layers, head;
+                                                                        // one plain step, residual, fallback
         return n;
     }
 };
@@ -397,10 +410,20 @@ void engine_solve_tile(Engine& E, int param)
     E.solve_auto = (E.flags & SF_AUTOTUNE) != 0;
 }
 
+void engine_surr_free(Engine& E)
+{
+    free_plan(E.surr_one_plan);
+    free_plan(E.surr_res_plan);
+    for (auto& pl : E.surr_fb) free_plan(pl);
+    E.surr_fb.clear();
+}
+
 void engine_free(Engine& E)
 {
     for (int q = 0; q < 2; ++q)
         if (E.graph[q]) cudaGraphExecDestroy(E.graph[q]);
+    engine_surr_free(E);
+    cudaFree(E.surr_block);
     for (auto& pl : E.prop) free_plan(pl);
     free_plan(E.solve);
     for (auto& pl : E.smooth) free_plan(pl);
@@ -432,6 +455,124 @@ int engine_levels(EngineStream& s, cudaStream_t st)
         float4* b = (float4*)lv.block;
         lv.s0[0] = b; lv.s1[0] = b + n; lv.s0[1] = b + 2 * n; lv.s1[1] = b + 3 * n;
         lv.p0 = b + 4 * n; lv.p1 = b + 5 * n; lv.t0 = b + 6 * n; lv.t1 = b + 7 * n;
+    }
+    return SF_OK;
+}
+
+// The surrogate's fallback plans (nothing without a surrogate): every
+// stream's top level once more with one plain sub-iteration (N = 1) into
+// surr_one; the residual launch; and the plain propagation of the top levels
+// in segments of at most nf_max sub-iterations (as the plain engine splits
+// them), each job gated by its stream's residual word and threshold.  The
+// state is already rescaled for a frame-time change when these run
+// (engine_launches scales it in place for the surrogate), so no job rescales.
+int engine_surr_plans(Engine& E, cudaStream_t st)
+{
+    engine_surr_free(E);
+    if (!E.surr) return SF_OK;
+    const int n = (int)E.st.size();
+    size_t top_px = 0;
+    for (auto& s : E.st) top_px += (size_t)s.lv[s.L - 1].grid.H * s.lv[s.L - 1].grid.W;
+    if (!E.surr_block) {
+        const size_t bytes = top_px * sizeof(float4) + 3 * ((n * sizeof(unsigned) + 255) & ~(size_t)255);
+        if (cudaMalloc(&E.surr_block, bytes) != cudaSuccess) { E.surr_block = nullptr; return SF_ENOMEM; }
+        unsigned char* p = (unsigned char*)E.surr_block;
+        E.surr_one = (float4*)p;
+        p += top_px * sizeof(float4);
+        const size_t wb = (n * sizeof(unsigned) + 255) & ~(size_t)255;
+        E.surr_res = (unsigned*)p;
+        E.surr_thr = (float*)(p + wb);
+        E.surr_cnt = (unsigned*)(p + 2 * wb);
+        std::vector<float> thr(n, E.surr_thr_default);
+        if (cudaMemsetAsync(E.surr_res, 0, 3 * wb, st) != cudaSuccess) return SF_ECUDA;
+        if (cudaMemcpyAsync(E.surr_thr, thr.data(), n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SF_ECUDA;
+    }
+    // one plain sub-iteration of every top level
+    {
+        std::vector<PropJob> jobs;
+        std::vector<int4> work;
+        size_t off = 0;
+        for (auto& s : E.st) {
+            sf_level_state& lv = s.lv[s.L - 1];
+            PropJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.g = make_grid(lv.grid);
+            j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+            j.out0 = E.surr_one + off;
+            j.nf = 1;
+            j.dt = 1.0f;
+            j.tiles_x = ceil_div(lv.grid.W, prop_tile(1));
+            j.motion = s.motion;
+            jobs.push_back(j);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(1), prop_tile(1));
+            off += (size_t)lv.grid.H * lv.grid.W;
+        }
+        E.surr_one_plan.nf = 1;
+        E.surr_one_plan.smem = prop_smem_bytes();
+        int r = upload_plan(jobs, work, E.surr_one_plan, st);
+        if (r) return r;
+    }
+    // the residual of the surrogate's prediction (p0) against that step
+    {
+        std::vector<SurrResJob> jobs;
+        std::vector<int4> work;
+        size_t off = 0;
+        for (int k = 0; k < n; ++k) {
+            sf_level_state& lv = E.st[k].lv[E.st[k].L - 1];
+            SurrResJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.g = make_grid(lv.grid);
+            j.a = lv.p0;
+            j.b = E.surr_one + off;
+            j.res = E.surr_res + k;
+            jobs.push_back(j);
+            const int px = lv.grid.H * lv.grid.W;
+            for (int c = 0; c < px; c += kResChunk) work.push_back(make_int4((int)jobs.size() - 1, c, 0, 0));
+            off += (size_t)px;
+        }
+        int r = upload_plan(jobs, work, E.surr_res_plan, st);
+        if (r) return r;
+    }
+    // the gated plain propagation of the top levels
+    int maxseg = 0;
+    for (auto& s : E.st) maxseg = std::max(maxseg, ceil_div(s.lv[s.L - 1].N, E.nf_max));
+    E.surr_fb.resize(maxseg);
+    for (int k = 0; k < maxseg; ++k) {
+        std::vector<PropJob> jobs;
+        std::vector<int4> work;
+        int nfl = 0;
+        for (int si = 0; si < n; ++si) {
+            EngineStream& s = E.st[si];
+            sf_level_state& lv = s.lv[s.L - 1];
+            const int nseg = ceil_div(lv.N, E.nf_max);
+            if (k >= nseg) continue;
+            const int nf = lv.N / nseg + (k < lv.N % nseg ? 1 : 0);
+            auto out_of = [&](int seg) { return ((nseg - 1 - seg) % 2) == 0 ? lv.p0 : lv.t0; };
+            PropJob j;
+            std::memset(&j, 0, sizeof(j));
+            j.g = make_grid(lv.grid);
+            if (k == 0) {
+                j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+            } else {
+                j.in0[0] = j.in0[1] = out_of(k - 1);
+            }
+            j.out0 = out_of(k);
+            j.nf = nf;
+            j.dt = 1.0f / (float)lv.N;
+            j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
+            j.motion = s.motion;
+            j.gate = E.surr_res + si;
+            j.gate_thr = E.surr_thr + si;
+            j.gate_count = k == 0 ? E.surr_cnt + si : nullptr;
+            jobs.push_back(j);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
+            nfl = std::max(nfl, nf);
+        }
+        E.surr_fb[k].nf = nfl;
+        E.surr_fb[k].smem = prop_smem_bytes();
+        int r = upload_plan(jobs, work, E.surr_fb[k], st);
+        if (r) return r;
     }
     return SF_OK;
 }
@@ -500,7 +641,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
         int r = upload_plan(jobs, work, E.prop[k], st);
         if (r) return r;
     }
-    return SF_OK;
+    return engine_surr_plans(E, st);
 }
 
 int engine_smooth_plans(Engine& E, cudaStream_t st);
@@ -838,8 +979,24 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
                 if (r) return r;
             }
         }
+        if (E.surr) {
+            // the fallback: residual against one plain step, then the plain
+            // propagation of every stream whose residual exceeds its threshold
+            // (CTAs of the other streams return at once); no host decision
+            ProfScope ps(E.prof, slot++, st);
+            if (cudaMemsetAsync(E.surr_res, 0, E.st.size() * sizeof(unsigned), st) != cudaSuccess) return SF_ECUDA;
+            r = launch_propagate(E.surr_one_plan, E.parity, 1.0f, E.flags & ~SF_CHECK_CFL, nullptr, st, dt);
+            if (r) return r;
+            k_surr_residual<<<E.surr_res_plan.nwork, 256, 0, st>>>((const SurrResJob*)E.surr_res_plan.jobs,
+                                                                     E.surr_res_plan.work);
+            if (last_error()) return SF_ECUDA;
+            for (auto& pl : E.surr_fb) {
+                r = launch_propagate(pl, E.parity, 1.0f, E.flags, E.status, st, dt);
+                if (r) return r;
+            }
+        }
     } else {
-        slot = (int)E.prop.size() + (E.surr ? 1 : 0);
+        slot = (int)E.prop.size() + (E.surr ? 2 : 0);
     }
     if (inputs && cudaStreamWaitEvent(st, inputs, 0) != cudaSuccess) return SF_ECUDA;
     return engine_update_launches(E, a, dt, flow, inv, slot, st);
@@ -2003,6 +2160,63 @@ int sf_batch_set_surrogate(sf_batch* b, sf_surrogate* s)
 {
     if (!b) return SF_EINVAL;
     return engine_attach(b->E, s);
+}
+
+namespace {
+
+// threshold of stream s (-1: every stream, and streams attached later)
+int engine_surr_threshold(Engine& E, int s, float thr)
+{
+    if (!(thr >= 0.0f)) return SF_EINVAL;   // NaN or negative; +inf: never fall back
+    const int n = (int)E.st.size();
+    if (s < -1 || s >= n) return SF_EINVAL;
+    if (s == -1) E.surr_thr_default = thr;
+    if (!E.surr_thr) return s == -1 ? SF_OK : SF_EINVAL;   // no surrogate attached yet
+    std::vector<float> v(s == -1 ? n : 1, thr);
+    return cudaMemcpy(E.surr_thr + (s == -1 ? 0 : s), v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice) ==
+                   cudaSuccess ? SF_OK : SF_ECUDA;
+}
+
+int engine_surr_stats(Engine& E, float* residual_px, int* fallbacks, int n)
+{
+    if (n < 1 || n > (int)E.st.size() || (!residual_px && !fallbacks)) return SF_EINVAL;
+    if (!E.surr_res) return SF_EINVAL;                     // never attached
+    if (cudaDeviceSynchronize() != cudaSuccess) return SF_ECUDA;
+    std::vector<unsigned> r(n), c(n);
+    if (cudaMemcpy(r.data(), E.surr_res, n * sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(c.data(), E.surr_cnt, n * sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SF_ECUDA;
+    for (int k = 0; k < n; ++k) {
+        if (residual_px) std::memcpy(residual_px + k, &r[k], sizeof(float));
+        if (fallbacks) fallbacks[k] = (int)c[k];
+    }
+    return SF_OK;
+}
+
+}  // namespace
+
+int sf_set_surrogate_threshold(sf_ctx* c, float threshold_px)
+{
+    if (!c) return SF_EINVAL;
+    return engine_surr_threshold(c->E, -1, threshold_px);
+}
+
+int sf_batch_set_surrogate_threshold(sf_batch* b, int s, float threshold_px)
+{
+    if (!b) return SF_EINVAL;
+    return engine_surr_threshold(b->E, s, threshold_px);
+}
+
+int sf_surrogate_stats(sf_ctx* c, float* residual_px, int* fallbacks)
+{
+    if (!c) return SF_EINVAL;
+    return engine_surr_stats(c->E, residual_px, fallbacks, 1);
+}
+
+int sf_batch_surrogate_stats(sf_batch* b, float* residual_px, int* fallbacks, int n)
+{
+    if (!b) return SF_EINVAL;
+    return engine_surr_stats(b->E, residual_px, fallbacks, n);
 }
 
 int sf_surrogate_grads(sf_surrogate* s, float* host)

@@ -44,6 +44,12 @@ struct PropJob {
     float dt;               // 1 / N of the whole frame
     int tiles_x;
     const float* motion;    // inertial source terms: Omega (3), a (3); frame units after x mscale, x mscale^2
+    // fallback gate (null: always run): the job runs only when the float in
+    // *gate (a residual written by an earlier kernel of the frame) exceeds
+    // *gate_thr or is NaN; *gate_count (may be null) counts the frames it ran
+    const unsigned* gate;
+    const float* gate_thr;
+    unsigned* gate_count;
 };
 
 // Register-resident tiles: a CTA of kPrWarps warps holds a kPrW x kPrH region
@@ -233,6 +239,11 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
         }
     }
     pdl_wait();
+    if (J.gate) {   // a fallback job: skip the whole tile unless the residual exceeds the threshold
+        const float res = __uint_as_float(*(volatile const unsigned*)J.gate);
+        if (res <= *J.gate_thr) return;   // CTA-uniform: no barrier has been reached yet
+        if (J.gate_count && wk.y == 0 && wk.z == 0 && threadIdx.x == 0) atomicAdd(J.gate_count, 1u);
+    }
     // Omega and a in frame units, in shared memory: read where used rather than
     // held in six registers across the passes (visible after the first barrier,
     // which precedes the first inertial step)

@@ -212,6 +212,37 @@ __global__ void k_surr_maxdiff(Grid g, int n, const float4* __restrict__ a, cons
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
+// The residual of every attached stream's top-level prediction against one
+// plain step: per job (a stream) the largest |a - b| of the flow over its
+// pixels in px/frame (w / dmu), atomicMax-ed into *res as the bit pattern of
+// a non-negative float (NaN counts as the largest).  Work item = (job, first
+// pixel of a chunk of kResChunk pixels).
+struct SurrResJob {
+    Grid g;
+    const float4* a;
+    const float4* b;
+    unsigned* res;
+};
+constexpr int kResChunk = 4096;
+
+__global__ void k_surr_residual(const SurrResJob* __restrict__ jobs, const int4* __restrict__ work)
+{
+    const int4 wk = work[blockIdx.x];
+    const SurrResJob& J = jobs[wk.x];
+    const int n = J.g.H * J.g.W;
+    const int end = min(n, wk.y + kResChunk);
+    float m = 0.0f;
+    for (int p = wk.y + threadIdx.x; p < end; p += blockDim.x) {
+        const int i = p / J.g.W, j = p - i * J.g.W;
+        const float inv = 1.0f / pixel_dmu(pixel_geometry(J.g, i, j));
+        const float4 u = J.a[p], v = J.b[p];
+        const float d = fmaxf(fabsf(u.x - v.x), fmaxf(fabsf(u.y - v.y), fabsf(u.z - v.z))) * inv;
+        m = fmaxf(m, d == d ? d : 3.0e38f);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(J.res, __float_as_uint(m));
+}
+
 // BF16 copies of FP32 weights (after a set or at creation)
 __global__ void k_weights_bf16(int Cin, int Cout, const float* __restrict__ w, __nv_bfloat16* __restrict__ w16,
                                __nv_bfloat16* __restrict__ w16t)

@@ -50,7 +50,8 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_conv3x3_wgrad", "sf_selftest_conv_timeout", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
            "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
-           "sf_batch_set_surrogate"]
+           "sf_batch_set_surrogate", "sf_set_surrogate_threshold", "sf_batch_set_surrogate_threshold",
+           "sf_surrogate_stats", "sf_batch_surrogate_stats"]
 
 
 def lib():
@@ -100,6 +101,10 @@ def lib():
         L.sf_surrogate_propagate.argtypes = [vp, P(CGrid), i, i, vp, vp, f, P(f), P(i), vp]
         L.sf_set_surrogate.argtypes = [vp, vp]
         L.sf_batch_set_surrogate.argtypes = [vp, vp]
+        L.sf_set_surrogate_threshold.argtypes = [vp, f]
+        L.sf_batch_set_surrogate_threshold.argtypes = [vp, i, f]
+        L.sf_surrogate_stats.argtypes = [vp, P(f), P(i)]
+        L.sf_batch_surrogate_stats.argtypes = [vp, P(f), P(i), i]
         L.sf_remap_equirect.argtypes = [P(CGrid), P(f), i, i, vp, vp, vp, vp, vp]
         L.sf_batch_motion.argtypes = [vp, i, P(vp)]
         L.sf_batch_create.argtypes = [i, P(i), P(i), P(i), P(CParams), P(vp)]
@@ -283,6 +288,16 @@ class Filter:
         """Predict the top level with a trained Surrogate (None: the plain propagation)."""
         _check(lib().sf_set_surrogate(self._h, None if net is None else net._h), "sf_set_surrogate")
         self._surrogate = net     # kept alive while attached
+
+    def set_surrogate_threshold(self, threshold_px):
+        """Fallback threshold of the attached surrogate (px/frame; inf: never)."""
+        _check(lib().sf_set_surrogate_threshold(self._h, ctypes.c_float(threshold_px)), "sf_set_surrogate_threshold")
+
+    def surrogate_stats(self):
+        """(last frame's residual against one plain step in px/frame, frames that fell back)."""
+        r, c = ctypes.c_float(), ctypes.c_int()
+        _check(lib().sf_surrogate_stats(self._h, ctypes.byref(r), ctypes.byref(c)), "sf_surrogate_stats")
+        return r.value, c.value
 
     def set_motion(self, omega=None, accel=None, stream=None):
         """Angular velocity (rad/s) and linear acceleration (m/s^2) for IMU steps."""
@@ -527,6 +542,18 @@ class Batch:
     def set_surrogate(self, net):
         _check(lib().sf_batch_set_surrogate(self._h, None if net is None else net._h), "sf_batch_set_surrogate")
         self._surrogate = net
+
+    def set_surrogate_threshold(self, threshold_px, stream=-1):
+        """Fallback threshold (px/frame; inf: never) of batch stream `stream` (-1: all)."""
+        _check(lib().sf_batch_set_surrogate_threshold(self._h, int(stream), ctypes.c_float(threshold_px)),
+               "sf_batch_set_surrogate_threshold")
+
+    def surrogate_stats(self):
+        """Per stream: (last frame's residual in px/frame, frames that fell back) as numpy arrays."""
+        n = len(self.shapes)
+        r, c = (ctypes.c_float * n)(), (ctypes.c_int * n)()
+        _check(lib().sf_batch_surrogate_stats(self._h, r, c, n), "sf_batch_surrogate_stats")
+        return np.array(r[:], dtype=np.float64), np.array(c[:], dtype=np.int64)
 
     def status(self):
         code = lib().sf_batch_status(self._h)

@@ -32,9 +32,9 @@ def _pair(seq, gamma=None, flags=0, gpu_flags=0, nf_max=None, update_mode=None, 
 
 
 def _run(seq, frames, dts=None, flags=0, check_every=True, tol=gu.FLOW_TOL_PX, gpu_flags=0, nf_max=None,
-         filt=None, update_mode=None, solve_tile=None):
+         filt=None, update_mode=None, solve_tile=None, gamma=None):
     """Run both filters; returns per-frame (max px error, max rho error) and the final outputs."""
-    g, r = _pair(seq, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max, update_mode=update_mode,
+    g, r = _pair(seq, gamma=gamma, flags=flags, gpu_flags=gpu_flags, nf_max=nf_max, update_mode=update_mode,
                  solve_tile=solve_tile)
     if filt is not None:
         filt.append(g)
@@ -204,9 +204,15 @@ def test_hundred_frame_drift_full_size(case):
     # the contract's 1e-3 relative after 100 frames on the benchmark's
     # workload (512x512, 2 levels, N = [8, 4], S = [2, 4], 8 px/frame) and on
     # the driving workload (384x1248, 3 levels, N = [32, 16, 8], S = [2, 4, 4]),
-    # both at full size, 100 consecutive frames of their sequences
+    # both at full size, 100 consecutive frames of their sequences.  On the
+    # driving sequence the default prior weight (gamma3 = 1e-2) lets the flow
+    # grow without bound near frame 45 in the FP64 oracle and the GPU filter
+    # alike (both reach inf/NaN); the drift there is compared with gamma3 = 1,
+    # under which the filter stays bounded for the 100 frames.
     seq = scenes.scene512(frames=100) if case == "scene512" else scenes.drive(frames=100)
-    errs, (gf, gi), (rf, ri), st = _run(seq, 100, check_every=False)
+    gamma = None if case == "scene512" else (1.0, 1.0, 1.0, 1.0, 1.0)
+    errs, (gf, gi), (rf, ri), st = _run(seq, 100, check_every=False, gamma=gamma)
+    assert np.isfinite(rf).all() and np.isfinite(gf).all()
     assert gu.rel_l2(gf, rf) <= gu.DRIFT_TOL, gu.rel_l2(gf, rf)
     assert gu.rel_l2(gi, ri) <= gu.DRIFT_TOL, gu.rel_l2(gi, ri)
     assert st >= 0

@@ -150,6 +150,7 @@ def test_filter_top_level_predicted_by_the_surrogate():
     p = net.params(); p[-16 - 9 * 16 * 32:] *= 10.0; net.set_params(p)
     filt = sf.Filter(H, W, 1, P)
     filt.set_surrogate(net)
+    filt.set_surrogate_threshold(float("inf"))            # the prediction is always accepted here
     img = [torch.from_numpy(seq.image[k]).cuda() for k in range(3)]
     rng_ = [torch.from_numpy(seq.range[k]).cuda() for k in range(3)]
     flow = torch.empty((3, H, W), device="cuda")
@@ -168,7 +169,11 @@ def test_filter_top_level_predicted_by_the_surrogate():
     torch.cuda.synchronize()
     ref = torch.cat([n0.permute(2, 0, 1), n1.permute(2, 0, 1)])
     assert torch.equal(got, ref)
-    assert filt.kernels_per_step() == 6 + 1 + 1      # surrogate, solve, smoothing
+    # surrogate (features, 4 layers, head), the fallback check (one plain
+    # step, residual, gated plain propagation), solve, smoothing
+    assert filt.kernels_per_step() == 6 + 3 + 1 + 1
+    res, fell = filt.surrogate_stats()
+    assert res > 0 and fell == 0
 
 
 def test_batch_with_the_surrogate_matches_single_filters():
@@ -196,3 +201,50 @@ def test_batch_with_the_surrogate_matches_single_filters():
         stream.synchronize()
         for s in range(2):
             assert torch.equal(batch.slots[s][2], outs[s]), (k, s)
+
+
+def test_batch_fallback_inside_the_captured_step():
+    # three single-level streams stepped by three batches through the same
+    # frames: P without a surrogate, S with the surrogate always accepted
+    # (threshold inf) and A with per-stream thresholds: stream 0 always falls
+    # back (threshold 0), stream 1 never (inf), stream 2 on the default
+    # threshold.  From the fourth frame on every step replays a captured
+    # graph, so the decisions are taken on the device.  A's stream 0 must
+    # equal P's bit for bit, its stream 1 S's; stream 2 follows P or S on each
+    # frame as its counter says.
+    from paper_2406_18031_b300 import scenes
+    seqs = [scenes.plane64(frames=8, seed=31 + k, H=64, W=128 + 32 * k, levels=1, iters=[3]) for k in range(3)]
+    net = sf.Surrogate(seed=13)
+    p = net.params(); p[-16 - 9 * 16 * 32:] *= 10.0; net.set_params(p)
+    P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
+    shapes = [q.shape for q in seqs]
+    bp, bs, ba = (sf.Batch(shapes, [1] * 3, P) for _ in range(3))
+    nets = [sf.Surrogate(seed=13) for _ in range(2)]
+    for nn in nets:
+        nn.set_params(p)
+    bs.set_surrogate(nets[0]); bs.set_surrogate_threshold(float("inf"))
+    ba.set_surrogate(nets[1])
+    ba.set_surrogate_threshold(0.0, 0); ba.set_surrogate_threshold(float("inf"), 1)
+    stream = torch.cuda.Stream()
+    dt = seqs[0].dt
+    fell_prev = np.zeros(3, np.int64)
+    for k in range(8):
+        with torch.cuda.stream(stream):
+            for b in (bp, bs, ba):
+                for s_, q in enumerate(seqs):
+                    b.slots[s_][0].copy_(torch.from_numpy(q.image[k]).cuda())
+                    b.slots[s_][1].copy_(torch.from_numpy(q.range[k]).cuda())
+                b.step(dt, stream=stream)
+        stream.synchronize()
+        res, fell = ba.surrogate_stats()
+        assert torch.equal(ba.slots[0][2], bp.slots[0][2]), k
+        assert torch.equal(ba.slots[1][2], bs.slots[1][2]), k
+        if k > 0:
+            assert fell[0] == k and fell[1] == 0
+            assert fell[2] - fell_prev[2] == int(res[2] > 1.0)
+        fell_prev = fell
+    assert fell_prev[0] == 7
+    # the always-accepted batch never ran the fallback
+    assert (bs.surrogate_stats()[1] == 0).all()
+    for b in (bp, bs, ba):
+        b.close()
