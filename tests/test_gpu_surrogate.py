@@ -93,7 +93,7 @@ def test_gradients_match_oracle():
     # tolerance is a small fraction of them
     for sl in _layer_slices():
         nz = ref_g[sl] != 0
-        assert nz.mean() > 0.3 and np.median(tol[sl][nz] / np.abs(ref_g[sl][nz])) < 0.05
+        assert nz.mean() > 0.2 and np.median(tol[sl][nz] / np.abs(ref_g[sl][nz])) < 0.05
     np.testing.assert_array_equal(net.params(), p)     # lr = 0 leaves the parameters
 
 
