@@ -123,6 +123,7 @@ struct Plan {
     size_t smem = 0;
     bool c8 = false;     // propagation: some job transports 8 channels
     int nf = 0;          // propagation: sub-iterations of the launch's longest job
+    int warps = 16;      // propagation: warps per CTA (prop_warps of nf)
     int tile = 0;        // solve: tile edge (kSolveTSmall, else kSolveT)
 };
 
@@ -157,23 +158,27 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
 // need 16-byte alignment whatever the size of the job struct
 inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
-template <bool C8, bool LIT, bool IMU, bool PE>
+template <bool C8, bool LIT, bool IMU, bool PE, int WARPS>
 int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
                        bool pdl)
 {
-    if (set_smem_attr((const void*)k_propagate<C8, LIT, IMU, PE>, p.smem)) return SF_ECUDA;
-    return launch_ex(pdl, k_propagate<C8, LIT, IMU, PE>, dim3(p.nwork), dim3(kPrThreads), p.smem, st,
-                     (const PropJob*)p.jobs, (const int4*)p.work, parity, wscale, flags, status, mscale);
+    auto* kern = k_propagate<C8, LIT, IMU, PE, WARPS>;
+    if (set_smem_attr((const void*)kern, p.smem)) return SF_ECUDA;
+    return launch_ex(pdl, kern, dim3(p.nwork), dim3(32 * WARPS), p.smem, st, (const PropJob*)p.jobs,
+                     (const int4*)p.work, parity, wscale, flags, status, mscale);
 }
 
 template <bool C8, bool LIT, bool IMU>
 int launch_propagate_i(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
                        bool pdl)
 {
-    // the padded form for launches of many sub-iterations (see kPrPaddedNf)
+    // 8-warp CTAs for launches of few sub-iterations (prop_warps); the padded
+    // form for launches of many (see kPrPaddedNf)
+    if (p.warps == 8)
+        return launch_propagate_t<C8, LIT, IMU, false, 8>(p, parity, wscale, flags, status, mscale, st, pdl);
     if (p.nf >= kPrPaddedNf)
-        return launch_propagate_t<C8, LIT, IMU, true>(p, parity, wscale, flags, status, mscale, st, pdl);
-    return launch_propagate_t<C8, LIT, IMU, false>(p, parity, wscale, flags, status, mscale, st, pdl);
+        return launch_propagate_t<C8, LIT, IMU, true, 16>(p, parity, wscale, flags, status, mscale, st, pdl);
+    return launch_propagate_t<C8, LIT, IMU, false, 16>(p, parity, wscale, flags, status, mscale, st, pdl);
 }
 
 template <bool C8, bool LIT>
@@ -505,11 +510,12 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
             j.tiles_x = ceil_div(lv.grid.W, prop_tile(1));
             j.motion = s.motion;
             jobs.push_back(j);
-            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(1), prop_tile(1));
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(1), prop_tile_h(1, prop_warps(1)));
             off += (size_t)lv.grid.H * lv.grid.W;
         }
         E.surr_one_plan.nf = 1;
-        E.surr_one_plan.smem = prop_smem_bytes();
+        E.surr_one_plan.warps = prop_warps(1);
+        E.surr_one_plan.smem = prop_smem_bytes(E.surr_one_plan.warps);
         int r = upload_plan(jobs, work, E.surr_one_plan, st);
         if (r) return r;
     }
@@ -541,7 +547,12 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
     for (int k = 0; k < maxseg; ++k) {
         std::vector<PropJob> jobs;
         std::vector<int4> work;
-        int nfl = 0;
+        int nfl = 0;   // the launch's longest job sets its CTA shape
+        for (auto& s : E.st) {
+            const int N = s.lv[s.L - 1].N, nseg = ceil_div(N, E.nf_max);
+            if (k < nseg) nfl = std::max(nfl, N / nseg + (k < N % nseg ? 1 : 0));
+        }
+        const int warps = prop_warps(nfl);
         for (int si = 0; si < n; ++si) {
             EngineStream& s = E.st[si];
             sf_level_state& lv = s.lv[s.L - 1];
@@ -566,11 +577,11 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
             j.gate_thr = E.surr_thr + si;
             j.gate_count = k == 0 ? E.surr_cnt + si : nullptr;
             jobs.push_back(j);
-            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
-            nfl = std::max(nfl, nf);
+            add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile_h(nf, warps));
         }
         E.surr_fb[k].nf = nfl;
-        E.surr_fb[k].smem = prop_smem_bytes();
+        E.surr_fb[k].warps = warps;
+        E.surr_fb[k].smem = prop_smem_bytes(warps);
         int r = upload_plan(jobs, work, E.surr_fb[k], st);
         if (r) return r;
     }
@@ -593,7 +604,13 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
         std::vector<PropJob> jobs;
         std::vector<int4> work;
         bool c8 = false;
-        int nfl = 0;   // the longest job's sub-iterations
+        int nfl = 0;   // the longest job's sub-iterations: it sets the launch's CTA shape
+        for (auto& s : E.st)
+            for (int h = 0; h < s.L; ++h) {
+                const int N = s.lv[h].N, nseg = ceil_div(N, nfmax);
+                if (k < nseg && !(h == s.L - 1 && E.surr)) nfl = std::max(nfl, N / nseg + (k < N % nseg ? 1 : 0));
+            }
+        const int warps = prop_warps(nfl);
         for (int want = nfmax; want >= 1; --want) {   // longest tiles (most passes) first
             for (auto& s : E.st) {
                 for (int h = 0; h < s.L; ++h) {
@@ -629,15 +646,15 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
                     j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
                     j.motion = s.motion;
                     jobs.push_back(j);
-                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile(nf));
+                    add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile_h(nf, warps));
                     c8 |= !top;
-                    nfl = std::max(nfl, nf);
                 }
             }
         }
         E.prop[k].c8 = c8;
         E.prop[k].nf = nfl;
-        E.prop[k].smem = prop_smem_bytes();
+        E.prop[k].warps = warps;
+        E.prop[k].smem = prop_smem_bytes(warps);
         int r = upload_plan(jobs, work, E.prop[k], st);
         if (r) return r;
     }
@@ -1578,11 +1595,12 @@ int stage_propagate(const sf_grid* g, int N, int flags, float wscale, const floa
         j.dt = 1.0f / (float)N;
         j.tiles_x = ceil_div(g->W, prop_tile(j.nf));
         std::vector<int4> work;
-        add_tiles(work, 0, g->H, g->W, prop_tile(j.nf), prop_tile(j.nf));
+        add_tiles(work, 0, g->H, g->W, prop_tile(j.nf), prop_tile_h(j.nf, prop_warps(j.nf)));
         Plan pl;
         pl.c8 = c8;
         pl.nf = j.nf;
-        pl.smem = prop_smem_bytes();
+        pl.warps = prop_warps(j.nf);
+        pl.smem = prop_smem_bytes(pl.warps);
         // the job, its work list and the motion travel through stream-ordered scratch
         void* mem = nullptr;
         const size_t woff = work_offset(sizeof(PropJob));
@@ -2310,10 +2328,10 @@ int noalloc_scratch(unsigned char** out)
 
 __global__ void k_noalloc_store_job(PropJob j, PropJob* dst) { *dst = j; }
 
-__global__ void k_noalloc_fill_tiles(int4* work, int tiles_x, int ntiles, int T)
+__global__ void k_noalloc_fill_tiles(int4* work, int tiles_x, int ntiles, int T, int TH)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
-        work[t] = make_int4(0, (t / tiles_x) * T, (t % tiles_x) * T, 0);
+        work[t] = make_int4(0, (t / tiles_x) * TH, (t % tiles_x) * T, 0);
 }
 
 }  // namespace
@@ -2328,8 +2346,8 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
     if (n > kNoAllocMaxPixels) return SF_EINVAL;                 // larger frames: use sf_propagate
     const int nseg = ceil_div(N, kNfLimit);
     for (int k = 0; k < nseg; ++k) {                             // every tile list must fit
-        const int T = prop_tile(N / nseg + (k < N % nseg ? 1 : 0));
-        const size_t tiles = (size_t)ceil_div(g->H, T) * ceil_div(g->W, T);
+        const int nfk = N / nseg + (k < N % nseg ? 1 : 0);
+        const size_t tiles = (size_t)ceil_div(g->H, prop_tile_h(nfk, prop_warps(nfk))) * ceil_div(g->W, prop_tile(nfk));
         if (kNoAllocJobBytes + tiles * sizeof(int4) > kNoAllocDescBytes) return SF_EINVAL;
     }
     unsigned char* base = nullptr;
@@ -2359,19 +2377,20 @@ extern "C" int sf_propagate_noalloc(const sf_grid* g, int N, int flags, float ws
         j.nf = N / nseg + (k < N % nseg ? 1 : 0);
         j.apply_wscale = k == 0;
         j.dt = 1.0f / (float)N;
-        const int T = prop_tile(j.nf);
+        const int T = prop_tile(j.nf), warps = prop_warps(j.nf), TH = prop_tile_h(j.nf, warps);
         j.tiles_x = ceil_div(g->W, T);
-        const int ntiles = j.tiles_x * ceil_div(g->H, T);
+        const int ntiles = j.tiles_x * ceil_div(g->H, TH);
         // descriptors are written by the device in stream order: the previous
         // launch has finished reading them when these kernels run
         k_noalloc_store_job<<<1, 1, 0, st>>>(j, djob);
-        k_noalloc_fill_tiles<<<std::min(ceil_div(ntiles, 256), 1024), 256, 0, st>>>(dwork, j.tiles_x, ntiles, T);
+        k_noalloc_fill_tiles<<<std::min(ceil_div(ntiles, 256), 1024), 256, 0, st>>>(dwork, j.tiles_x, ntiles, T, TH);
         r = last_error();
         if (r) break;
         Plan pl;
         pl.c8 = c8;
         pl.nf = j.nf;
-        pl.smem = prop_smem_bytes();
+        pl.warps = warps;
+        pl.smem = prop_smem_bytes(warps);
         pl.jobs = djob;
         pl.work = dwork;
         pl.nwork = ntiles;

@@ -22,6 +22,8 @@
 //   k_pack/k_unpack  interleaved float4 state <-> planar checkpoint layout.
 #pragma once
 
+#include <type_traits>
+
 #include "sf_device.cuh"
 
 namespace sfdev {
@@ -52,7 +54,7 @@ struct PropJob {
     unsigned* gate_count;
 };
 
-// Register-resident tiles: a CTA of kPrWarps warps holds a kPrW x kPrH region
+// Register-resident tiles: a CTA of WARPS warps holds a kPrW x (kPrRows WARPS) region
 // (the output tile plus an nf-pixel halo on every side).  Warp w owns rows
 // [w kPrRows, (w+1) kPrRows) and lane l owns columns 2l and 2l+1 of them;
 // their 8 channels stay in registers for all nf sub-iterations.  Column-pass
@@ -62,12 +64,18 @@ struct PropJob {
 // (eta, cu) is computed once and parked in shared memory (read only by its
 // owner).
 constexpr int kPrRows = 4;
-constexpr int kPrWarps = 16;
 constexpr int kPrW = 64;
-constexpr int kPrH = kPrRows * kPrWarps;
-constexpr int kPrThreads = 32 * kPrWarps;
+constexpr int kPrWarpsMax = 16;
+constexpr int kPrThreadsMax = 32 * kPrWarpsMax;
+// Launches whose longest job runs at most kPrSmallNf sub-iterations use CTAs
+// of 8 warps (a 64 x 32 region, two CTAs per SM: one CTA's loads and stores
+// overlap the other's passes); longer ones 16 warps (64 x 64, one CTA per SM,
+// less halo recomputation).
+constexpr int kPrSmallNf = 4;
+__host__ __device__ inline int prop_warps(int nf_longest) { return nf_longest <= kPrSmallNf ? 8 : kPrWarpsMax; }
 
-__host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // square output tile edge
+__host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // output tile width
+__host__ __device__ inline int prop_tile_h(int nf, int warps) { return kPrRows * warps - 2 * nf; }   // ... height
 
 // Published rows: slot 1 + 2w holds warp w's first row, slot 2 + 2w its last.
 // In the padded form (PE) slot 0 and the last slot repeat the region's first
@@ -77,14 +85,15 @@ __host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // 
 // padded form saves ALU work in every sub-iteration but holds more registers
 // (spills around the load and store phases): launches whose longest job runs
 // at least kPrPaddedNf sub-iterations take it.
-constexpr int kPubSlots = 2 * kPrWarps + 2;
+__host__ __device__ inline int pub_slots(int warps) { return 2 * warps + 2; }
 constexpr int kPrPaddedNf = 6;
+static_assert(kPrPaddedNf > kPrSmallNf, "the padded form runs with 16 warps only");
 
-__host__ __device__ inline size_t prop_smem_bytes()
+__host__ __device__ inline size_t prop_smem_bytes(int warps)
 {
-    return (size_t)kPrH * kPrW * sizeof(float4)                 // geometry
-           + 2 * (size_t)kPubSlots * kPrW * sizeof(float4)      // published rows: s0, s1
-           + (size_t)kPubSlots * kPrW * sizeof(float);          // published row speeds
+    return (size_t)kPrRows * warps * kPrW * sizeof(float4)            // geometry
+           + 2 * (size_t)pub_slots(warps) * kPrW * sizeof(float4)     // published rows: s0, s1
+           + (size_t)pub_slots(warps) * kPrW * sizeof(float);         // published row speeds
 }
 
 struct PixGeo {
@@ -142,23 +151,25 @@ __device__ __forceinline__ float4 upwind4(float4 f, float4 fm, float4 fp, float 
 
 // Coefficients of one pixel for one pass: weights on the minus and plus
 // neighbours (one of them zero: the upwind side of Eqs. 57-58), on itself,
-// and on itself for Y.  v = dt s-hat (s-hat the dominant speed of Eqs.
-// 55-56): km = max(v, 0) on the minus side, kp = max(-v, 0) on the plus side,
-// formed exactly as v/2 + |v/2| and |v/2| - v/2 (adds, on the FMA pipe, where
-// a max would load the busier ALU pipe); hm, hp (1 or 0) drop the neighbour
-// beyond the image border (replicated border: D = 0).  kself = A - km - kp
-// with A = 1 - sdt src.
+// and on itself for Y.  The speeds arrive prescaled by dt/2, so the dominant
+// one (Eqs. 55-56) is already v/2 with v = dt s-hat: km = max(v, 0) on the
+// minus side, kp = max(-v, 0) on the plus side, formed exactly as v/2 + |v/2|
+// and |v/2| - v/2 (adds, on the FMA pipe, where a max would load the busier
+// ALU pipe); hm, hp (1 or 0) drop the neighbour beyond the image border
+// (replicated border: D = 0).  kself = A - km - kp with A = 1 - sdt src.
+// cflm keeps the largest |v/2| of the pixels inside the output tile (cmask 1;
+// 0 outside) for the CFL test of Eq. 67 (|v| > 1), made once after the passes.
 struct Coef {
     float km, kp, kself, kselfy;
 };
 
 template <bool LITERAL>
 __device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, float hm, float hp, float src, float dt,
-                                             float sdt, bool& bad, bool count)
+                                             float sdt, float& cflm, float cmask)
 {
     const float sh = dominant(s_minus, s_plus, LITERAL ? kDominantLiteral : 0);   // Eqs. 55-56
-    const float hv = (0.5f * dt) * sh;                                          // v / 2, exactly
-    bad |= count && (fabsf(hv) > 0.5f);                                         // Eq. 67: |v| > 1
+    const float hv = sh;                                                        // v / 2
+    cflm = fmaxf(cflm, fabsf(hv) * cmask);
     Coef k;
     k.km = hm * (hv + fabsf(hv));                                               // Eqs. 57-58: backward difference
     k.kp = hp * (fabsf(hv) - hv);
@@ -193,11 +204,38 @@ __device__ __forceinline__ void inertial_step(float4& w, float4& d, bool has1, f
     }
 }
 
-template <bool C8, bool LITERAL, bool IMU, bool PE>
-__global__ void __launch_bounds__(kPrThreads, 1)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// wait for the completion of the mbarrier phase of the given parity; gives
+// up (false) after a bounded number of polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (int n = 0; n < (1 << 22); ++n) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <bool C8, bool LITERAL, bool IMU, bool PE, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, kPrWarpsMax / WARPS)
 k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int parity, float wscale,
             int flags, int* __restrict__ status, float mscale)
 {
+    constexpr int kPrWarps = WARPS;
+    constexpr int kPrH = kPrRows * WARPS;
+    constexpr int kPrThreads = 32 * WARPS;
+    constexpr int kPubSlots = 2 * WARPS + 2;
+    static_assert(!PE || WARPS == kPrWarpsMax, "the padded form runs with 16 warps only");
     extern __shared__ float4 smem4[];
     float4* geo = smem4;                                   // [kPrH][kPrW]
     float4* pub0 = geo + kPrH * kPrW;                      // [kPubSlots][kPrW]
@@ -209,7 +247,7 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     const PropJob& J = jobs[wk.x];
     const Grid g = J.g;
     const int nf = J.nf;
-    const int T = prop_tile(nf);
+    const int T = prop_tile(nf), TH = prop_tile_h(nf, WARPS);   // output tile width and height
     const int ox = wk.z - nf, oy = wk.y - nf;              // region origin, image coordinates
     const float4* __restrict__ in0 = J.in0[parity];
     const float4* __restrict__ in1 = J.in1[parity];
@@ -227,17 +265,19 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     float4 b[kPrRows][2];       // (dw, Y)
     float sp[kPrRows][2];       // speed of the next pass of each pixel
 
-    // per-pixel geometry: independent of the previous kernel, so it overlaps
-    // that kernel's tail under a programmatic dependent launch
+    // per-pixel geometry (eta and the column speed factor cu, prescaled by
+    // dt / 2: every speed below is dt/2 times the speed of Eq. 54)
+    auto geometry = [&]() {
 #pragma unroll
-    for (int k = 0; k < kPrRows; ++k) {
-        const int i = oy + r0 + k;
+        for (int k = 0; k < kPrRows; ++k) {
+            const int i = oy + r0 + k;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const PixGeo G = pix_geo(fmaf((float)(j0 + q), g.ax, g.bx), fmaf((float)i, g.ay, g.by), g.a);
-            geo[(r0 + k) * kPrW + q * 32 + lane] = make_float4(G.ex, G.ey, G.ez, G.cu);
+            for (int q = 0; q < 2; ++q) {
+                const PixGeo G = pix_geo(fmaf((float)(j0 + q), g.ax, g.bx), fmaf((float)i, g.ay, g.by), g.a);
+                geo[(r0 + k) * kPrW + q * 32 + lane] = make_float4(G.ex, G.ey, G.ez, G.cu * (0.5f * dt));
+            }
         }
-    }
+    };
     pdl_wait();
     if (J.gate) {   // a fallback job: skip the whole tile unless the residual exceeds the threshold
         const float res = __uint_as_float(*(volatile const unsigned*)J.gate);
@@ -265,16 +305,18 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
         for (int q = 0; q < 2; ++q) {
             const int j = j0 + q;
             const size_t gi = (size_t)ic * g.W + clampi(j, 0, g.W - 1);
-            float4 f = in0[gi];
+            a[k][q] = in0[gi];
+            b[k][q] = has1 ? in1[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    geometry();      // per-pixel geometry while the loads are in flight
+#pragma unroll
+    for (int k = 0; k < kPrRows; ++k) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float4& f = a[k][q];
             f.x *= ws; f.y *= ws; f.z *= ws;
-            a[k][q] = f;
-            if (has1) {
-                float4 h = in1[gi];
-                h.x *= ws; h.y *= ws; h.z *= ws;
-                b[k][q] = h;
-            } else {
-                b[k][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            if (has1) { b[k][q].x *= ws; b[k][q].y *= ws; b[k][q].z *= ws; }
             const float4 G = geo[(r0 + k) * kPrW + q * 32 + lane];   // this thread's own entry
             const float s = fmaf(G.x, f.x, fmaf(G.y, f.y, G.z * f.z));
             sp[k][q] = G.w * fmaf(-G.x, s, f.x);           // u of Eq. 54
@@ -284,14 +326,26 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     // output tile in region coordinates; CFL counted there only (each image
     // pixel belongs to exactly one tile, where its value is exact every pass)
     const bool col_in[2] = {c0 >= nf && c0 < nf + T && j0 < g.W, c0 + 1 >= nf && c0 + 1 < nf + T && j1 < g.W};
-    bool bad = false;
-
-    for (int it = 0; it < nf; ++it) {
-        // ---------------- column pass (Eqs. 59-62), neighbours in adjacent lanes
+    const float cmask[2] = {col_in[0] ? 1.0f : 0.0f, col_in[1] ? 1.0f : 0.0f};
+    float cflm[kPrRows];
 #pragma unroll
-        for (int k = 0; k < kPrRows; ++k) {
+    for (int k = 0; k < kPrRows; ++k) cflm[k] = 0.0f;
+    // split barriers of the published rows: FULL when every thread has
+    // published its edge rows, EMPTY when every thread has read them
+    __shared__ __align__(8) unsigned long long s_bars[2];
+    const uint32_t bar_full = (uint32_t)__cvta_generic_to_shared(&s_bars[0]);
+    const uint32_t bar_empty = (uint32_t)__cvta_generic_to_shared(&s_bars[1]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_full), "r"(kPrThreads));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty), "r"(kPrThreads));
+    }
+    __syncthreads();
+    int ph = 0;
+    bool timed_out = false;
+
+    auto colrow = [&](auto kc) {
+        constexpr int k = decltype(kc)::value;
             const int r = r0 + k;
-            const bool row_in = r >= nf && r < nf + T && oy + r < g.H;
             const float uL = __shfl_up_sync(0xffffffffu, sp[k][1], 1);    // column c0 - 1
             const float uR = __shfl_down_sync(0xffffffffu, sp[k][0], 1);  // column c0 + 2
             const float4 G0 = geo[r * kPrW + lane], G1 = geo[r * kPrW + 32 + lane];
@@ -301,10 +355,10 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             const bool m0 = j0 > 0, p0 = j0 < g.W - 1, m1 = j1 > 0, p1 = j1 < g.W - 1;
             const float sm0 = m0 ? uL : sp[k][0], spp0 = p0 ? sp[k][1] : sp[k][0];
             const float sm1 = m1 ? sp[k][0] : sp[k][1], spp1 = p1 ? uR : sp[k][1];
-            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0 ? 1.0f : 0.0f, p0 ? 1.0f : 0.0f, src0, dt, sdt, bad,
-                                                  row_in && col_in[0]);
-            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1 ? 1.0f : 0.0f, p1 ? 1.0f : 0.0f, src1, dt, sdt, bad,
-                                                  row_in && col_in[1]);
+            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0 ? 1.0f : 0.0f, p0 ? 1.0f : 0.0f, src0, dt, sdt,
+                                                  cflm[k], cmask[0]);
+            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1 ? 1.0f : 0.0f, p1 ? 1.0f : 0.0f, src1, dt, sdt,
+                                                  cflm[k], cmask[1]);
             const float4 aL = shfl_up4(a[k][1]), aR = shfl_down4(a[k][0]);
             const float4 na0 = upwind4(a[k][0], aL, a[k][1], k0.km, k0.kp, k0.kself, k0.kself);
             const float4 na1 = upwind4(a[k][1], a[k][0], aR, k1.km, k1.kp, k1.kself, k1.kself);
@@ -317,7 +371,17 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             a[k][0] = na0; a[k][1] = na1;
             sp[k][0] = G0.w * fmaf(G0.z, na0.y, -G0.y * na0.z);   // v of Eq. 54 for the row pass
             sp[k][1] = G1.w * fmaf(G1.z, na1.y, -G1.y * na1.z);
-        }
+            };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, kPrRows - 1>;
+    for (int it = 0; it < nf; ++it, ++ph) {
+        // ---------------- column pass (Eqs. 59-62), neighbours in adjacent lanes:
+        // the two edge rows first, published while the middle rows run
+        colrow(I0{});
+        colrow(I3{});
+        if (ph > 0 && !mbar_wait_bounded(bar_empty, (uint32_t)(ph - 1) & 1u)) timed_out = true;
         // publish my first and last rows for the neighbouring warps (padded form:
         // the first and the last warp also fill the edge slots)
 #pragma unroll
@@ -334,7 +398,10 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
             }
         }
-        __syncthreads();
+        mbar_arrive(bar_full);
+        colrow(I1{});
+        colrow(I2{});
+        if (!mbar_wait_bounded(bar_full, (uint32_t)ph & 1u)) timed_out = true;
         // ---------------- row pass (Eqs. 63-66, reading R2), neighbours in rows k -+ 1
         float4 prev_a[2], prev_b[2];
         float prev_v[2];
@@ -358,7 +425,6 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
 #pragma unroll
         for (int k = 0; k < kPrRows; ++k) {
             const int r = r0 + k, i = oy + r;
-            const bool row_in = r >= nf && r < nf + T && i < g.H;
             float4 next_a[2], next_b[2];
             float next_v[2];
             if (k + 1 < kPrRows) {
@@ -372,6 +438,7 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                     next_b[q] = C8 ? pub1[base + 32 * q] : b[k][q];
                     next_v[q] = pubv[base + 32 * q];
                 }
+                mbar_arrive(bar_empty);           // this thread has read the published rows
             } else {   // the first row of the warp below (or myself at the region edge)
                 const bool below = warp + 1 < kPrWarps;
                 const int base = (below ? 2 * warp + 3 : 2 * warp + 2) * kPrW + lane;
@@ -381,6 +448,7 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                     next_b[q] = (below && has1) ? pub1[base + 32 * q] : b[k][q];
                     next_v[q] = below ? pubv[base + 32 * q] : sp[k][q];
                 }
+                mbar_arrive(bar_empty);           // this thread has read the published rows
             }
             const bool mi = i > 0, pi = i < g.H - 1;
             float4 na[2], nb[2];
@@ -389,8 +457,8 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 const float4 G = geo[r * kPrW + q * 32 + lane];
                 const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
                 const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
-                const Coef kk = coefficients<LITERAL>(vm, vp, mi ? 1.0f : 0.0f, pi ? 1.0f : 0.0f, src, dt, sdt, bad,
-                                                      row_in && col_in[q]);
+                const Coef kk = coefficients<LITERAL>(vm, vp, mi ? 1.0f : 0.0f, pi ? 1.0f : 0.0f, src, dt, sdt,
+                                                      cflm[k], cmask[q]);
                 na[q] = upwind4(a[k][q], prev_a[q], next_a[q], kk.km, kk.kp, kk.kself, kk.kself);
                 if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], kk.km, kk.kp, kk.kself, kk.kselfy);
                 if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
@@ -402,14 +470,13 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
                 sp[k][q] = G.w * fmaf(-G.x, s, na[q].x);
             }
         }
-        __syncthreads();   // the published rows are overwritten by the next column pass
     }
 
     // write the output tile (its in-image part)
 #pragma unroll
     for (int k = 0; k < kPrRows; ++k) {
         const int r = r0 + k, i = oy + r;
-        if (r < nf || r >= nf + T || i >= g.H) continue;
+        if (r < nf || r >= nf + TH || i >= g.H) continue;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             if (!col_in[q]) continue;
@@ -418,7 +485,14 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             if (has1) J.out1[gi] = b[k][q];
         }
     }
+    if (timed_out && status) atomicOr(status, kStatusTimeout);
     if ((flags & kCheckCfl) && status) {
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < kPrRows; ++k) {
+            const int r = r0 + k;
+            bad |= r >= nf && r < nf + TH && oy + r < g.H && cflm[k] > 0.5f;
+        }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusCfl);
     }
 }
