@@ -1866,12 +1866,22 @@ inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255)
 // weight and bias gradients of one 3x3 layer, ADDED into dw [9][Cout][Cin]
 // and db [Cout] (the caller zeroes them)
 int wgrad_launch(int N, int H, int W, int Cin, int Cout, const __nv_bfloat16* x, const __nv_bfloat16* dy, float* dw,
-                 float* db, cudaStream_t st)
+                 float* db, cudaStream_t st, int* status = nullptr)
 {
-    const int blocks = std::min(N * H * ((W + 127) / 128), kSmCount * 2);
-    const size_t wsm = wgrad_smem_bytes(Cin, Cout);
-    if (set_smem_attr((const void*)k_wgrad, wsm)) return SF_ECUDA;
-    k_wgrad<<<blocks, kWgThreads, wsm, st>>>(N, H, W, Cin, Cout, x, dy, dw, db);
+    WgradArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = N; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout;
+    a.x = x; a.dy = dy; a.dw = dw; a.db = db;
+    a.tiles_x = ceil_div(W, kConvM);
+    a.spin_limit = kConvSpinLimit;
+    a.status = status;
+    // strips of up to 32 rows, shorter when that leaves fewer than 2 per SM
+    const int columns = N * a.tiles_x;
+    a.strip = std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(kSmCount * 2, columns)))));
+    const int strips = columns * ceil_div(H, a.strip);
+    const size_t smem = wgrad_tc_smem_bytes();
+    if (set_smem_attr((const void*)k_wgrad_tc, smem)) return SF_ECUDA;
+    k_wgrad_tc<<<std::min(strips, kSmCount * 2), kWgtThreads, smem, st>>>(a);
     return last_error();
 }
 
@@ -2058,7 +2068,7 @@ int sf_surrogate_train_step(sf_surrogate* s, const sf_grid* g, int n, const floa
     for (int l = sf_surrogate::kL - 1; l >= 0 && !r; --l) {
         const __nv_bfloat16* in = l == 0 ? s->x0 : s->a[l - 1];
         r = wgrad_launch(n, g->H, g->W, s->cin[l], s->cout[l], in, d, s->grad + s->off[l],
-                         s->grad + s->off[l] + 9 * s->cin[l] * s->cout[l], st);
+                         s->grad + s->off[l] + 9 * s->cin[l] * s->cout[l], st, s->status);
         if (r || l == 0) break;
         __nv_bfloat16* dx = bufs[l & 1];
         r = conv_launch(s, n, g->H, g->W, s->cout[l], s->cin[l], d, s->w16t[l], nullptr, 0, dx, nullptr, st);

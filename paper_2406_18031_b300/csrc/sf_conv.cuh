@@ -299,3 +299,221 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
 }
 
 }  // namespace sfdev
+
+namespace sfdev {
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3 layer on the tensor cores:
+//   dW[3 dy + dx][co][ci] = sum over pixels p of g[p][co] x[p + (dy - 1, dx - 1)][ci]
+// a contraction over pixels.  For one image row y and one horizontal tap dx
+// it is a GEMM with K = the 128 pixels of a tile and
+//   A[(dy, ci)][p] = x[y + dy - 1][p + dx - 1][ci]   (M = 4 staged rows x 32 channels = 128)
+//   B[p][co]       = g[y][p][co]                      (N = Cout)
+// both read in the MN-major layout straight from the staged rows: in the
+// channel-chunk-major staging (chunk c of slot p at c P 16 + p 16) a core
+// matrix of 8 channels x 8 consecutive pixels is 128 contiguous bytes, the
+// next 8 pixels are 128 bytes on (leading byte offset, K direction) and the
+// next channel chunk -- of the same row or of the next row -- P 16 bytes on
+// (stride byte offset, M direction).  So the three input rows a tile needs
+// (plus one more, whose products land in D rows 96..127 and are dropped) are
+// four consecutive row slots, and dx moves the start by dx slots.  The rows
+// live in a ring of four slots, the first three mirrored after the fourth,
+// so any four consecutive slots are contiguous.  The accumulators D_dx (128
+// lanes x 32 FP32 columns each) stay in tensor memory for all the rows a
+// CTA walks and are added to dW once at the end.  Cin = 16 is staged as 32
+// channels (zeros).  The bias gradient (a plain sum of g) runs on the CUDA
+// cores beside the staging.
+// ---------------------------------------------------------------------------
+
+struct WgradArgs {
+    int N, H, W, Cin, Cout;
+    const __nv_bfloat16* x;      // N x H x W x Cin
+    const __nv_bfloat16* dy;     // N x H x W x Cout
+    float* dw;                   // 9 x Cout x Cin, added to
+    float* db;                   // Cout, added to
+    int tiles_x;                 // ceil(W / 128)
+    int strip;                   // output rows per strip
+    int spin_limit;
+    int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
+};
+
+constexpr int kWgC = 32;                                   // staged channels per input pixel
+constexpr int kWgRowBytes = (kWgC / 8) * kConvSlots * 16;  // one staged input row
+constexpr int kWgRingSlots = 7;                            // 4 slots + mirrors of slots 0..2
+constexpr int kWgYBytes = (32 / 8) * kConvM * 16;          // one staged row of g (Cout <= 32)
+constexpr int kWgtThreads = 128;
+static_assert(kWgtThreads == kConvM, "one staged pixel of g per thread");
+
+__host__ __device__ inline size_t wgrad_tc_smem_bytes()
+{
+    return (size_t)kWgRingSlots * kWgRowBytes + 2 * (size_t)kWgYBytes + 32;   // + two mbarriers, the TMEM address
+}
+
+// instruction descriptor of kind::f16 with both operands MN-major
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_mn(int n)
+{
+    return umma_idesc_bf16(n) | (1u << 15) | (1u << 16);
+}
+
+// input row iy of image nn, pixels x0 - 1 .. x0 + 134 (zero outside the image
+// and beyond Cin), into ring slot `slot` and its mirror
+__device__ __forceinline__ void wg_stage_x(const WgradArgs& a, unsigned char* ring, int nn, int iy, int x0, int slot)
+{
+    const bool row_in = iy >= 0 && iy < a.H;
+    const int C8 = a.Cin / 8;
+    unsigned char* d0 = ring + (size_t)slot * kWgRowBytes;
+    unsigned char* d1 = slot < 3 ? d0 + (size_t)4 * kWgRowBytes : nullptr;
+    for (int p = threadIdx.x; p < kConvSlots; p += kWgtThreads) {
+        const int ix = x0 + p - 1;
+        const bool in = row_in && ix >= 0 && ix < a.W && p < kConvM + 2;
+        const uint4* src = reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + (in ? iy : 0)) * a.W +
+                                                                   (in ? ix : 0)) * a.Cin);
+        uint4 v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = (in && c < C8) ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            *reinterpret_cast<uint4*>(d0 + (size_t)c * kConvSlots * 16 + p * 16) = v[c];
+            if (d1) *reinterpret_cast<uint4*>(d1 + (size_t)c * kConvSlots * 16 + p * 16) = v[c];
+        }
+    }
+}
+
+// row yy of g into buffer yb (pixel p of the tile at p 16 in each chunk),
+// adding the thread's pixel to its bias sums
+__device__ __forceinline__ void wg_stage_g(const WgradArgs& a, unsigned char* yb, int nn, int yy, int x0, float* bsum)
+{
+    const int p = threadIdx.x;                 // kWgtThreads == kConvM: one pixel per thread
+    const int ix = x0 + p;
+    const bool in = ix < a.W;
+    const int C8 = a.Cout / 8;
+    const uint4* src = reinterpret_cast<const uint4*>(a.dy + (((size_t)nn * a.H + yy) * a.W + (in ? ix : 0)) * a.Cout);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c >= C8) break;
+        const uint4 v = in ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(yb + (size_t)c * kConvM * 16 + p * 16) = v;
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(h[e]);
+            bsum[8 * c + 2 * e] += f.x;
+            bsum[8 * c + 2 * e + 1] += f.y;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kWgtThreads) k_wgrad_tc(WgradArgs a)
+{
+    extern __shared__ __align__(16) unsigned char wsm[];
+    unsigned char* ring = wsm;
+    unsigned char* ybuf = wsm + (size_t)kWgRingSlots * kWgRowBytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ybuf + 2 * kWgYBytes);   // two: groups of even and odd rows
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_holder))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t idesc = umma_idesc_bf16_mn(a.Cout);
+    const uint32_t ring_base = smem_u32(ring), y_base = smem_u32(ybuf);
+    const uint32_t mb[2] = {smem_u32(mbar), smem_u32(mbar + 1)};
+    uint32_t phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};
+    bool failed = false, any = false;
+    float bsum[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) bsum[k] = 0.0f;
+    // wait (CTA-wide, bounded) for the group committed to mbarrier b, if any
+    auto drain = [&](int b) {
+        if (!pend[b]) return true;
+        const bool done = mbar_wait(mb[b], phase[b], a.spin_limit);
+        if (!__syncthreads_and(done)) return false;
+        phase[b] ^= 1u;
+        pend[b] = false;
+        return true;
+    };
+
+    const int strips_y = (a.H + a.strip - 1) / a.strip;
+    const int n_strips = a.N * a.tiles_x * strips_y;
+    for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
+        const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
+        const int x0 = tx * kConvM, y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
+        // the previous strip's groups still read the ring and g
+        if (!drain(0) || !drain(1)) { failed = true; break; }
+        for (int r = y_begin - 1; r <= y_begin + 1; ++r) wg_stage_x(a, ring, nn, r, x0, (r + 4) & 3);
+        wg_stage_g(a, ybuf + (y_begin & 1) * kWgYBytes, nn, y_begin, x0, bsum);
+        for (int y = y_begin; y < y_end; ++y) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            // the group of row y: the four ring slots from that of row y - 1
+            // (rows y - 1, y, y + 1 and a dropped fourth) and g of row y
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = ring_base + (uint32_t)(((y - 1 + 4) & 3) * kWgRowBytes);
+                const uint32_t b0 = y_base + (uint32_t)((y & 1) * kWgYBytes);
+                for (int dx = 0; dx < 3; ++dx)
+                    for (int k = 0; k < kConvM / 16; ++k) {
+                        const uint64_t ad = umma_desc(a0 + (uint32_t)((dx + 16 * k) * 16), 128, kConvSlots * 16);
+                        const uint64_t bd = umma_desc(b0 + (uint32_t)(16 * k * 16), 128, kConvM * 16);
+                        umma_bf16(tmem + (uint32_t)(32 * dx), ad, bd, idesc, (any || k > 0) ? 1 : 0);
+                    }
+                umma_commit(mb[y & 1]);
+            }
+            any = true;
+            pend[y & 1] = true;
+            // stage the next row while this group runs: the slot of row y + 2
+            // held row y - 2 and the other g buffer row y - 1, both read by
+            // the previous group (this group reads the slot of row y + 2 only
+            // for its dropped fourth row)
+            if (y + 1 < y_end) {
+                if (!drain((y + 1) & 1)) { failed = true; break; }
+                if (y + 2 <= y_end) wg_stage_x(a, ring, nn, y + 2, x0, (y + 2) & 3);
+                wg_stage_g(a, ybuf + ((y + 1) & 1) * kWgYBytes, nn, y + 1, x0, bsum);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+    }
+    if (!failed && (!drain(0) || !drain(1))) failed = true;
+    if (failed) {
+        if (tid == 0 && a.status) atomicOr(a.status, kStatusTimeout);
+        // a second bounded wait for the groups still in flight
+        for (int b = 0; b < 2; ++b)
+            if (pend[b]) mbar_wait(mb[b], phase[b], a.spin_limit);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // D_dx lane (dy, ci) = warp dy, lane ci; warp 3 holds the dropped fourth row
+    if (!failed && any) {
+        for (int dx = 0; dx < 3; ++dx) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * dx), v);
+            if (warp < 3 && lane < a.Cin) {
+                float* dst = a.dw + (size_t)(3 * warp + dx) * a.Cout * a.Cin + lane;
+                for (int co = 0; co < a.Cout; ++co) atomicAdd(dst + (size_t)co * a.Cin, v[co]);
+            }
+        }
+    }
+    // bias: sum the threads' partial sums of g
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float s = bsum[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && k < a.Cout && !failed) atomicAdd(a.db + k, s);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+}  // namespace sfdev

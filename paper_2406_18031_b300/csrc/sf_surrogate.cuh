@@ -3,9 +3,10 @@
 // activations and weights, FP32 accumulation on the tensor cores) that maps
 // the top-level state (w, rho) of one frame to its prediction for the next,
 // trained on pairs that the plain propagation produces.  The convolutions are
-// k_conv3x3 (forward, and backward-data with flipped, transposed weights);
-// this file holds the per-pixel feature and head kernels, the loss gradient,
-// the weight gradient, the ReLU mask and the Adam step.
+// k_conv3x3 (forward, and backward-data with flipped, transposed weights) and
+// k_wgrad_tc (the weight gradient), both on the tensor cores; this file holds
+// the per-pixel feature and head kernels, the loss gradient, the ReLU mask,
+// the Adam step and the fallback's residual.
 //
 // Features of a pixel: w / (4 dmu) (3, px/frame over 4), rho, eta_x, eta_y,
 // and 10 zero channels.  Output channels 0..3 are the change over one frame
@@ -91,74 +92,6 @@ __global__ void k_relu_mask(size_t n, __nv_bfloat16* __restrict__ da, const __nv
 {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
         if (!(__bfloat162float(a[k]) > 0.0f)) da[k] = __float2bfloat16(0.0f);
-}
-
-// Weight and bias gradients of a 3x3 layer: dW[tap][co][ci] += sum over
-// pixels of dy[p][co] x[p + off(tap)][ci] (zero padding), db[co] += sum dy.
-// Tiles of 128 pixels of one row; a CTA walks several tiles, each thread
-// keeps its outputs (tap, co, ci) in registers and adds them to global
-// memory once.
-constexpr int kWgThreads = 256;
-constexpr int kWgPerThread = 9 * 32 * 32 / kWgThreads;   // 36 outputs per thread at most
-
-__host__ __device__ inline size_t wgrad_smem_bytes(int Cin, int Cout)
-{
-    return (size_t)(3 * 130 * Cin + 128 * Cout) * sizeof(float);
-}
-
-__global__ void __launch_bounds__(kWgThreads) k_wgrad(int N, int H, int W, int Cin, int Cout,
-                                                     const __nv_bfloat16* __restrict__ x,
-                                                     const __nv_bfloat16* __restrict__ dy, float* __restrict__ dW,
-                                                     float* __restrict__ db)
-{
-    extern __shared__ float wsm[];
-    float* xs = wsm;                       // [3][130][Cin]
-    float* ys = wsm + 3 * 130 * Cin;       // [128][Cout]
-    const int tid = threadIdx.x;
-    const int n_out = 9 * Cout * Cin;
-    float acc[kWgPerThread];
-#pragma unroll
-    for (int k = 0; k < kWgPerThread; ++k) acc[k] = 0.0f;
-    float bacc = 0.0f;
-    const int tiles_x = (W + 127) / 128, n_tiles = N * H * tiles_x;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int tx = t % tiles_x, row = t / tiles_x, yy = row % H, nn = row / H, x0 = tx * 128;
-        __syncthreads();
-        for (int idx = tid; idx < 3 * 130 * Cin; idx += kWgThreads) {
-            const int c = idx % Cin, p = (idx / Cin) % 130, r = idx / (Cin * 130);
-            const int iy = yy + r - 1, ix = x0 + p - 1;
-            float v = 0.0f;
-            if (iy >= 0 && iy < H && ix >= 0 && ix < W)
-                v = __bfloat162float(x[(((size_t)nn * H + iy) * W + ix) * Cin + c]);
-            xs[(r * 130 + p) * Cin + c] = v;
-        }
-        for (int idx = tid; idx < 128 * Cout; idx += kWgThreads) {
-            const int c = idx % Cout, p = idx / Cout, ix = x0 + p;
-            ys[p * Cout + c] = ix < W ? __bfloat162float(dy[(((size_t)nn * H + yy) * W + ix) * Cout + c]) : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kWgPerThread; ++k) {
-            const int o = tid + k * kWgThreads;
-            if (o < n_out) {
-                const int ci = o % Cin, co = (o / Cin) % Cout, tap = o / (Cin * Cout);
-                const int r = tap / 3, dx = tap % 3;
-                float s = 0.0f;
-                const float* xr = xs + (r * 130 + dx) * Cin + ci;
-                const float* yr = ys + co;
-                for (int p = 0; p < 128; ++p) s = fmaf(yr[p * Cout], xr[p * Cin], s);
-                acc[k] += s;
-            }
-        }
-        if (tid < Cout)
-            for (int p = 0; p < 128; ++p) bacc += ys[p * Cout + tid];
-    }
-#pragma unroll
-    for (int k = 0; k < kWgPerThread; ++k) {
-        const int o = tid + k * kWgThreads;
-        if (o < n_out) atomicAdd(dW + o, acc[k]);
-    }
-    if (tid < Cout) atomicAdd(db + tid, bacc);
 }
 
 // Adam on one layer's FP32 master weights and biases; writes the BF16
