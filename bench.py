@@ -1295,6 +1295,18 @@ def run_conv_line(args):
     flops = 2 * 9 * C * C * n * H * W
     peaks, kind = measured_peaks()
     tf = flops / (ms / 1e3) / 1e12
+    # the same layer's weight gradient (training): a contraction over the 16.8 M pixels
+    dwt = torch.empty((9, C, C), device=dev)
+    dbt = torch.empty((C,), device=dev)
+    for _ in range(3):
+        sf.conv3x3_wgrad(x, y, dwt, dbt, stream=stream)
+    evw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evw[k][0].record(stream)
+        sf.conv3x3_wgrad(x, y, dwt, dbt, stream=stream)
+        evw[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms_w = sum(a.elapsed_time(c) for a, c in evw) / args.steps
     line = {"metric": "TFLOP/s of one surrogate layer", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -1303,7 +1315,11 @@ def run_conv_line(args):
                          "frac": tf / peaks["bf16_tflops"], "traffic": None,
                          "peak_source": f"{kind} bf16_tflops (burst)"},
             "hbm_gbs_algorithmic": 2 * C * 2 * n * H * W / (ms / 1e3) / 1e9,
-            "gpu_launches": args.steps, "clocks": clocks}
+            "wgrad": {"ms": ms_w, "tflops": flops / (ms_w / 1e3) / 1e12,
+                      "frac_of_bf16_peak": flops / (ms_w / 1e3) / 1e12 / peaks["bf16_tflops"],
+                      "hbm_gbs_algorithmic": 2 * C * 2 * n * H * W / (ms_w / 1e3) / 1e9,
+                      "kernel": "k_wgrad_tc (sf_conv3x3_wgrad), tensor cores, same layer"},
+            "gpu_launches": 2 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
