@@ -23,6 +23,8 @@
 #include <random>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sf.h"
 #include "sf_conv.cuh"
 #include "sf_kernels.cuh"
@@ -78,6 +80,13 @@ int set_smem_attr(const void* fn, size_t bytes)
 }
 
 int last_error() { return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA; }
+
+// NVTX range around the host-side issue of one stage's launch (visible in a
+// system trace next to the kernel it issued; free when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // The frame's kernels are launched with programmatic stream serialisation:
 // each may be scheduled while the previous kernel of the stream finishes, and
@@ -940,19 +949,28 @@ int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, f
 {
     int r;
     {
+        NvtxRange nv("sf update: models + 3x3 solve + blend, every level");
         ProfScope ps(E.prof, slot++, st);
         r = launch_solve(E.solve, a, st);
         if (r) return r;
     }
     const int check = (E.flags & SF_CHECK_FINITE) != 0;
+    static const char* const kSmoothNames[] = {"sf smoothing + reconstruction: top level",
+                                               "sf smoothing + reconstruction: top level - 1",
+                                               "sf smoothing + reconstruction: top level - 2",
+                                               "sf smoothing + reconstruction: top level - 3"};
+    int depth = 0;
     for (auto& pl : E.smooth) {
         if (!pl.nwork) continue;
+        NvtxRange nv(E.update_mode == 2 ? "sf smoothing: every level" : kSmoothNames[std::min(depth, 3)]);
+        ++depth;
         ProfScope ps(E.prof, slot++, st);
         r = launch_smooth(pl, a.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
         if (r) return r;
     }
     for (auto& pl : E.recon) {
         if (!pl.nwork) continue;
+        NvtxRange nv("sf reconstruction of one level");
         ProfScope ps(E.prof, slot++, st);
         r = launch_recon(pl, a.parity ^ 1, 1.0f / dt, check, E.status, flow, inv, st);
         if (r) return r;
@@ -975,14 +993,17 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
     a.lambda_ref = E.st[0].p.lambda_ref;
     a.parity = E.parity;
     a.init = !E.initialised;
+    NvtxRange frame("sf frame");
     int slot = 0, r;
     if (!a.init) {
         for (auto& pl : E.prop) {
+            NvtxRange nv("sf prediction: propagation launch (every level of every stream)");
             ProfScope ps(E.prof, slot++, st);
             r = launch_propagate(pl, E.parity, wscale, E.flags, E.status, st, dt);
             if (r) return r;
         }
         if (E.surr) {
+            NvtxRange nv("sf prediction: surrogate network (top levels)");
             ProfScope ps(E.prof, slot++, st);
             for (auto& s : E.st) {
                 sf_level_state& lv = s.lv[s.L - 1];
@@ -1000,6 +1021,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
             // the fallback: residual against one plain step, then the plain
             // propagation of every stream whose residual exceeds its threshold
             // (CTAs of the other streams return at once); no host decision
+            NvtxRange nv("sf prediction: surrogate check and gated plain fallback");
             ProfScope ps(E.prof, slot++, st);
             if (cudaMemsetAsync(E.surr_res, 0, E.st.size() * sizeof(unsigned), st) != cudaSuccess) return SF_ECUDA;
             r = launch_propagate(E.surr_one_plan, E.parity, 1.0f, E.flags & ~SF_CHECK_CFL, nullptr, st, dt);
