@@ -1784,6 +1784,56 @@ int sf_remap_equirect(const sf_grid* dst, const float* R, int Hs, int Ws, const 
     return remap_launch(1, dst, R, Hs, Ws, nullptr, src_image, src_range, out_image, out_range, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The TMA description of an NHWC bf16 input for the convolution: dimensions
+// (C, W, H, N) innermost first, boxes of 8 channels x kConvSlots pixels x 1 row
+// x 1 image, zero fill outside the tensor.  cuTensorMapEncodeTiled comes from
+// the driver through the runtime's entry-point query (no link to the driver
+// library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int conv_input_map(const void* x, int N, int H, int W, int Cin, CUtensorMap* out)
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!fn) {
+            void* p = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+                return SF_ECUDA;
+            fn = (EncodeTiledFn)p;
+        }
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)kConvSlots, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SF_OK : SF_ECUDA;
+}
+
+// strips of up to 32 output rows, shorter when that leaves fewer than three
+// per SM (three CTAs fit an SM)
+int conv_strip(int N, int H, int tiles_x)
+{
+    const int columns = N * tiles_x;
+    return std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(kSmCount * 3, columns)))));
+}
+
+}  // namespace
+
+extern "C" {
+
 int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void* w, const float* bias, int relu,
                void* y, float* y32, int* status, void* stream)
 {
@@ -1805,14 +1855,13 @@ int sf_conv3x3(int N, int H, int W, int Cin, int Cout, const void* x, const void
     a.n_tiles = N * H * a.tiles_x;
     a.status = status;
     a.spin_limit = kConvSpinLimit;
-    const size_t smem = conv_smem_bytes(Cin, Cout);
+    a.strip = conv_strip(N, H, a.tiles_x);
+    CUtensorMap map;
+    if (conv_input_map(x, N, H, W, Cin, &map)) return SF_ECUDA;
+    const size_t smem = conv_ws_smem_bytes(Cin, Cout);
     if (set_smem_attr((const void*)k_conv3x3, smem)) return SF_ECUDA;
-    // strips of up to 32 rows, shorter when that leaves fewer than 4 per SM
-    const int columns = N * a.tiles_x;
-    a.strip = std::max(1, std::min(kConvStrip, ceil_div(H, std::max(1, ceil_div(kSmCount * 4, columns)))));
-    const int strips = columns * ceil_div(H, a.strip);
-    const int grid = std::min(strips, kSmCount * 4);
-    k_conv3x3<<<grid, kConvThreads, smem, (cudaStream_t)stream>>>(a);
+    const int strips = N * a.tiles_x * ceil_div(H, a.strip);
+    k_conv3x3<<<std::min(strips, kSmCount * 3), kConvWsThreads, smem, (cudaStream_t)stream>>>(map, a);
     return last_error();
 }
 
@@ -1884,6 +1933,7 @@ int conv_launch(const sf_surrogate* s, int N, int H, int W, int cin, int cout, c
 }
 
 inline int grid_stride_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, kSmCount * 8); }
+
 
 // weight and bias gradients of one 3x3 layer, ADDED into dw [9][Cout][Cin]
 // and db [Cout] (the caller zeroes them)
@@ -1961,9 +2011,11 @@ int sf_selftest_conv_timeout(void* stream)
     a.status = (int*)(mem + xb + wb + yb);
     a.spin_limit = 1024;      // a short limit: the test ends in well under a second
     a.no_commit = 1;          // nothing is issued, so the wait cannot complete
-    if (!r && set_smem_attr((const void*)k_conv3x3, conv_smem_bytes(16, 16))) r = SF_ECUDA;
+    CUtensorMap map;
+    if (!r && conv_input_map(a.x, 1, 1, 128, 16, &map)) r = SF_ECUDA;
+    if (!r && set_smem_attr((const void*)k_conv3x3, conv_ws_smem_bytes(16, 16))) r = SF_ECUDA;
     if (!r) {
-        k_conv3x3<<<1, kConvThreads, conv_smem_bytes(16, 16), st>>>(a);
+        k_conv3x3<<<1, kConvWsThreads, conv_ws_smem_bytes(16, 16), st>>>(map, a);
         r = last_error();
     }
     int s = 0;
@@ -2183,7 +2235,7 @@ int engine_attach(Engine& E, sf_surrogate* s)
         for (auto& es : E.st) mx = std::max(mx, (size_t)es.lv[es.L - 1].grid.H * es.lv[es.L - 1].grid.W);
         r = surrogate_capacity(s, mx);
         // the convolution's shared-memory limit is raised here, outside any stream capture
-        if (!r && set_smem_attr((const void*)k_conv3x3, conv_smem_bytes(kSurrHidden, kSurrHidden))) r = SF_ECUDA;
+        if (!r && set_smem_attr((const void*)k_conv3x3, conv_ws_smem_bytes(kSurrHidden, kSurrHidden))) r = SF_ECUDA;
         if (r) return r;
     }
     cudaStream_t st;

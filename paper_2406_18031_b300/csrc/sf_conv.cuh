@@ -1,21 +1,25 @@
 // sf_conv.cuh -- 3x3 convolution layers of the propagation surrogate on the
 // 5th-generation tensor cores (tcgen05, sm_103a): BF16 operands staged in
-// shared memory, FP32 accumulators in tensor memory.
+// shared memory by the tensor memory accelerator, FP32 accumulators in tensor
+// memory.
 //
 // Implicit GEMM per tile of 128 consecutive output pixels of one image row:
 // D[128 x Cout] = sum over the 9 taps of A_tap[128 x Cin] B_tap[Cin x Cout]
-// (K = 16 per instruction, 9 Cin / 16 instructions per tile).  The three
-// input rows the tile needs are staged once, "channel-chunk major": chunk c
-// (8 channels, 16 bytes) of slot p at  c * P * 16 + p * 16.  Any 8
-// consecutive slots of one chunk are then a core matrix (8 rows x 16 bytes,
-// rows 16 bytes apart), so the A operand of tap (dy, dx) is the same buffer
-// with its start moved by dx slots: no im2col copy.  Descriptors use the
-// no-swizzle K-major layout: leading byte offset = distance between the two
-// K-adjacent core matrices of an instruction (the next chunk, P * 16 bytes),
-// stride byte offset = distance between M-adjacent core matrices (8 slots,
-// 128 bytes).  The weights use the same layout with Cout rows.
+// (K = 16 per instruction, 9 Cin / 16 instructions per tile).  Each input row
+// a tile needs is staged once, "channel-chunk major": chunk c (8 channels,
+// 16 bytes) of slot p at  c * P * 16 + p * 16 -- exactly what one TMA copy of
+// an 8-channel x P-pixel box of the NHWC input writes, so a row is C8 tiled
+// bulk copies (zero fill beyond the image).  Any 8 consecutive slots of one
+// chunk are then a core matrix (8 rows x 16 bytes, rows 16 bytes apart), so
+// the A operand of tap (dy, dx) is the same buffer with its start moved by dx
+// slots: no im2col copy.  Descriptors use the no-swizzle K-major layout:
+// leading byte offset = distance between the two K-adjacent core matrices of
+// an instruction (the next chunk, P * 16 bytes), stride byte offset = distance
+// between M-adjacent core matrices (8 slots, 128 bytes).  The weights use the
+// same layout with Cout rows.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "sf_device.cuh"
@@ -23,7 +27,6 @@
 namespace sfdev {
 
 constexpr int kConvM = 128;           // output pixels per tile (TMEM lanes)
-constexpr int kConvThreads = 128;     // 4 warps: warp w owns TMEM lanes 32w .. 32w + 31
 constexpr int kConvSlots = 136;       // staged pixels per row: 128 + 2 halo, rounded up
 constexpr int kConvTmemCols = 32;     // FP32 accumulator columns (Cout <= 32)
 constexpr int kConvSpinLimit = 1 << 22;
@@ -44,15 +47,7 @@ struct ConvArgs {
     int* status;                 // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
-constexpr int kConvRows = 4;          // staged input rows: a ring of 4
 constexpr int kConvStrip = 32;        // the longest strip of output rows (a CTA's unit of work)
-
-__host__ __device__ inline size_t conv_smem_bytes(int Cin, int Cout)
-{
-    const size_t a = (size_t)kConvRows * (Cin / 8) * kConvSlots * 16;
-    const size_t b = (size_t)9 * (Cin / 8) * Cout * 16;
-    return a + b + 32;   // + two mbarriers (8 bytes each) and the TMEM address
-}
 
 // shared::cta address of a generic pointer into shared memory
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -122,31 +117,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// stage input row `iy` of image nn, columns x0 - 1 .. x0 + 134 (zero outside
-// the image), into row slot `slot`, channel-chunk major
-__device__ __forceinline__ void conv_stage_row(const ConvArgs& a, unsigned char* As, int C8, int nn, int iy, int x0,
-                                               int slot)
-{
-    unsigned char* dst = As + (size_t)slot * C8 * kConvSlots * 16;
-    const bool row_in = iy >= 0 && iy < a.H;
-    // one pixel per thread: its C8 chunks are contiguous in global memory, and
-    // the threads of a warp store one chunk of 32 consecutive slots at a time
-    // (consecutive 16-byte addresses: no bank conflicts)
-    for (int p = threadIdx.x; p < kConvSlots; p += kConvThreads) {
-        const int ix = x0 + p - 1;
-        const bool in = row_in && ix >= 0 && ix < a.W && p < kConvM + 2;
-        const uint4* src = reinterpret_cast<const uint4*>(a.x + (((size_t)nn * a.H + (in ? iy : 0)) * a.W +
-                                                                   (in ? ix : 0)) * a.Cin);
-        uint4 v[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (c < C8) v[c] = in ? src[c] : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (c < C8) *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16 + p * 16) = v[c];
-    }
-}
-
 // TMEM buffer `buf` (output row yy) -> bias, ReLU, global memory
 __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int buf, int nn, int yy, int x0)
 {
@@ -187,113 +157,233 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, 
     }
 }
 
-// A CTA walks strips of output rows of one 128-pixel column of tiles.  The input rows live in a ring of 4 slots, so each output row stages
-// one new input row; two TMEM accumulators let the MMAs of row y run while
-// the epilogue of row y - 1 and the staging of row y + 2 proceed:
-//   step y:  [sync] MMA(y) -> TMEM[y & 1]  |  wait MMA(y - 1), epilogue(y - 1)
-//            |  stage input row y + 2 into the slot of row y - 2
-// (rows y - 1 .. y + 1 feed MMA(y); row y - 2 was last read by MMA(y - 1)).
-__global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a)
+// Warp-specialised pipeline.  A CTA walks strips of output rows of one
+// 128-pixel column of tiles with 6 warps:
+//   warp 4 (one thread): the producer -- tiled TMA copies of every input row
+//     the strip needs into a ring of kConvRing row slots (mbarrier "full"
+//     with the expected bytes; it reuses a slot once the MMAs that read it
+//     have completed, mbarrier "empty");
+//   warp 5 (one thread): the MMA issuer -- for output row y the 9 taps x
+//     Cin/16 instructions into accumulator y % kConvAcc (mbarrier "acc full"
+//     on completion), then releases the slot of row y - 1, whose last reader
+//     this was;
+//   warps 0..3: the epilogue -- TMEM lanes 32w .. 32w + 31 (pixels of the
+//     tile), bias, ReLU, BF16/FP32 stores, then "acc empty".
+// Copies, MMAs and stores of different rows overlap; no CTA-wide barrier
+// inside the strip loop.  Every wait is bounded: a role that gives up sets
+// the timeout bit and an abort flag the other roles see, and the CTA waits
+// (bounded) for MMAs still in flight before it frees its tensor memory.
+constexpr int kConvRing = 6;                 // staged input row slots
+constexpr int kConvAcc = 4;                  // TMEM accumulators of 32 columns
+constexpr int kConvWsThreads = 192;          // 4 epilogue warps, producer warp, MMA warp
+
+__host__ __device__ inline size_t conv_ws_smem_bytes(int Cin, int Cout)
+{
+    const size_t row = (size_t)(Cin / 8) * kConvSlots * 16;          // a multiple of 128 bytes
+    const size_t b = (size_t)9 * (Cin / 8) * Cout * 16;
+    return 128 + kConvRing * row + b + 8 * (2 * kConvRing + 2 * kConvAcc + 1) + 16;   // + alignment slack
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_one(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, int limit, volatile int* abort_flag)
+{
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+// one 8-channel x kConvSlots-pixel box of input row y (tensor coordinates
+// channel c0, pixel x, row y, image n; zero fill outside the tensor)
+__device__ __forceinline__ void tma_load_row_chunk(uint32_t dst, const CUtensorMap* map, int c0, int x, int y, int n,
+                                                   uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(x), "r"(y), "r"(n), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constant__ CUtensorMap xmap, ConvArgs a)
 {
     extern __shared__ __align__(16) unsigned char csm[];
     const int C8 = a.Cin / 8;
-    const size_t row_bytes = (size_t)C8 * kConvSlots * 16;
-    const size_t a_bytes = kConvRows * row_bytes;
-    const size_t b_bytes = (size_t)9 * C8 * a.Cout * 16;
-    unsigned char* As = csm;
-    unsigned char* Bs = csm + a_bytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(csm + a_bytes + b_bytes);   // two
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 2);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t row_bytes = (uint32_t)C8 * kConvSlots * 16;
+    const uint32_t raw = smem_u32(csm);
+    const uint32_t base = (raw + 127u) & ~127u;                    // TMA destinations: 128-byte aligned
+    unsigned char* basep = csm + (base - raw);
+    const uint32_t ring = base;
+    const uint32_t b_base = ring + kConvRing * row_bytes;
+    unsigned char* Bs = basep + kConvRing * row_bytes;
+    const uint32_t bars = b_base + (uint32_t)(9 * C8 * a.Cout * 16);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(basep + (bars - base) + 8 * (2 * kConvRing + 2 * kConvAcc + 1));
+    __shared__ int s_abort;
+    auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bars + 8u * (uint32_t)(kConvRing + s); };
+    auto acc_full = [&](int b) { return bars + 8u * (uint32_t)(2 * kConvRing + b); };
+    auto acc_empty = [&](int b) { return bars + 8u * (uint32_t)(2 * kConvRing + kConvAcc + b); };
+    const uint32_t drain_bar = bars + 8u * (uint32_t)(2 * kConvRing + 2 * kConvAcc);   // the issuer's last MMAs
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // weights: B_tap[n][k] at tap * (C8 Cout 16) + chunk * (Cout 16) + n * 16
-    for (int idx = tid; idx < 9 * a.Cout * C8; idx += kConvThreads) {
+    for (int idx = tid; idx < 9 * a.Cout * C8; idx += kConvWsThreads) {
         const int c = idx % C8, n = (idx / C8) % a.Cout, tap = idx / (C8 * a.Cout);
         const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.Cout + n) * a.Cin + 8 * c);
         *reinterpret_cast<uint4*>(Bs + (size_t)tap * C8 * a.Cout * 16 + (size_t)c * a.Cout * 16 + n * 16) = v;
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
+        for (int s = 0; s < kConvRing; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
+        for (int b = 0; b < kConvAcc; ++b) { mbar_init(acc_full(b), 1); mbar_init(acc_empty(b), 4 * 32); }
+        mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(2 * kConvTmemCols)
+                     "r"(kConvAcc * kConvTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the weights, for the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
-    const uint32_t idesc = umma_idesc_bf16(a.Cout);
-    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-    const uint32_t mb[2] = {smem_u32(mbar), smem_u32(mbar + 1)};
-    uint32_t phase[2] = {0u, 0u};
+    volatile int* abort_flag = &s_abort;
     bool failed = false;
-    int pending = 0;                          // MMA groups issued and not yet waited for (0..2)
 
     const int strips_y = (a.H + a.strip - 1) / a.strip;
     const int n_strips = a.N * a.tiles_x * strips_y;
-    for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
-        const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
-        const int x0 = tx * kConvM, y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
-        for (int r = y_begin - 1; r <= y_begin + 1; ++r) conv_stage_row(a, As, C8, nn, r, x0, (r + 4) & 3);
-        for (int y = y_begin; y < y_end; ++y) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            const int buf = y & 1;
-            if (tid == 0 && !a.no_commit) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                int first = 1;
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap % 3;
-                    const uint32_t row_base = a_base + (uint32_t)(((y + dy - 1 + 4) & 3) * row_bytes);
-                    for (int s = 0; s < C8 / 2; ++s) {
-                        const uint32_t aa = row_base + (uint32_t)(2 * s * kConvSlots * 16 + dx * 16);
-                        const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * s * a.Cout * 16);
-                        umma_bf16(tmem + (uint32_t)(kConvTmemCols * buf), umma_desc(aa, kConvSlots * 16, 128),
-                                  umma_desc(bb, a.Cout * 16, 128), idesc, first ? 0 : 1);
-                        first = 0;
+    if (warp == 4) {
+        // ---------------- producer: input rows y_begin - 1 .. y_end of every strip
+        if (lane == 0) {
+            long long cnt = 0;
+            long long last_use[kConvRing];
+            for (int s = 0; s < kConvRing; ++s) last_use[s] = -1;
+            for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
+                const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
+                const int x0 = tx * kConvM, y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
+                for (int r = y_begin - 1; r <= y_end; ++r, ++cnt) {
+                    const int s = (int)(cnt % kConvRing);
+                    const long long use = cnt / kConvRing;
+                    if (use > 0 && !mbar_wait_or_abort(empty(s), (uint32_t)((use - 1) & 1), a.spin_limit, abort_flag)) {
+                        failed = true;
+                        break;
+                    }
+                    mbar_expect_tx(full(s), row_bytes);
+                    for (int c = 0; c < C8; ++c)
+                        tma_load_row_chunk(ring + (uint32_t)s * row_bytes + (uint32_t)(c * kConvSlots * 16), &xmap, 8 * c,
+                                           x0 - 1, r, nn, full(s));
+                    last_use[s] = use;
+                }
+            }
+            if (failed) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
+            // no copy may still be landing in shared memory when the CTA leaves
+            for (int s = 0; s < kConvRing; ++s)
+                if (last_use[s] >= 0) mbar_wait(full(s), (uint32_t)(last_use[s] & 1), a.spin_limit);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16(a.Cout);
+            long long cnt = 0;        // input rows, as the producer counts them
+            long long row = 0;        // output rows issued (accumulator ring)
+            for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
+                const int sy = t % strips_y;
+                const int y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
+                const long long first = cnt;                 // counter of input row y_begin - 1
+                cnt += (y_end - y_begin) + 2;
+                auto slot_of = [&](int r) { return (int)((first + (r - (y_begin - 1))) % kConvRing); };
+                auto use_of = [&](int r) { return (first + (r - (y_begin - 1))) / kConvRing; };
+                auto wait_row = [&](int r) {
+                    return mbar_wait_or_abort(full(slot_of(r)), (uint32_t)(use_of(r) & 1), a.spin_limit, abort_flag);
+                };
+                if (!wait_row(y_begin - 1) || !wait_row(y_begin)) { failed = true; break; }
+                for (int y = y_begin; y < y_end; ++y, ++row) {
+                    if (!wait_row(y + 1)) { failed = true; break; }
+                    const int b = (int)(row % kConvAcc);
+                    if (row >= kConvAcc &&
+                        !mbar_wait_or_abort(acc_empty(b), (uint32_t)(((row / kConvAcc) - 1) & 1), a.spin_limit,
+                                            abort_flag)) {
+                        failed = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (!a.no_commit) {
+                        int first_mma = 1;
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const int dy = tap / 3, dx = tap % 3;
+                            const uint32_t row_base = ring + (uint32_t)slot_of(y + dy - 1) * row_bytes;
+                            for (int k2 = 0; k2 < C8 / 2; ++k2) {
+                                const uint32_t aa = row_base + (uint32_t)(2 * k2 * kConvSlots * 16 + dx * 16);
+                                const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * k2 * a.Cout * 16);
+                                umma_bf16(tmem + (uint32_t)(kConvTmemCols * b), umma_desc(aa, kConvSlots * 16, 128),
+                                          umma_desc(bb, a.Cout * 16, 128), idesc, first_mma ? 0 : 1);
+                                first_mma = 0;
+                            }
+                        }
+                        umma_commit(acc_full(b));
+                        umma_commit(empty(slot_of(y - 1)));          // row y - 1: this was its last reader
+                        if (y == y_end - 1) {                        // the strip's last two rows
+                            umma_commit(empty(slot_of(y)));
+                            umma_commit(empty(slot_of(y + 1)));
+                        }
                     }
                 }
-                umma_commit(mb[buf]);
             }
-            ++pending;
-            if (y > y_begin) {
-                const int pb = buf ^ 1;
-                const bool done = mbar_wait(mb[pb], phase[pb], a.spin_limit);
-                if (!__syncthreads_and(done)) { failed = true; break; }
-                phase[pb] ^= 1u;
-                --pending;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                conv_epilogue(a, tmem, pb, nn, y - 1, x0);
-            }
-            if (y + 2 <= y_end) conv_stage_row(a, As, C8, nn, y + 2, x0, (y + 2) & 3);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (failed) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
+            // every MMA this thread issued has completed before the tensor memory is freed
+            umma_commit(drain_bar);
+            mbar_wait(drain_bar, 0u, a.spin_limit);
         }
-        if (failed) break;
-        // drain: the strip's last row
-        const int lb = (y_end - 1) & 1;
-        const bool done = mbar_wait(mb[lb], phase[lb], a.spin_limit);
-        if (!__syncthreads_and(done)) { failed = true; break; }
-        phase[lb] ^= 1u;
-        --pending;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        conv_epilogue(a, tmem, lb, nn, y_end - 1, x0);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // the next strip restages every slot and reuses both accumulators
+    } else {
+        // ---------------- epilogue: warps 0..3, TMEM lanes 32 warp .. 32 warp + 31
+        long long row = 0;
+        for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
+            const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
+            const int x0 = tx * kConvM, y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
+            for (int y = y_begin; y < y_end; ++y, ++row) {
+                const int b = (int)(row % kConvAcc);
+                const bool ok = mbar_wait_or_abort(acc_full(b), (uint32_t)((row / kConvAcc) & 1), a.spin_limit,
+                                                   abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                conv_epilogue(a, tmem, b, nn, y, x0);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive_one(acc_empty(b));
+            }
+        }
+        if (failed && lane == 0) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
     }
-    if (failed) {
-        if (tid == 0 && a.status) atomicOr(a.status, kStatusTimeout);
-        // a second bounded wait for the groups still in flight (oldest first)
-        for (int b = 0; b < 2 && pending > 0; ++b)
-            if (mbar_wait(mb[b], phase[b], a.spin_limit)) --pending;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kConvTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kConvAcc * kConvTmemCols)
                      : "memory");
     }
 }
