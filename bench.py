@@ -1227,6 +1227,7 @@ def main():
                     help="form of the update (skips the autotuner; for profiling)")
     ap.add_argument("--solve-tile", type=int, default=0, choices=[0, 16, 32],
                     help="tile edge of the solve launch (skips the autotuner; for profiling)")
+    ap.add_argument("--frames", type=int, default=16, help="conv workload: frames of 1024 x 1024 (profiling: fewer)")
     ap.add_argument("--workload", choices=["scene512", "batch", "surrogate", "conv"], default="scene512",
                     help="batch / surrogate: only that configuration, as its own line")
     args = ap.parse_args()
@@ -1274,7 +1275,7 @@ def run_conv_line(args):
     torch.cuda.set_device(local)
     sfbuild.build()
     dev = torch.device("cuda", local)
-    n, H, W, C = 16, 1024, 1024, 32
+    n, H, W, C = args.frames, 1024, 1024, 32
     g = torch.Generator(device=dev); g.manual_seed(5)
     x = (torch.randn((n, H, W, C), device=dev, generator=g) * 0.5).to(torch.bfloat16)
     w = (torch.randn((9, C, C), device=dev, generator=g) * 0.06).to(torch.bfloat16)
@@ -1310,7 +1311,7 @@ def run_conv_line(args):
     line = {"metric": "TFLOP/s of one surrogate layer", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "3x3 conv 32->32 + ReLU, NHWC bf16, 16 x 1024 x 1024, FP32 accumulation"},
+            "config": {"workload": f"3x3 conv 32->32 + ReLU, NHWC bf16, {n} x 1024 x 1024, FP32 accumulation"},
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": tf / peaks["bf16_tflops"], "traffic": None,
                          "peak_source": f"{kind} bf16_tflops (burst)"},

@@ -118,7 +118,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 }
 
 // TMEM buffer `buf` (output row yy) -> bias, ReLU, global memory
-__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int buf, int nn, int yy, int x0)
+// (bias: the layer's bias in registers, zero beyond Cout or without one)
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int buf, int nn, int yy, int x0,
+                                              const float* bias)
 {
     const int warp = threadIdx.x >> 5;
     float v[32];
@@ -129,7 +131,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, 
     float r[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const float u = v[k] + ((a.bias && k < a.Cout) ? a.bias[k] : 0.0f);
+        const float u = v[k] + bias[k];
         r[k] = a.relu ? fmaxf(u, 0.0f) : u;
     }
     if (a.y) {
@@ -362,6 +364,9 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
         }
     } else {
         // ---------------- epilogue: warps 0..3, TMEM lanes 32 warp .. 32 warp + 31
+        float bias[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) bias[k] = (a.bias && k < a.Cout) ? a.bias[k] : 0.0f;
         long long row = 0;
         for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
             const int sy = t % strips_y, tx = (t / strips_y) % a.tiles_x, nn = t / (strips_y * a.tiles_x);
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
                                                    abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                conv_epilogue(a, tmem, b, nn, y, x0);
+                conv_epilogue(a, tmem, b, nn, y, x0, bias);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive_one(acc_empty(b));
             }
