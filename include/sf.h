@@ -516,6 +516,14 @@ int sf_surrogate_propagate(sf_surrogate* s, const sf_grid* g, int n, int N, cons
 int sf_set_surrogate(sf_ctx* c, sf_surrogate* s);
 int sf_batch_set_surrogate(sf_batch* b, sf_surrogate* s);
 
+/* NVTX ranges (one per frame and one per stage launch: propagation,
+ * surrogate, its fallback check, solve, smoothing and reconstruction of each
+ * pyramid depth) for a system trace: enable != 0 turns them on for every
+ * filter and batch of the process, 0 (the default) off.  They mark the host
+ * side of each launch; with a tracing tool attached each costs microseconds
+ * of host time, so they are off unless asked for.  Always SF_OK. */
+int sf_set_trace(int enable);
+
 /* Threshold (px/frame, >= 0; +inf: never fall back) of the surrogate's
  * fallback: for a filter, or for batch stream s (s = -1: every stream, and
  * the default of later attachments).  Synchronous copy to the device; takes

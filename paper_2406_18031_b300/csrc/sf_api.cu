@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -82,10 +83,21 @@ int set_smem_attr(const void* fn, size_t bytes)
 int last_error() { return cudaGetLastError() == cudaSuccess ? SF_OK : SF_ECUDA; }
 
 // NVTX range around the host-side issue of one stage's launch (visible in a
-// system trace next to the kernel it issued; free when no tool is attached)
+// system trace next to the kernel it issued).  Off unless sf_set_trace(1):
+// with a tracing tool injected a range costs microseconds of host time, which
+// a 60-microsecond frame cannot hide.
+std::atomic<int> g_trace{0};
+
 struct NvtxRange {
-    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
+    const bool on;
+    explicit NvtxRange(const char* name) : on(g_trace.load(std::memory_order_relaxed) != 0)
+    {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxRange()
+    {
+        if (on) nvtxRangePop();
+    }
 };
 
 // The frame's kernels are launched with programmatic stream serialisation:
@@ -2296,6 +2308,12 @@ int engine_surr_stats(Engine& E, float* residual_px, int* fallbacks, int n)
 }
 
 }  // namespace
+
+int sf_set_trace(int enable)
+{
+    g_trace.store(enable != 0, std::memory_order_relaxed);
+    return SF_OK;
+}
 
 int sf_set_surrogate_threshold(sf_ctx* c, float threshold_px)
 {

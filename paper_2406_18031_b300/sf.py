@@ -51,7 +51,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
            "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
            "sf_batch_set_surrogate", "sf_set_surrogate_threshold", "sf_batch_set_surrogate_threshold",
-           "sf_surrogate_stats", "sf_batch_surrogate_stats"]
+           "sf_surrogate_stats", "sf_batch_surrogate_stats", "sf_set_trace"]
 
 
 def lib():
@@ -101,6 +101,7 @@ def lib():
         L.sf_surrogate_propagate.argtypes = [vp, P(CGrid), i, i, vp, vp, f, P(f), P(i), vp]
         L.sf_set_surrogate.argtypes = [vp, vp]
         L.sf_batch_set_surrogate.argtypes = [vp, vp]
+        L.sf_set_trace.argtypes = [i]
         L.sf_set_surrogate_threshold.argtypes = [vp, f]
         L.sf_batch_set_surrogate_threshold.argtypes = [vp, i, f]
         L.sf_surrogate_stats.argtypes = [vp, P(f), P(i)]
@@ -434,6 +435,11 @@ def conv3x3(x, w, bias=None, relu=False, y=None, y32=None, status=None, stream=N
                                    _tptr(bias, f32, Cout, "bias"), int(bool(relu)), _tptr(y, bf, m, "y"),
                                    _tptr(y32, f32, m, "y32"), _tptr(status, torch.int32, 1, "status"),
                                    _stream(stream)), "sf_conv3x3")
+
+
+def set_trace(enable):
+    """``sf_set_trace``: NVTX ranges around every frame and stage launch (off by default)."""
+    return _check(lib().sf_set_trace(int(bool(enable))), "sf_set_trace")
 
 
 def conv3x3_wgrad(x, dy, dw, db, stream=None):

@@ -424,3 +424,22 @@ def test_small_and_ragged_grids(H, W, levels):
     seq = scenes.plane64(frames=4, H=H, W=W, levels=levels, iters=[2] * levels)
     errs, _, _, _ = _run(seq, 4)
     assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+
+
+def test_trace_ranges_leave_results_unchanged():
+    # sf_set_trace(1) adds NVTX ranges around every frame and stage launch;
+    # the filter computes the same bits with and without them
+    seq = scenes.scene512(frames=3, H=64, W=96, max_flow=2.0, levels=2, iters=(2, 1), smooth=(2, 4))
+    H, W = seq.shape
+    outs = []
+    for trace in (True, False):
+        sf.set_trace(trace)
+        g, _ = _pair(seq)
+        flow = torch.empty((3, H, W), device="cuda")
+        for k in range(3):
+            g.step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(), seq.dt, flow)
+        torch.cuda.synchronize()
+        outs.append(flow.clone())
+        g.close()
+    sf.set_trace(False)
+    assert torch.equal(outs[0], outs[1])
