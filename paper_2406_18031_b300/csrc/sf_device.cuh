@@ -66,42 +66,6 @@ __device__ __forceinline__ Geo pixel_geometry(const Grid& g, int i, int j)
     return o;
 }
 
-// column-axis pixel speed u and row-axis pixel speed v of Eq. 54
-__device__ __forceinline__ float col_speed(const Geo& g, float wx, float wy, float wz)
-{
-    const float s = fmaf(g.ex, wx, fmaf(g.ey, wy, g.ez * wz));
-    return g.cu * fmaf(-g.ex, s, wx);
-}
-
-__device__ __forceinline__ float row_speed(const Geo& g, float wx, float wy, float wz)
-{
-    (void)wx;
-    return g.cu * fmaf(g.ez, wy, -g.ey * wz);
-}
-
-// dominant speed of Eqs. 55-56: the neighbour of larger |speed| (reading R1),
-// ties to the minus side; the literal text takes the smaller.
-__device__ __forceinline__ float dominant(float s_minus, float s_plus, int flags)
-{
-    const bool plus_larger = (fabsf(s_plus) - fabsf(s_minus)) > 0.0f;
-    if (flags & kDominantLiteral) return plus_larger ? s_minus : s_plus;
-    return plus_larger ? s_plus : s_minus;
-}
-
-// one explicit Euler step of one axis pass (Eqs. 59-66) for a field with the
-// source term: f - dt [speed D + f src]; split: the source with dt/2.
-__device__ __forceinline__ float advance_src(float f, float fn, float speed, float src, float dt, float sdt)
-{
-    const float D = speed > 0.0f ? f - fn : fn - f;
-    return f - (dt * (speed * D) + sdt * (f * src));
-}
-
-__device__ __forceinline__ float advance_nosrc(float f, float fn, float speed, float dt)
-{
-    const float D = speed > 0.0f ? f - fn : fn - f;
-    return f - dt * (speed * D);
-}
-
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream

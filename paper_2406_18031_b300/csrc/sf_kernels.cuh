@@ -77,23 +77,29 @@ __host__ __device__ inline int prop_warps(int nf_longest) { return nf_longest <=
 __host__ __device__ inline int prop_tile(int nf) { return kPrW - 2 * nf; }   // output tile width
 __host__ __device__ inline int prop_tile_h(int nf, int warps) { return kPrRows * warps - 2 * nf; }   // ... height
 
-// Published rows: slot 1 + 2w holds warp w's first row, slot 2 + 2w its last.
-// In the padded form (PE) slot 0 and the last slot repeat the region's first
-// and last rows (the row beyond a region edge is the edge row itself), so every
-// warp reads the rows above and below its own from fixed slots without a
-// select; the plain form selects the warp's own row at the region edges.  The
-// padded form saves ALU work in every sub-iteration but holds more registers
-// (spills around the load and store phases): launches whose longest job runs
-// at least kPrPaddedNf sub-iterations take it.
-__host__ __device__ inline int pub_slots(int warps) { return 2 * warps + 2; }
+// Published rows: in the plain form slot 2w holds warp w's first row and slot
+// 2w + 1 its last.  The padded form (PE) adds a slot before and after them that
+// repeats the region's first and last rows (the row beyond a region edge is
+// the edge row itself), so every warp reads the rows above and below its own
+// from fixed slots without a select; the plain form selects the warp's own row
+// at the region edges.  The padded form saves ALU work in every sub-iteration
+// but holds more registers (spills around the load and store phases):
+// launches whose longest job runs at least kPrPaddedNf sub-iterations take it.
+// (A second buffer of published rows, which would spare the barrier that
+// guards them until every warp has read them, measured 13% slower on the
+// 8-warp launches: two such CTAs leave the SM too little L1.)
+__host__ __device__ inline int pub_slots(int warps, bool pe) { return 2 * warps + (pe ? 2 : 0); }
 constexpr int kPrPaddedNf = 6;
 static_assert(kPrPaddedNf > kPrSmallNf, "the padded form runs with 16 warps only");
 
+// dynamic shared memory of a launch with CTAs of `warps` warps (the padded
+// form is possible with 16 warps only)
 __host__ __device__ inline size_t prop_smem_bytes(int warps)
 {
-    return (size_t)kPrRows * warps * kPrW * sizeof(float4)            // geometry
-           + 2 * (size_t)pub_slots(warps) * kPrW * sizeof(float4)     // published rows: s0, s1
-           + (size_t)pub_slots(warps) * kPrW * sizeof(float);         // published row speeds
+    const int slots = pub_slots(warps, warps == kPrWarpsMax);
+    return (size_t)kPrRows * warps * kPrW * sizeof(float4)                  // geometry
+           + 2 * (size_t)slots * kPrW * sizeof(float4)                      // published rows: s0, s1
+           + (size_t)slots * kPrW * sizeof(float);                          // ... and their speeds
 }
 
 struct PixGeo {
@@ -155,27 +161,39 @@ __device__ __forceinline__ float4 upwind4(float4 f, float4 fm, float4 fp, float 
 // one (Eqs. 55-56) is already v/2 with v = dt s-hat: km = max(v, 0) on the
 // minus side, kp = max(-v, 0) on the plus side, formed exactly as v/2 + |v/2|
 // and |v/2| - v/2 (adds, on the FMA pipe, where a max would load the busier
-// ALU pipe); hm, hp (1 or 0) drop the neighbour beyond the image border
-// (replicated border: D = 0).  kself = A - km - kp with A = 1 - sdt src.
-// cflm keeps the largest |v/2| of the pixels inside the output tile (cmask 1;
-// 0 outside) for the CFL test of Eq. 67 (|v| > 1), made once after the passes.
+// ALU pipe).  At the image border (BORDER) hm, hp (1 or 0) drop the neighbour
+// beyond it (replicated border: D = 0) and kself = A - km - kp with
+// A = 1 - sdt src; away from it km + kp = 2 |v/2| exactly, so kself =
+// A - 2 |v/2| in one FMA (the same value).  cflm keeps the largest |v/2| of
+// the pixels inside the output tile (cmask 1; 0 outside) for the CFL test of
+// Eq. 67 (|v| > 1), made once after the passes.
 struct Coef {
     float km, kp, kself, kselfy;
 };
 
-template <bool LITERAL>
-__device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, float hm, float hp, float src, float dt,
-                                             float sdt, float& cflm, float cmask)
+template <bool LITERAL, bool BORDER>
+__device__ __forceinline__ Coef coefficients(float s_minus, float s_plus, float hm, float hp, float src, float sdt,
+                                             float& cflm, float cmask)
 {
-    const float sh = dominant(s_minus, s_plus, LITERAL ? kDominantLiteral : 0);   // Eqs. 55-56
-    const float hv = sh;                                                        // v / 2
-    cflm = fmaxf(cflm, fabsf(hv) * cmask);
+    // Eqs. 55-56: |s+| > |s-| is (|s+| - |s-|) > 0 for IEEE floats with subnormals
+    const bool plus_larger = fabsf(s_plus) > fabsf(s_minus);
+    const float hv = (plus_larger != LITERAL) ? s_plus : s_minus;   // v / 2
+    const float av = fabsf(hv);
+    cflm = fmaxf(cflm, av * cmask);
     Coef k;
-    k.km = hm * (hv + fabsf(hv));                                               // Eqs. 57-58: backward difference
-    k.kp = hp * (fabsf(hv) - hv);
-    const float knb = k.km + k.kp;
-    k.kself = fmaf(-sdt, src, 1.0f) - knb;
-    k.kselfy = 1.0f - knb;
+    const float A = fmaf(-sdt, src, 1.0f);
+    if constexpr (BORDER) {
+        k.km = hm * (hv + av);                                                  // Eqs. 57-58: backward difference
+        k.kp = hp * (av - hv);
+        const float knb = k.km + k.kp;
+        k.kself = A - knb;
+        k.kselfy = 1.0f - knb;
+    } else {
+        k.km = hv + av;
+        k.kp = av - hv;
+        k.kself = fmaf(-2.0f, av, A);
+        k.kselfy = fmaf(-2.0f, av, 1.0f);
+    }
     return k;
 }
 
@@ -210,7 +228,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // wait for the completion of the mbarrier phase of the given parity; gives
-// up (false) after a bounded number of polls
+// up (false) after a bounded number of polls (a suspend-time hint on the
+// try_wait measured no faster)
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
     for (int n = 0; n < (1 << 22); ++n) {
@@ -234,13 +253,14 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     constexpr int kPrWarps = WARPS;
     constexpr int kPrH = kPrRows * WARPS;
     constexpr int kPrThreads = 32 * WARPS;
-    constexpr int kPubSlots = 2 * WARPS + 2;
+    constexpr int kSlots = 2 * WARPS + (PE ? 2 : 0);      // published-row slots
+    constexpr int kSlot0 = PE ? 1 : 0;                     // slot of warp 0's first row
     static_assert(!PE || WARPS == kPrWarpsMax, "the padded form runs with 16 warps only");
     extern __shared__ float4 smem4[];
     float4* geo = smem4;                                   // [kPrH][kPrW]
-    float4* pub0 = geo + kPrH * kPrW;                      // [kPubSlots][kPrW]
-    float4* pub1 = pub0 + kPubSlots * kPrW;
-    float* pubv = reinterpret_cast<float*>(pub1 + kPubSlots * kPrW);
+    float4* pub0 = geo + kPrH * kPrW;                      // [kSlots][kPrW]
+    float4* pub1 = pub0 + kSlots * kPrW;
+    float* pubv = reinterpret_cast<float*>(pub1 + kSlots * kPrW);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 wk = work[blockIdx.x];
@@ -260,6 +280,9 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     const int c0 = 2 * lane;                               // my region columns c0, c0 + 1
     const int j0 = ox + c0, j1 = j0 + 1;                   // ... image columns
     const int r0 = warp * kPrRows;                         // my first region row
+    // a region clear of the image border (every pixel has both neighbours on
+    // both axes inside the image) runs the passes without the border terms
+    const bool interior = ox >= 1 && oy >= 1 && ox + kPrW <= g.W - 1 && oy + kPrH <= g.H - 1;
 
     float4 a[kPrRows][2];       // (w, rho)
     float4 b[kPrRows][2];       // (dw, Y)
@@ -340,25 +363,34 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty), "r"(kPrThreads));
     }
     __syncthreads();
-    int ph = 0;
     bool timed_out = false;
 
-    auto colrow = [&](auto kc) {
-        constexpr int k = decltype(kc)::value;
+    // the nf sub-iterations; BORDER: the region touches the image border
+    auto passes = [&](auto border) {
+        constexpr bool BORDER = decltype(border)::value;
+        // column pass of my row k (Eqs. 59-62): neighbours in the adjacent lanes
+        auto colrow = [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
             const int r = r0 + k;
             const float uL = __shfl_up_sync(0xffffffffu, sp[k][1], 1);    // column c0 - 1
             const float uR = __shfl_down_sync(0xffffffffu, sp[k][0], 1);  // column c0 + 2
             const float4 G0 = geo[r * kPrW + lane], G1 = geo[r * kPrW + 32 + lane];
             const float src0 = fmaf(G0.x, a[k][0].x, fmaf(G0.y, a[k][0].y, G0.z * a[k][0].z));
             const float src1 = fmaf(G1.x, a[k][1].x, fmaf(G1.y, a[k][1].y, G1.z * a[k][1].z));
-            // replicated border: the neighbour beyond the image edge is the pixel itself
-            const bool m0 = j0 > 0, p0 = j0 < g.W - 1, m1 = j1 > 0, p1 = j1 < g.W - 1;
-            const float sm0 = m0 ? uL : sp[k][0], spp0 = p0 ? sp[k][1] : sp[k][0];
-            const float sm1 = m1 ? sp[k][0] : sp[k][1], spp1 = p1 ? uR : sp[k][1];
-            const Coef k0 = coefficients<LITERAL>(sm0, spp0, m0 ? 1.0f : 0.0f, p0 ? 1.0f : 0.0f, src0, dt, sdt,
-                                                  cflm[k], cmask[0]);
-            const Coef k1 = coefficients<LITERAL>(sm1, spp1, m1 ? 1.0f : 0.0f, p1 ? 1.0f : 0.0f, src1, dt, sdt,
-                                                  cflm[k], cmask[1]);
+            Coef k0, k1;
+            if constexpr (BORDER) {
+                // replicated border: the neighbour beyond the image edge is the pixel itself
+                const bool m0 = j0 > 0, p0 = j0 < g.W - 1, m1 = j1 > 0, p1 = j1 < g.W - 1;
+                const float sm0 = m0 ? uL : sp[k][0], spp0 = p0 ? sp[k][1] : sp[k][0];
+                const float sm1 = m1 ? sp[k][0] : sp[k][1], spp1 = p1 ? uR : sp[k][1];
+                k0 = coefficients<LITERAL, true>(sm0, spp0, m0 ? 1.0f : 0.0f, p0 ? 1.0f : 0.0f, src0, sdt, cflm[k],
+                                                 cmask[0]);
+                k1 = coefficients<LITERAL, true>(sm1, spp1, m1 ? 1.0f : 0.0f, p1 ? 1.0f : 0.0f, src1, sdt, cflm[k],
+                                                 cmask[1]);
+            } else {
+                k0 = coefficients<LITERAL, false>(uL, sp[k][1], 1.0f, 1.0f, src0, sdt, cflm[k], cmask[0]);
+                k1 = coefficients<LITERAL, false>(sp[k][0], uR, 1.0f, 1.0f, src1, sdt, cflm[k], cmask[1]);
+            }
             const float4 aL = shfl_up4(a[k][1]), aR = shfl_down4(a[k][0]);
             const float4 na0 = upwind4(a[k][0], aL, a[k][1], k0.km, k0.kp, k0.kself, k0.kself);
             const float4 na1 = upwind4(a[k][1], a[k][0], aR, k1.km, k1.kp, k1.kself, k1.kself);
@@ -371,106 +403,114 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             a[k][0] = na0; a[k][1] = na1;
             sp[k][0] = G0.w * fmaf(G0.z, na0.y, -G0.y * na0.z);   // v of Eq. 54 for the row pass
             sp[k][1] = G1.w * fmaf(G1.z, na1.y, -G1.y * na1.z);
-            };
-    using I0 = std::integral_constant<int, 0>;
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
-    using I3 = std::integral_constant<int, kPrRows - 1>;
-    for (int it = 0; it < nf; ++it, ++ph) {
-        // ---------------- column pass (Eqs. 59-62), neighbours in adjacent lanes:
-        // the two edge rows first, published while the middle rows run
-        colrow(I0{});
-        colrow(I3{});
-        if (ph > 0 && !mbar_wait_bounded(bar_empty, (uint32_t)(ph - 1) & 1u)) timed_out = true;
-        // publish my first and last rows for the neighbouring warps (padded form:
-        // the first and the last warp also fill the edge slots)
+        };
+        using I0 = std::integral_constant<int, 0>;
+        using I1 = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
+        using I3 = std::integral_constant<int, kPrRows - 1>;
+        for (int it = 0; it < nf; ++it) {
+            // ---------------- column pass: the two edge rows first, published while the middle rows run
+            colrow(I0{});
+            colrow(I3{});
+            if (it > 0 && !mbar_wait_bounded(bar_empty, (uint32_t)(it - 1) & 1u)) timed_out = true;
+            // publish my first and last rows for the neighbouring warps (padded form:
+            // the first and the last warp also fill the edge slots)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int k = e ? kPrRows - 1 : 0;
-            const int edge = !PE ? -1 : e == 0 ? (warp == 0 ? 0 : -1) : (warp == kPrWarps - 1 ? kPubSlots - 1 : -1);
+            for (int e = 0; e < 2; ++e) {
+                const int k = e ? kPrRows - 1 : 0;
+                const int edge = !PE ? -1 : e == 0 ? (warp == 0 ? 0 : -1) : (warp == kPrWarps - 1 ? kSlots - 1 : -1);
 #pragma unroll
-            for (int m = 0; m < (PE ? 2 : 1); ++m) {
-                const int slot = m ? edge : 1 + warp * 2 + e;
-                if (slot < 0) continue;                    // warp-uniform
-                const int base = slot * kPrW + lane;
-                pub0[base] = a[k][0]; pub0[base + 32] = a[k][1];
-                if (PE ? C8 : has1) { pub1[base] = b[k][0]; pub1[base + 32] = b[k][1]; }   // zeros at the top level
-                pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
+                for (int m = 0; m < (PE ? 2 : 1); ++m) {
+                    const int slot = m ? edge : kSlot0 + warp * 2 + e;
+                    if (slot < 0) continue;                    // warp-uniform
+                    const int base = slot * kPrW + lane;
+                    pub0[base] = a[k][0]; pub0[base + 32] = a[k][1];
+                    if (PE ? C8 : has1) { pub1[base] = b[k][0]; pub1[base + 32] = b[k][1]; }   // zeros at the top level
+                    pubv[base] = sp[k][0]; pubv[base + 32] = sp[k][1];
+                }
             }
-        }
-        mbar_arrive(bar_full);
-        colrow(I1{});
-        colrow(I2{});
-        if (!mbar_wait_bounded(bar_full, (uint32_t)ph & 1u)) timed_out = true;
-        // ---------------- row pass (Eqs. 63-66, reading R2), neighbours in rows k -+ 1
-        float4 prev_a[2], prev_b[2];
-        float prev_v[2];
-        if constexpr (PE) {   // the row above my first row: slot 2w (the warp above's last, or mine at the edge)
-            const int base = (2 * warp) * kPrW + lane;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                prev_a[q] = pub0[base + 32 * q];
-                prev_b[q] = C8 ? pub1[base + 32 * q] : b[0][q];
-                prev_v[q] = pubv[base + 32 * q];
-            }
-        } else {   // the last row of the warp above (or myself at the region edge)
-            const int base = (warp > 0 ? 2 * warp : 1) * kPrW + lane;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                prev_a[q] = warp > 0 ? pub0[base + 32 * q] : a[0][q];
-                prev_b[q] = (warp > 0 && has1) ? pub1[base + 32 * q] : b[0][q];
-                prev_v[q] = warp > 0 ? pubv[base + 32 * q] : sp[0][q];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kPrRows; ++k) {
-            const int r = r0 + k, i = oy + r;
-            float4 next_a[2], next_b[2];
-            float next_v[2];
-            if (k + 1 < kPrRows) {
-#pragma unroll
-                for (int q = 0; q < 2; ++q) { next_a[q] = a[k + 1][q]; next_b[q] = b[k + 1][q]; next_v[q] = sp[k + 1][q]; }
-            } else if constexpr (PE) {   // slot 2w + 3: the warp below's first row, or mine at the edge
-                const int base = (2 * warp + 3) * kPrW + lane;
+            mbar_arrive(bar_full);
+            colrow(I1{});
+            colrow(I2{});
+            if (!mbar_wait_bounded(bar_full, (uint32_t)it & 1u)) timed_out = true;
+            // ---------------- row pass (Eqs. 63-66, reading R2), neighbours in rows k -+ 1
+            float4 prev_a[2], prev_b[2];
+            float prev_v[2];
+            if constexpr (PE) {   // the row above my first row: the warp above's last, or mine at the edge
+                const int base = (2 * warp) * kPrW + lane;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    next_a[q] = pub0[base + 32 * q];
-                    next_b[q] = C8 ? pub1[base + 32 * q] : b[k][q];
-                    next_v[q] = pubv[base + 32 * q];
+                    prev_a[q] = pub0[base + 32 * q];
+                    prev_b[q] = C8 ? pub1[base + 32 * q] : b[0][q];
+                    prev_v[q] = pubv[base + 32 * q];
                 }
-                mbar_arrive(bar_empty);           // this thread has read the published rows
-            } else {   // the first row of the warp below (or myself at the region edge)
-                const bool below = warp + 1 < kPrWarps;
-                const int base = (below ? 2 * warp + 3 : 2 * warp + 2) * kPrW + lane;
+            } else {   // the last row of the warp above (or myself at the region edge)
+                const int base = (warp > 0 ? 2 * warp - 1 : 0) * kPrW + lane;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    next_a[q] = below ? pub0[base + 32 * q] : a[k][q];
-                    next_b[q] = (below && has1) ? pub1[base + 32 * q] : b[k][q];
-                    next_v[q] = below ? pubv[base + 32 * q] : sp[k][q];
+                    prev_a[q] = warp > 0 ? pub0[base + 32 * q] : a[0][q];
+                    prev_b[q] = (warp > 0 && has1) ? pub1[base + 32 * q] : b[0][q];
+                    prev_v[q] = warp > 0 ? pubv[base + 32 * q] : sp[0][q];
                 }
-                mbar_arrive(bar_empty);           // this thread has read the published rows
             }
-            const bool mi = i > 0, pi = i < g.H - 1;
-            float4 na[2], nb[2];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float4 G = geo[r * kPrW + q * 32 + lane];
-                const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
-                const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
-                const Coef kk = coefficients<LITERAL>(vm, vp, mi ? 1.0f : 0.0f, pi ? 1.0f : 0.0f, src, dt, sdt,
-                                                      cflm[k], cmask[q]);
-                na[q] = upwind4(a[k][q], prev_a[q], next_a[q], kk.km, kk.kp, kk.kself, kk.kself);
-                if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], kk.km, kk.kp, kk.kself, kk.kselfy);
-                if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
-                prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
-                a[k][q] = na[q];
-                if (has1) b[k][q] = nb[q];
-                // u of Eq. 54 for the next column pass
-                const float s = fmaf(G.x, na[q].x, fmaf(G.y, na[q].y, G.z * na[q].z));
-                sp[k][q] = G.w * fmaf(-G.x, s, na[q].x);
+            for (int k = 0; k < kPrRows; ++k) {
+                const int r = r0 + k;
+                float4 next_a[2], next_b[2];
+                float next_v[2];
+                if (k + 1 < kPrRows) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) { next_a[q] = a[k + 1][q]; next_b[q] = b[k + 1][q]; next_v[q] = sp[k + 1][q]; }
+                } else if constexpr (PE) {   // the warp below's first row, or mine at the edge
+                    const int base = (2 * warp + 3) * kPrW + lane;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        next_a[q] = pub0[base + 32 * q];
+                        next_b[q] = C8 ? pub1[base + 32 * q] : b[k][q];
+                        next_v[q] = pubv[base + 32 * q];
+                    }
+                    mbar_arrive(bar_empty);           // this thread has read the published rows
+                } else {   // the first row of the warp below (or myself at the region edge)
+                    const bool below = warp + 1 < kPrWarps;
+                    const int base = (below ? 2 * warp + 2 : 0) * kPrW + lane;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        next_a[q] = below ? pub0[base + 32 * q] : a[k][q];
+                        next_b[q] = (below && has1) ? pub1[base + 32 * q] : b[k][q];
+                        next_v[q] = below ? pubv[base + 32 * q] : sp[k][q];
+                    }
+                    mbar_arrive(bar_empty);           // this thread has read the published rows
+                }
+                float4 na[2], nb[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 G = geo[r * kPrW + q * 32 + lane];
+                    const float src = fmaf(G.x, a[k][q].x, fmaf(G.y, a[k][q].y, G.z * a[k][q].z));
+                    Coef kk;
+                    if constexpr (BORDER) {
+                        const int i = oy + r;
+                        const bool mi = i > 0, pi = i < g.H - 1;
+                        const float vm = mi ? prev_v[q] : sp[k][q], vp = pi ? next_v[q] : sp[k][q];
+                        kk = coefficients<LITERAL, true>(vm, vp, mi ? 1.0f : 0.0f, pi ? 1.0f : 0.0f, src, sdt, cflm[k],
+                                                         cmask[q]);
+                    } else {
+                        kk = coefficients<LITERAL, false>(prev_v[q], next_v[q], 1.0f, 1.0f, src, sdt, cflm[k], cmask[q]);
+                    }
+                    na[q] = upwind4(a[k][q], prev_a[q], next_a[q], kk.km, kk.kp, kk.kself, kk.kself);
+                    if (has1) nb[q] = upwind4(b[k][q], prev_b[q], next_b[q], kk.km, kk.kp, kk.kself, kk.kselfy);
+                    if (IMU) inertial_step(na[q], nb[q], has1, G.x, G.y, G.z, om, ac, dt);   // end of the sub-iteration
+                    prev_a[q] = a[k][q]; prev_b[q] = b[k][q]; prev_v[q] = sp[k][q];
+                    a[k][q] = na[q];
+                    if (has1) b[k][q] = nb[q];
+                    // u of Eq. 54 for the next column pass
+                    const float s = fmaf(G.x, na[q].x, fmaf(G.y, na[q].y, G.z * na[q].z));
+                    sp[k][q] = G.w * fmaf(-G.x, s, na[q].x);
+                }
             }
         }
-    }
+    };
+    if (interior) passes(std::false_type{});
+    else passes(std::true_type{});
 
     // write the output tile (its in-image part)
 #pragma unroll
