@@ -1308,6 +1308,27 @@ def run_conv_line(args):
         evw[k][1].record(stream)
     torch.cuda.synchronize()
     ms_w = sum(a.elapsed_time(c) for a, c in evw) / args.steps
+    # the whole network (features, four layers, head) on the same frames: the
+    # fused kernel (hidden activations in shared memory) and the layered form
+    net = sf.Surrogate(seed=11)
+    grid = sf.CGrid(H, W, 0.5 * W, 0.5 * W, 0.5 * W, 0.5 * H)
+    s0 = torch.zeros((n, H, W, 4), device=dev)
+    s0[..., :3] = torch.randn((n, H, W, 3), device=dev, generator=g) * 1e-3
+    s0[..., 3] = 0.3
+    p0 = torch.empty_like(s0)
+    net_flops = 2 * 9 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16) * n * H * W
+    net_ms = {}
+    for form in ("fused", "layered"):
+        for _ in range(3):
+            net.forward(grid, s0, p0, stream=stream, layered=form == "layered")
+        evn = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            evn[k][0].record(stream)
+            net.forward(grid, s0, p0, stream=stream, layered=form == "layered")
+            evn[k][1].record(stream)
+        torch.cuda.synchronize()
+        net_ms[form] = sum(a.elapsed_time(c) for a, c in evn) / args.steps
+    net.close()
     line = {"metric": "TFLOP/s of one surrogate layer", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -1320,6 +1341,13 @@ def run_conv_line(args):
                       "frac_of_bf16_peak": flops / (ms_w / 1e3) / 1e12 / peaks["bf16_tflops"],
                       "hbm_gbs_algorithmic": 2 * C * 2 * n * H * W / (ms_w / 1e3) / 1e9,
                       "kernel": "k_wgrad_tc (sf_conv3x3_wgrad), tensor cores, same layer"},
+            "network": {"workload": f"features + 4 layers (16-32-32-32-16) + head, {n} x 1024 x 1024",
+                        "flops_per_px": net_flops // (n * H * W),
+                        **{f"{f}_ms": v for f, v in net_ms.items()},
+                        **{f"{f}_tflops": net_flops / (v / 1e3) / 1e12 for f, v in net_ms.items()},
+                        "fused_frac_of_bf16_peak": net_flops / (net_ms["fused"] / 1e3) / 1e12 / peaks["bf16_tflops"],
+                        "kernels": "fused: k_surr_features + k_surr_net; layered: k_surr_features, 4 x k_conv3x3, "
+                                   "k_surr_head"},
             "gpu_launches": 2 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0

@@ -480,9 +480,18 @@ int sf_surrogate_params(sf_surrogate* s, float* host, int set);
 int sf_surrogate_grads(sf_surrogate* s, float* host);
 /* Predict: s0 = n frames of the grid g's top-level state (device
  * n x H x W float4 (w_x, w_y, w_z, rho), w in rad/frame) -> p0 (same layout).
- * Activation buffers grow on demand (about 450 bytes per pixel). */
+ * The four layers and the head run in one tensor-core kernel that keeps the
+ * hidden activations in shared memory (only the features, the state and
+ * the prediction touch HBM).  Activation buffers grow on demand (about 450
+ * bytes per pixel). */
 int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0,
                          void* stream);
+/* The same prediction computed layer by layer (the forward pass of
+ * sf_surrogate_train_step): every hidden activation goes to HBM as BF16 and
+ * back.  The same arithmetic at the same rounding points as
+ * sf_surrogate_forward; kept for comparison and measurement. */
+int sf_surrogate_forward_layered(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0,
+                                 void* stream);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8) on the mean squared error, over
  * the 4 used output channels in the network's units, between the
  * prediction from s0 and `target` (the plain propagation's p0 of the same

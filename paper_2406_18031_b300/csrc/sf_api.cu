@@ -1988,6 +1988,38 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
     return r;
 }
 
+// the features, then the whole network and the head in one launch
+// (k_surr_net): strips of kNetStrip output rows, halved while the launch
+// would still fill at most half the SMs; one CTA per SM walks the units
+int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, float4* p0, cudaStream_t st)
+{
+    const size_t px = (size_t)n * g.H * g.W;
+    k_surr_features<<<grid_stride_blocks(px), 256, 0, st>>>(g, n, s0, s->x0);
+    int r = last_error();
+    if (r) return r;
+    NetArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.N = n;
+    a.s0 = s0;
+    a.p0 = p0;
+    for (int l = 0; l < sf_surrogate::kL; ++l) {
+        a.w16[l] = s->w16[l];
+        a.bias[l] = s->param + s->off[l] + 9 * s->cin[l] * s->cout[l];
+    }
+    a.tiles_x = ceil_div(g.W, kNetValid);
+    a.spin_limit = kConvSpinLimit;
+    a.status = s->status;
+    a.strip = kNetStrip;
+    auto units = [&](int strip) { return (long)n * a.tiles_x * ceil_div(g.H, strip); };
+    while (a.strip > 16 && units(a.strip) * 2 <= kSmCount) a.strip /= 2;
+    CUtensorMap map;
+    if (conv_input_map(s->x0, n, g.H, g.W, kSurrIn, &map)) return SF_ECUDA;
+    if (set_smem_attr((const void*)k_surr_net, net_smem_bytes())) return SF_ECUDA;
+    k_surr_net<<<(int)std::min<long>(units(a.strip), kSmCount), kNetThreads, net_smem_bytes(), st>>>(map, a);
+    return last_error();
+}
+
 }  // namespace
 
 int sf_conv3x3_wgrad(int N, int H, int W, int Cin, int Cout, const void* x, const void* dy, float* dw, float* db,
@@ -2112,7 +2144,7 @@ int sf_surrogate_params(sf_surrogate* s, float* host, int set)
     return cudaDeviceSynchronize() == cudaSuccess ? SF_OK : SF_ECUDA;
 }
 
-int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0, void* stream)
+int sf_surrogate_forward_layered(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0, void* stream)
 {
     if (!s || !g || g->H < 1 || g->W < 1 || n < 1 || !s0 || !p0 || !aligned16(s0) || !aligned16(p0)) return SF_EINVAL;
     const size_t px = (size_t)n * g->H * g->W;
@@ -2125,6 +2157,17 @@ int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* 
         k_surr_head<<<grid_stride_blocks(px), 256, 0, st>>>(gg, n, (const float4*)s0, s->y32, (float4*)p0);
         r = last_error();
     }
+    return r;
+}
+
+int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0, void* stream)
+{
+    if (!s || !g || g->H < 1 || g->W < 1 || n < 1 || !s0 || !p0 || !aligned16(s0) || !aligned16(p0)) return SF_EINVAL;
+    const size_t px = (size_t)n * g->H * g->W;
+    if (px * kSurrHidden > 2147483647ull) return SF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = surrogate_capacity(s, px);
+    if (!r) r = net_forward(s, make_grid(*g), n, (const float4*)s0, (float4*)p0, st);
     return r;
 }
 

@@ -49,7 +49,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_batch_profile_read",
            "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_conv3x3_wgrad", "sf_selftest_conv_timeout", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
-           "sf_surrogate_forward", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
+           "sf_surrogate_forward", "sf_surrogate_forward_layered", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
            "sf_batch_set_surrogate", "sf_set_surrogate_threshold", "sf_batch_set_surrogate_threshold",
            "sf_surrogate_stats", "sf_batch_surrogate_stats", "sf_set_trace"]
 
@@ -97,6 +97,7 @@ def lib():
         L.sf_surrogate_params.argtypes = [vp, P(f), i]
         L.sf_surrogate_grads.argtypes = [vp, P(f)]
         L.sf_surrogate_forward.argtypes = [vp, P(CGrid), i, vp, vp, vp]
+        L.sf_surrogate_forward_layered.argtypes = [vp, P(CGrid), i, vp, vp, vp]
         L.sf_surrogate_train_step.argtypes = [vp, P(CGrid), i, vp, vp, f, P(f), vp]
         L.sf_surrogate_propagate.argtypes = [vp, P(CGrid), i, i, vp, vp, f, P(f), P(i), vp]
         L.sf_set_surrogate.argtypes = [vp, vp]
@@ -485,11 +486,13 @@ class Surrogate:
                "sf_surrogate_grads")
         return out
 
-    def forward(self, g: CGrid, s0, p0, stream=None):
-        """s0, p0: [n, H, W, 4] float32 CUDA tensors (top-level state, w in rad/frame)."""
+    def forward(self, g: CGrid, s0, p0, stream=None, layered=False):
+        """s0, p0: [n, H, W, 4] float32 CUDA tensors (top-level state, w in rad/frame).
+        layered: the layer-by-layer form (activations through HBM) instead of the fused kernel."""
         n = s0.shape[0] if s0.dim() == 4 else 1
-        return _check(lib().sf_surrogate_forward(self._h, ctypes.byref(g), n, _ptr(s0), _ptr(p0), _stream(stream)),
-                      "sf_surrogate_forward")
+        fn = lib().sf_surrogate_forward_layered if layered else lib().sf_surrogate_forward
+        return _check(fn(self._h, ctypes.byref(g), n, _ptr(s0), _ptr(p0), _stream(stream)),
+                      "sf_surrogate_forward_layered" if layered else "sf_surrogate_forward")
 
     def train_step(self, g: CGrid, s0, target, lr, stream=None):
         n = s0.shape[0] if s0.dim() == 4 else 1

@@ -48,17 +48,22 @@ def _layer_slices():
     return out
 
 
-def test_forward_matches_oracle():
-    rng = np.random.default_rng(1)
-    H, W = 40, 160
-    g, eta, B, dmu = gu.level_grid(H, W, 80.0, 80.0, 80.0, 20.0, 1)
+# the fused kernel (k_surr_net: tiles of 120 columns, strips of 16..64 rows)
+# and the layered form; 40 x 160: two tiles, the second ragged; 33 x 47: one
+# ragged tile shorter than a strip; 130 x 250, one frame: strips of 16 rows,
+# three tiles
+@pytest.mark.parametrize("form", ["fused", "layered"])
+@pytest.mark.parametrize("n,H,W", [(2, 40, 160), (3, 33, 47), (1, 130, 250)])
+def test_forward_matches_oracle(form, n, H, W):
+    rng = np.random.default_rng(1 + H)
+    g, eta, B, dmu = gu.level_grid(H, W, 0.5 * W, 0.5 * W, 0.5 * W, 0.5 * H, 1)
     net = sf.Surrogate(seed=3)
     p = net.params()
     p[-16 - 9 * 16 * 32:] *= 10.0          # a larger last layer than at creation: visible outputs
     net.set_params(p)
-    s0 = _states(rng, 2, H, W, dmu, eta, B, 1.5)
-    p0 = torch.empty_like(torch.from_numpy(s0)).cuda()
-    net.forward(g, torch.from_numpy(s0).cuda(), p0)
+    s0 = _states(rng, n, H, W, dmu, eta, B, 1.5)
+    p0 = torch.full(s0.shape, np.nan, device="cuda")
+    net.forward(g, torch.from_numpy(s0).cuda(), p0, layered=form == "layered")
     torch.cuda.synchronize()
     _, y = S.forward(S.features(eta, dmu, s0), p, q=S.bf16)
     ref = np.empty_like(s0, dtype=np.float64)
@@ -68,6 +73,31 @@ def test_forward_matches_oracle():
     tol = 2.0 ** -7 * np.abs(y[..., :4]).max() + 1e-4
     assert np.abs((got[..., 0:3] - ref[..., 0:3]) / (4 * dmu[None, ..., None])).max() <= tol
     assert np.abs(got[..., 3] - ref[..., 3]).max() <= tol
+
+
+@pytest.mark.parametrize("n,H,W", [(1, 1024, 1024), (2, 96, 312), (1, 8, 8)])
+def test_fused_forward_matches_layered(n, H, W):
+    # the same arithmetic at the same rounding points: the tensor cores' sums
+    # in the same order, bias and ReLU in float32, bfloat16 stores of the
+    # hidden activations (in shared memory instead of HBM), the same head
+    rng = np.random.default_rng(7 + W)
+    g, eta, B, dmu = gu.level_grid(H, W, 0.5 * W, 0.5 * W, 0.5 * W, 0.5 * H, 1)
+    net = sf.Surrogate(seed=5)
+    p = net.params()
+    p[-16 - 9 * 16 * 32:] *= 10.0
+    net.set_params(p)
+    s0 = torch.from_numpy(_states(rng, n, H, W, dmu, eta, B, 2.0)).cuda()
+    a = torch.full(s0.shape, np.nan, device="cuda")
+    b = torch.full(s0.shape, np.nan, device="cuda")
+    for _ in range(2):                      # twice: the second call reuses the buffers
+        net.forward(g, s0, a)
+        net.forward(g, s0, b, layered=True)
+    torch.cuda.synchronize()
+    assert torch.isfinite(a).all()
+    d = (a - b).abs().max().item()
+    scale = (b - s0).abs().max().item()
+    assert scale > 0
+    assert d <= 1e-6 * scale, (d, scale)
 
 
 def test_gradients_match_oracle():
