@@ -187,30 +187,36 @@ __global__ void k_surr_residual(const SurrResJob* __restrict__ jobs, const int4*
 // columns of a strip of output rows, keeping the hidden activations on chip:
 // the layered form writes and reads 3 x 64 bytes of BF16 activations per
 // pixel and layer through HBM, this form reads the features (32 bytes) and the
-// state (16) and writes the prediction (16).  Per step t of a strip the MMA
-// thread issues, into accumulator buffer t % kNetBuf (4 x 32 TMEM columns),
-//   layer 1 for row a = y_b - 3 + t   (input rows a - 1 .. a + 1, TMA ring)
-//   layer 2 for row a - L, layer 3 for row a - 2 L, layer 4 for row a - 3 L
-// (L = kNetLag) each from the three rows of the layer below that the steps
-// t - L - 1 .. t - L + 1 produced, so step t waits for the epilogue of step
-// t - (L - 1) only and L - 1 steps are in flight: the tensor cores work on
-// one step while the epilogue drains the one before and the hand-offs'
-// latency is hidden.  The epilogue warps add the bias, apply ReLU and write
-// a hidden row as BF16 into that layer's ring of kNetR rows in the
-// channel-chunk-major staging of k_conv3x3 (zero outside the image: the next
-// layer's zero padding), and turn layer 4's first four channels into the
-// prediction (k_surr_head's arithmetic).  Columns: layer l computes the 128
-// positions x0 - 5 + l + m (TMEM lane m); its A operand for tap dx is the row
-// below at slots dx + 1 .. dx + 128 (the input ring at dx .. dx + 127), so the
-// right end loses one valid column per layer and layer 4's positions x0 ..
-// x0 + 119 (lanes 1 .. 120) are exact.  Rows: a layer runs only on the rows
-// the strip's output depends on (layer l on [y_b - 4 + l, y_e + 4 - l)); rows
-// outside the image are zero rows.
+// state (16) and writes the prediction (16).
+//
+// The three vertical taps share one operand: an input row q of a layer feeds
+// output rows q - 1, q, q + 1 (taps dy = 2, 1, 0), so one MMA per horizontal
+// tap dx and 16-channel chunk, D[128 x 3 Cout] += A[128 x 16] B_dx[16 x 3 Cout]
+// with B_dx the three dy blocks side by side, accumulates all three.  (An MMA
+// of N = Cout = 32 costs about as much as one of N = 96: the issue of the
+// 128 x 16 A tile dominates, so reading it once instead of three times is the
+// saving.)  Each layer's output rows accumulate in a ring of four blocks of
+// tensor memory (row x in block x mod 4, blocks Cout columns wide); the three
+// blocks of input row q are contiguous unless the ring wraps, where the MMA
+// is split in two.  A row is complete after input row x + 1; the epilogue
+// then drains it (bias, ReLU, BF16) into the layer's two-row ring in shared
+// memory, in the channel-chunk-major staging of k_conv3x3 (zero outside the
+// image: the next layer's zero padding), and zeroes its block, which row
+// x + 4 first reaches two steps later.  Per step t of a strip the MMA thread
+// issues layer l for its input row q_l = y_b - 4 - 3 l + t (layer 1 reads
+// the TMA ring of features, layer l > 1 the row that layer l - 1 completed
+// at step t - 2), so step t waits for the epilogue of step t - 2 only.
+// Layer 4's first four channels become the prediction (k_surr_head's
+// arithmetic).  Columns: layer l computes the 128 positions x0 - 5 + l + m
+// (TMEM lane m); its A operand for tap dx is the row below at slots dx + 1 ..
+// dx + 128 (the input ring at dx .. dx + 127), so the right end loses one
+// valid column per layer and layer 4's positions x0 .. x0 + 119 (lanes 1 ..
+// 120) are exact.  Rows: layer l consumes the input rows [y_b - 4 + l,
+// y_e + 4 - l) the strip's output depends on; input rows outside the image
+// are zero rows and need no MMA.
 constexpr int kNetValid = 120;        // output columns of a tile
-constexpr int kNetLag = 4;            // rows between consecutive layers' rows of a step
-constexpr int kNetBuf = 4;            // accumulator buffers (steps in tensor memory)
-constexpr int kNetR = kNetLag + 1;    // rows of each hidden layer's ring
-constexpr int kNetIR = 6;             // input rows in flight
+constexpr int kNetIR = 8;             // input rows in flight
+constexpr int kNetHR = 2;             // rows of each hidden layer's ring in shared memory
 constexpr int kNetStrip = 64;         // the longest strip of output rows
 constexpr int kNetThreads = 192;      // 4 epilogue warps, producer warp, MMA warp
 constexpr int kNetInRow = (kSurrIn / 8) * kConvSlots * 16;         // bytes of a staged input row
@@ -219,13 +225,13 @@ constexpr int kNetW1 = 9 * (kSurrIn / 8) * kSurrHidden * 16;
 constexpr int kNetW2 = 9 * (kSurrHidden / 8) * kSurrHidden * 16;
 constexpr int kNetW4 = 9 * (kSurrHidden / 8) * kSurrOut * 16;
 constexpr int kNetBias = 3 * kSurrHidden + kSurrOut;               // floats
-constexpr int kNetBars = 2 * kNetIR + 2 * kNetBuf + 1;
-constexpr int kNetTmemCols = 128 * kNetBuf;   // buffers x 4 layers x 32 columns
-static_assert(kNetTmemCols <= 512 && kNetBuf >= kNetLag - 1, "a step's buffer is free once step t - (lag - 1) is drained");
+constexpr int kNetBars = 2 * kNetIR + 2 + 2 + 1;
+constexpr int kNetRing = 4;           // output-row blocks of each layer in tensor memory
+constexpr int kNetTmemCols = 512;     // 3 layers x 4 x 32 columns + 4 x 16 (448 used)
 
 __host__ __device__ constexpr size_t net_smem_bytes()
 {
-    return 128 + (size_t)kNetIR * kNetInRow + 3 * (size_t)kNetR * kNetHidRow + kNetW1 + 2 * kNetW2 + kNetW4 +
+    return 128 + (size_t)kNetIR * kNetInRow + 3 * (size_t)kNetHR * kNetHidRow + kNetW1 + 2 * kNetW2 + kNetW4 +
            4 * kNetBias + 8 * kNetBars + 16;
 }
 
@@ -254,6 +260,31 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v)
     for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// zero 32 (X32) or 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+template <bool X32>
+__device__ __forceinline__ void tmem_zero(uint32_t taddr)
+{
+    const uint32_t z = 0u;
+    if constexpr (X32)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1};" ::"r"(taddr), "r"(z)
+            : "memory");
+}
+
+// TMEM column of layer l's block for row x (4 blocks of Cout columns per layer)
+__device__ __forceinline__ uint32_t net_block_col(int l, int x)
+{
+    const int blk = ((x % kNetRing) + kNetRing) % kNetRing;
+    return l < 3 ? (uint32_t)(l * kNetRing * kSurrHidden + blk * kSurrHidden)
+                 : (uint32_t)(3 * kNetRing * kSurrHidden + blk * kSurrOut);
+}
+
 __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant__ CUtensorMap xmap, NetArgs a)
 {
     extern __shared__ __align__(16) unsigned char nsm[];
@@ -261,8 +292,8 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     const uint32_t base = (raw + 127u) & ~127u;                    // TMA destinations: 128-byte aligned
     unsigned char* basep = nsm + (base - raw);
     const uint32_t ring_in = base;
-    const uint32_t ring_h = ring_in + kNetIR * kNetInRow;          // 3 layers x kNetR rows
-    const uint32_t wb = ring_h + 3 * kNetR * kNetHidRow;
+    const uint32_t ring_h = ring_in + kNetIR * kNetInRow;          // 3 layers x kNetHR rows
+    const uint32_t wb = ring_h + 3 * kNetHR * kNetHidRow;
     unsigned char* wbp = basep + (wb - base);
     const uint32_t wofs[4] = {0u, (uint32_t)kNetW1, (uint32_t)(kNetW1 + kNetW2), (uint32_t)(kNetW1 + 2 * kNetW2)};
     float* bias_s = reinterpret_cast<float*>(wbp + kNetW1 + 2 * kNetW2 + kNetW4);
@@ -272,20 +303,21 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     auto in_full = [&](int s) { return bars + 8u * (uint32_t)s; };
     auto in_empty = [&](int s) { return bars + 8u * (uint32_t)(kNetIR + s); };
     auto acc_full = [&](int b) { return bars + 8u * (uint32_t)(2 * kNetIR + b); };
-    auto epi_done = [&](int b) { return bars + 8u * (uint32_t)(2 * kNetIR + kNetBuf + b); };
-    const uint32_t drain_bar = bars + 8u * (uint32_t)(2 * kNetIR + 2 * kNetBuf);
+    auto epi_done = [&](int b) { return bars + 8u * (uint32_t)(2 * kNetIR + 2 + b); };
+    const uint32_t drain_bar = bars + 8u * (uint32_t)(2 * kNetIR + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cin[4] = {kSurrIn, kSurrHidden, kSurrHidden, kSurrHidden};
-    const int cout[4] = {kSurrHidden, kSurrHidden, kSurrHidden, kSurrOut};
 
-    // weights: layer l, B_tap[n][k] at wofs[l] + tap (C8 Cout 16) + chunk (Cout 16) + n 16; biases
+    // weights: layer l, tap (dy, dx): B_dx[n][k] with n = (2 - dy) Cout + co, at
+    // wofs[l] + dx (C8 3 Cout 16) + chunk (3 Cout 16) + n 16; biases
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        const int C8 = cin[l] / 8, Co = cout[l];
+        const int Ci = l == 0 ? kSurrIn : kSurrHidden, Co = l == 3 ? kSurrOut : kSurrHidden, C8 = Ci / 8;
         for (int idx = tid; idx < 9 * Co * C8; idx += kNetThreads) {
-            const int c = idx % C8, n = (idx / C8) % Co, tap = idx / (C8 * Co);
-            const uint4 v = *reinterpret_cast<const uint4*>(a.w16[l] + ((size_t)tap * Co + n) * cin[l] + 8 * c);
-            *reinterpret_cast<uint4*>(wbp + wofs[l] + (size_t)tap * C8 * Co * 16 + (size_t)c * Co * 16 + n * 16) = v;
+            const int c = idx % C8, co = (idx / C8) % Co, tap = idx / (C8 * Co);
+            const int dy = tap / 3, dx = tap % 3;
+            const uint4 v = *reinterpret_cast<const uint4*>(a.w16[l] + ((size_t)tap * Co + co) * Ci + 8 * c);
+            *reinterpret_cast<uint4*>(wbp + wofs[l] + (size_t)dx * C8 * 3 * Co * 16 + (size_t)c * 3 * Co * 16 +
+                                      (size_t)((2 - dy) * Co + co) * 16) = v;
         }
     }
     for (int k = tid; k < kNetBias; k += kNetThreads) {
@@ -295,7 +327,7 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     }
     if (tid == 0) {
         for (int s = 0; s < kNetIR; ++s) { mbar_init(in_full(s), 1); mbar_init(in_empty(s), 1); }
-        for (int b = 0; b < kNetBuf; ++b) { mbar_init(acc_full(b), 1); mbar_init(epi_done(b), 4 * 32); }
+        for (int b = 0; b < 2; ++b) { mbar_init(acc_full(b), 1); mbar_init(epi_done(b), 4 * 32); }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
@@ -311,6 +343,19 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
+    // every output-row block starts at zero (the MMAs only accumulate)
+    if (warp < 4) {
+        const uint32_t lanes = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int x = 0; x < kNetRing; ++x) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) tmem_zero<true>(lanes + net_block_col(l, x));
+            tmem_zero<false>(lanes + net_block_col(3, x));
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     volatile int* abort_flag = &s_abort;
     bool failed = false;
     const Grid& g = a.g;
@@ -318,11 +363,10 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
 
     const int strips_y = (H + a.strip - 1) / a.strip;
     const int n_units = a.N * a.tiles_x * strips_y;
-    // needed rows of layer l (0-based) at step t of a strip of S rows: rows
-    // a - L l (L = kNetLag) with t in [(L + 1) l, S + 6 + (L - 1) l); a strip takes
-    // S + 6 + 3 (L - 1) steps
-    auto needed = [](int l, int t, int S) { return t >= (kNetLag + 1) * l && t < S + 6 + (kNetLag - 1) * l; };
-    constexpr int kTail = 6 + 3 * (kNetLag - 1);
+    // layer l (0-based) consumes input row q = y_b - 4 - 3 l + t at step t of a
+    // strip of S rows when t is in [4 l, S + 8 + 2 l); a strip takes S + 14 steps
+    auto active = [](int l, int t, int S) { return t >= 4 * l && t < S + 8 + 2 * l; };
+    constexpr int kTail = 14;
     if (warp == 4) {
         // ---------------- producer: input rows y_b - 4 .. y_e + 3 of every strip
         if (lane == 0) {
@@ -355,30 +399,29 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
         if (lane == 0) {
             long long cnt = 0;        // input rows, as the producer counts them
             long long gs = 0;         // steps, as the epilogue counts them
+            const uint64_t a_hi = umma_desc(0u, kConvSlots * 16, 128) & 0xFFFFFFFF00000000ull;
             for (int u = blockIdx.x; u < n_units && !failed; u += gridDim.x) {
                 const int sy = u % strips_y;
                 const int y_b = sy * a.strip, S = min(H, y_b + a.strip) - y_b;
                 const long long first = cnt;
                 cnt += S + 8;
                 auto in_slot = [&](int r) { return (int)((first + r) % kNetIR); };
-                auto in_ready = [&](int r) {
-                    return mbar_wait_or_abort(in_full(in_slot(r)), (uint32_t)(((first + r) / kNetIR) & 1), a.spin_limit,
-                                              abort_flag);
-                };
-                if (!in_ready(0) || !in_ready(1)) { failed = true; break; }
                 for (int t = 0; t < S + kTail; ++t, ++gs) {
-                    const int b = (int)(gs % kNetBuf);
-                    if (t < S + 6 && !in_ready(t + 2)) { failed = true; break; }
-                    // the hidden rows this step reads were written by the epilogues up to step
-                    // t - (L - 1), which also frees this step's accumulator buffer
-                    const long long dep = gs - (kNetLag - 1);
-                    if (dep >= 0 && !mbar_wait_or_abort(epi_done((int)(dep % kNetBuf)), (uint32_t)((dep / kNetBuf) & 1),
-                                                        a.spin_limit, abort_flag)) {
+                    const int b = (int)(gs & 1);
+                    if (t < S + 8 &&
+                        !mbar_wait_or_abort(in_full(in_slot(t)), (uint32_t)(((first + t) / kNetIR) & 1), a.spin_limit,
+                                            abort_flag)) {
+                        failed = true;
+                        break;
+                    }
+                    // the hidden rows this step reads and the blocks it starts were
+                    // finished by the epilogue of step t - 2
+                    if (gs >= 2 &&
+                        !mbar_wait_or_abort(epi_done(b), (uint32_t)(((gs >> 1) - 1) & 1), a.spin_limit, abort_flag)) {
                         failed = true;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int ra = y_b - 3 + t;          // layer 1's row
                     // descriptors: the low word carries the start address >> 4 (below 2^14:
                     // shared memory < 256 KB), so an operand at a fixed byte offset from a
                     // row's start is the row's low word plus offset / 16 -- an add per MMA
@@ -386,28 +429,31 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                         constexpr int l = decltype(lc)::value;
                         constexpr int C8 = (l == 0 ? kSurrIn : kSurrHidden) / 8;
                         constexpr int Co = l == 3 ? kSurrOut : kSurrHidden;
-                        const int row = ra - kNetLag * l;
-                        if (!needed(l, t, S) || row < 0 || row >= H) return;   // zero rows need no MMA
-                        const uint32_t idesc = umma_idesc_bf16(Co);
-                        const uint32_t d = tmem + (uint32_t)(b * 128 + 32 * l);
-                        uint32_t alo[3];
+                        constexpr int NW = 3 * Co;
+                        const int q = y_b - 4 - 3 * l + t;                // the input row of this step
+                        if (!active(l, t, S) || q < 0 || q >= H) return;  // zero rows need no MMA
+                        // the row below: the features row t of the input ring, or the hidden row
+                        // that layer l - 1 completed at step t - 2 (its ring slot t % kNetHR)
+                        const uint32_t src = l == 0 ? ring_in + (uint32_t)in_slot(t) * kNetInRow
+                                                    : ring_h + (uint32_t)((l - 1) * kNetHR + t % kNetHR) * kNetHidRow + 16u;
+                        const uint32_t alo = (uint32_t)umma_desc(src, kConvSlots * 16, 128);
+                        const uint64_t bd = umma_desc(wb + wofs[l], NW * 16, 128);
+                        // output rows q - 1, q, q + 1 in blocks (q - 1) mod 4 ..: one MMA of N = 3 Cout,
+                        // or two where the ring wraps (B rows brow .. brow + n of the stacked taps)
+                        const int fb = (((q - 1) % kNetRing) + kNetRing) % kNetRing;
+                        uint32_t col0 = net_block_col(l, q - 1), col1 = 0;
+                        int n0 = NW, n1 = 0, brow1 = 0;
+                        if (fb == 2) { n0 = 2 * Co; n1 = Co; brow1 = 2 * Co; col1 = net_block_col(l, q + 1); }
+                        if (fb == 3) { n0 = Co; n1 = 2 * Co; brow1 = Co; col1 = net_block_col(l, q); }
+                        const uint32_t id0 = umma_idesc_bf16(n0), id1 = umma_idesc_bf16(n1 ? n1 : 16);
 #pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            // the row below: input row (t + dy) of the ring, or the hidden row of step t - L - 1 + dy
-                            const uint32_t src = l == 0 ? ring_in + (uint32_t)in_slot(t + dy) * kNetInRow
-                                                        : ring_h + (uint32_t)((l - 1) * kNetR + (t - kNetLag - 1 + dy + kNetR) % kNetR) *
-                                                                       kNetHidRow + 16u;
-                            alo[dy] = (uint32_t)umma_desc(src, kConvSlots * 16, 128);
-                        }
-                        const uint64_t a_hi = umma_desc(0u, kConvSlots * 16, 128) & 0xFFFFFFFF00000000ull;
-                        const uint64_t bd = umma_desc(wb + wofs[l], Co * 16, 128);
-#pragma unroll
-                        for (int tap = 0; tap < 9; ++tap) {
+                        for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                             for (int k2 = 0; k2 < C8 / 2; ++k2) {
-                                const uint64_t ad = a_hi | (uint64_t)(alo[tap / 3] + (uint32_t)(tap % 3 + 2 * k2 * kConvSlots));
-                                const uint64_t bb = bd + (uint64_t)(tap * C8 * Co + 2 * k2 * Co);
-                                umma_bf16(d, ad, bb, idesc, tap == 0 && k2 == 0 ? 0 : 1);
+                                const uint64_t ad = a_hi | (uint64_t)(alo + (uint32_t)(dx + 2 * k2 * kConvSlots));
+                                const uint64_t bb = bd + (uint64_t)(dx * C8 * NW + 2 * k2 * NW);
+                                umma_bf16(tmem + col0, ad, bb, id0, 1);
+                                if (n1) umma_bf16(tmem + col1, ad, bb + (uint64_t)brow1, id1, 1);
                             }
                         }
                     };
@@ -416,7 +462,7 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                     layer(std::integral_constant<int, 2>{});
                     layer(std::integral_constant<int, 3>{});
                     umma_commit(acc_full(b));
-                    if (t < S + 8) umma_commit(in_empty(in_slot(t)));   // input row t: this step was its last reader
+                    if (t < S + 8) umma_commit(in_empty(in_slot(t)));   // input row t: this step was its reader
                 }
             }
             if (failed) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
@@ -426,56 +472,70 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     } else {
         // ---------------- epilogue: warps 0..3, TMEM lane m = 32 warp + lane
         const int m = 32 * warp + lane;
+        const uint32_t lanes = tmem + ((uint32_t)(32 * warp) << 16);
         long long gs = 0;
         for (int u = blockIdx.x; u < n_units && !failed; u += gridDim.x) {
             const int sy = u % strips_y, tx = (u / strips_y) % a.tiles_x, nn = u / (strips_y * a.tiles_x);
             const int x0 = tx * kNetValid, y_b = sy * a.strip, S = min(H, y_b + a.strip) - y_b;
             for (int t = 0; t < S + kTail; ++t, ++gs) {
-                const int b = (int)(gs % kNetBuf);
-                const bool ok = mbar_wait_or_abort(acc_full(b), (uint32_t)((gs / kNetBuf) & 1), a.spin_limit, abort_flag);
+                const int b = (int)(gs & 1);
+                const bool ok = mbar_wait_or_abort(acc_full(b), (uint32_t)((gs >> 1) & 1), a.spin_limit, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int ra = y_b - 3 + t;
-                const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * 128);
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
-                    if (!needed(l, t, S)) continue;                       // warp-uniform
-                    const int row = ra - kNetLag * l;
-                    const int px = x0 - 4 + l + m;                        // this lane's position
-                    const bool in_row = row >= 0 && row < H;              // warp-uniform
-                    float v[32];
-                    if (in_row) tmem_ld32(lane_addr + (uint32_t)(32 * l), v);
-                    const bool in_img = in_row && px >= 0 && px < W;
-                    const float4* bl = reinterpret_cast<const float4*>(bias_s + 32 * l);
-                    unsigned char* dst = basep + (ring_h - base) + (size_t)(l * kNetR + t % kNetR) * kNetHidRow +
-                                         (size_t)(m + 1) * 16;
+                    if (!active(l, t, S)) continue;                      // warp-uniform
+                    const int q = y_b - 4 - 3 * l + t, x = q - 1;         // x: the row this step completed
+                    if (t >= 4 * l + 2) {                                 // a row the next layer reads
+                        const bool in_row = x >= 0 && x < H;              // warp-uniform
+                        float v[32];
+                        if (in_row) tmem_ld32(lanes + net_block_col(l, x), v);
+                        const int px = x0 - 4 + l + m;                    // this lane's position
+                        const bool in_img = in_row && px >= 0 && px < W;
+                        const float4* bl = reinterpret_cast<const float4*>(bias_s + 32 * l);
+                        unsigned char* dst = basep + (ring_h - base) + (size_t)(l * kNetHR + t % kNetHR) * kNetHidRow +
+                                             (size_t)(m + 1) * 16;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float4 b0 = bl[2 * c], b1 = bl[2 * c + 1];
-                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                        float r[8];
+                        for (int c = 0; c < 4; ++c) {
+                            const float4 b0 = bl[2 * c], b1 = bl[2 * c + 1];
+                            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                            float r[8];
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) r[k] = in_img ? fmaxf(v[8 * c + k] + bb[k], 0.0f) : 0.0f;
-                        *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16) =
-                            make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]), pack_bf16x2(r[4], r[5]),
-                                       pack_bf16x2(r[6], r[7]));
+                            for (int k = 0; k < 8; ++k) r[k] = in_img ? fmaxf(v[8 * c + k] + bb[k], 0.0f) : 0.0f;
+                            *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16) =
+                                make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]), pack_bf16x2(r[4], r[5]),
+                                           pack_bf16x2(r[6], r[7]));
+                        }
+                    }
+                    tmem_zero<true>(lanes + net_block_col(l, x));        // row x + 4 starts here in two steps
+                    if (t == S + 7 + 2 * l) {                             // the strip's last input row of this layer:
+                        tmem_zero<true>(lanes + net_block_col(l, q));     // rows q and q + 1 stay partial
+                        tmem_zero<true>(lanes + net_block_col(l, q + 1));
                     }
                 }
-                if (needed(3, t, S)) {
-                    const int row = ra - 3 * kNetLag;                     // in [y_b, y_e)
-                    float o[4];
-                    tmem_ld4(lane_addr + 96u, o);
-                    const int px = x0 - 1 + m;
-                    if (m >= 1 && m <= kNetValid && px < W) {
-                        const float4 bl = *reinterpret_cast<const float4*>(bias_s + 96);
-                        const size_t pi = ((size_t)nn * H + row) * W + px;
-                        const float dd = kSurrFlowScale * pixel_dmu(pixel_geometry(g, row, px));
-                        const float4 f = a.s0[pi];
-                        a.p0[pi] = make_float4(fmaf(dd, o[0] + bl.x, f.x), fmaf(dd, o[1] + bl.y, f.y),
-                                               fmaf(dd, o[2] + bl.z, f.z), f.w + (o[3] + bl.w));
+                if (active(3, t, S)) {
+                    const int q = y_b - 13 + t, x = q - 1;
+                    if (t >= 14) {                                        // x in [y_b, y_e): the prediction
+                        float o[4];
+                        tmem_ld4(lanes + net_block_col(3, x), o);
+                        const int px = x0 - 1 + m;
+                        if (m >= 1 && m <= kNetValid && px < W) {
+                            const float4 bl = *reinterpret_cast<const float4*>(bias_s + 96);
+                            const size_t pi = ((size_t)nn * H + x) * W + px;
+                            const float dd = kSurrFlowScale * pixel_dmu(pixel_geometry(g, x, px));
+                            const float4 f = a.s0[pi];
+                            a.p0[pi] = make_float4(fmaf(dd, o[0] + bl.x, f.x), fmaf(dd, o[1] + bl.y, f.y),
+                                                   fmaf(dd, o[2] + bl.z, f.z), f.w + (o[3] + bl.w));
+                        }
+                    }
+                    tmem_zero<false>(lanes + net_block_col(3, x));
+                    if (t == S + 13) {
+                        tmem_zero<false>(lanes + net_block_col(3, q));
+                        tmem_zero<false>(lanes + net_block_col(3, q + 1));
                     }
                 }
-                // the hidden rows, for the tensor cores (async proxy); the accumulators are free
+                // the zeros have landed, the hidden rows are visible to the tensor cores
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive_one(epi_done(b));
