@@ -49,9 +49,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "8def6e878b5d00b7",
-    "scene512_k_propagate_bytes": 9_483_520 + 1_280,
-    "batch_k_propagate_bytes": 1_070_273_792 + 1_021_769_472,
+    "kernel_sources_sha256_16": "1564c7329668f78e",
+    "scene512_k_propagate_bytes": 9_507_072 + 4_096,
+    "batch_k_propagate_bytes": 1_070_214_400 + 1_022_731_520,
 }
 
 
