@@ -1990,7 +1990,9 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
 
 // the features, then the whole network and the head in one launch
 // (k_surr_net): strips of kNetStrip output rows, halved while the launch
-// would still fill at most half the SMs; one CTA per SM walks the units
+// would still fill at most half the SMs (down to 16); one CTA per SM walks
+// the units.  Measured on 16 frames of 1024 x 1024: strips of 64, 128 and 256
+// rows ran 2.31, 2.21 and 2.16 ms
 int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, float4* p0, cudaStream_t st)
 {
     const size_t px = (size_t)n * g.H * g.W;

@@ -217,7 +217,7 @@ __global__ void k_surr_residual(const SurrResJob* __restrict__ jobs, const int4*
 constexpr int kNetValid = 120;        // output columns of a tile
 constexpr int kNetIR = 8;             // input rows in flight
 constexpr int kNetHR = 2;             // rows of each hidden layer's ring in shared memory
-constexpr int kNetStrip = 64;         // the longest strip of output rows
+constexpr int kNetStrip = 256;        // the longest strip of output rows (each strip pays a 14-step fill)
 constexpr int kNetThreads = 192;      // 4 epilogue warps, producer warp, MMA warp
 constexpr int kNetInRow = (kSurrIn / 8) * kConvSlots * 16;         // bytes of a staged input row
 constexpr int kNetHidRow = (kSurrHidden / 8) * kConvSlots * 16;    // ... of a hidden row
