@@ -398,6 +398,9 @@ struct Engine {
     // the plain propagation gated per stream by residual > threshold
     float surr_thr_default = 1.0f;   // px/frame, for streams attached later
     void* surr_block = nullptr;
+    void* surr_x = nullptr;          // the fused forward's features, owned by the engine (graphs bake it in)
+    size_t surr_x_px = 0;
+    bool surr_same_grid = false;     // every top level on one grid: one fused launch per 64 streams
     float4* surr_one = nullptr;      // one plain step (N = 1) of every stream's top level
     unsigned* surr_res = nullptr;    // per stream: the frame's residual (float bits), zeroed every frame
     float* surr_thr = nullptr;       // per stream: threshold (px/frame)
@@ -450,6 +453,7 @@ void engine_free(Engine& E)
         if (E.graph[q]) cudaGraphExecDestroy(E.graph[q]);
     engine_surr_free(E);
     cudaFree(E.surr_block);
+    cudaFree(E.surr_x);
     for (auto& pl : E.prop) free_plan(pl);
     free_plan(E.solve);
     for (auto& pl : E.smooth) free_plan(pl);
@@ -818,6 +822,8 @@ int engine_smooth_plans(Engine& E, cudaStream_t st)
 // data-dependent branches, so the timing is that of any state, and the
 // propagation of zeros writes zeros, so the engine is left as created.
 int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, float* inv, int slot, cudaStream_t st);
+int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0,
+                __nv_bfloat16* xbuf, cudaStream_t st);
 
 constexpr int kTuneRounds = 2;
 
@@ -1025,9 +1031,24 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
                                                                                               wscale);
                     if (last_error()) return SF_ECUDA;
                 }
-                r = sf_surrogate_forward(E.surr, &lv.grid, 1, (const float*)lv.s0[E.parity], (float*)lv.p0, st);
-                if (r) return r;
             }
+            // one fused launch per group of up to kNetMaxImg streams on one grid
+            // (else one per stream), into the engine's own features buffer
+            const int ns = (int)E.st.size();
+            const int group = E.surr_same_grid ? kNetMaxImg : 1;
+            for (int k0 = 0; k0 < ns && !r; k0 += group) {
+                const int m = std::min(group, ns - k0);
+                const float4* in[kNetMaxImg];
+                float4* out[kNetMaxImg];
+                for (int k = 0; k < m; ++k) {
+                    sf_level_state& lv = E.st[k0 + k].lv[E.st[k0 + k].L - 1];
+                    in[k] = lv.s0[E.parity];
+                    out[k] = lv.p0;
+                }
+                sf_level_state& lv0 = E.st[k0].lv[E.st[k0].L - 1];
+                r = net_forward(E.surr, make_grid(lv0.grid), m, in, out, (__nv_bfloat16*)E.surr_x, st);
+            }
+            if (r) return r;
         }
         if (E.surr) {
             // the fallback: residual against one plain step, then the plain
@@ -1899,6 +1920,9 @@ struct sf_surrogate {
     void* ablock = nullptr;
     __nv_bfloat16 *x0 = nullptr, *a[3] = {}, *dy = nullptr, *dA = nullptr, *dB = nullptr;
     float* y32 = nullptr;
+    // the fused forward's features (32 bytes per pixel), sized for ncap pixels
+    size_t ncap = 0;
+    __nv_bfloat16* xnet = nullptr;
     float* loss = nullptr;
     int* status = nullptr;
     int steps = 0;
@@ -1910,6 +1934,7 @@ inline size_t layer_params(int cin, int cout) { return (size_t)9 * cin * cout + 
 
 void surrogate_free(sf_surrogate* s)
 {
+    if (s) cudaFree(s->xnet);
     if (!s) return;
     cudaFree(s->wblock);
     cudaFree(s->ablock);
@@ -1935,6 +1960,18 @@ int surrogate_capacity(sf_surrogate* s, size_t px)
     s->dB = (__nv_bfloat16*)take(b16 * kSurrHidden);
     s->y32 = (float*)take(px * kSurrOut * sizeof(float));
     s->cap = px;
+    return SF_OK;
+}
+
+// the fused forward's features buffer for px pixels (grows, never shrinks)
+int net_capacity(sf_surrogate* s, size_t px)
+{
+    if (px <= s->ncap) return SF_OK;
+    cudaFree(s->xnet);
+    s->xnet = nullptr;
+    s->ncap = 0;
+    if (cudaMalloc(&s->xnet, px * kSurrIn * sizeof(__nv_bfloat16)) != cudaSuccess) { s->xnet = nullptr; return SF_ENOMEM; }
+    s->ncap = px;
     return SF_OK;
 }
 
@@ -1988,23 +2025,30 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
     return r;
 }
 
+extern "C++" {   // an internal helper, declared ahead of the engine code
 // the features, then the whole network and the head in one launch
-// (k_surr_net): strips of kNetStrip output rows, halved while the launch
-// would still fill at most half the SMs (down to 16); one CTA per SM walks
-// the units.  Measured on 16 frames of 1024 x 1024: strips of 64, 128 and 256
-// rows ran 2.31, 2.21 and 2.16 ms
-int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, float4* p0, cudaStream_t st)
+// (k_surr_net) for n <= kNetMaxImg images of one grid whose states are
+// separate planes s0[k] -> p0[k]: strips of kNetStrip output rows, halved
+// while the launch would still fill at most half the SMs (down to 16); one
+// CTA per SM walks the units.  Measured on 16 frames of 1024 x 1024: strips
+// of 64, 128 and 256 rows ran 2.31, 2.21 and 2.16 ms.  xbuf: the features,
+// n x H x W x 16 BF16, sized by the caller.
+int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0,
+                __nv_bfloat16* xbuf, cudaStream_t st)
 {
+    if (n < 1 || n > kNetMaxImg) return SF_EINVAL;
     const size_t px = (size_t)n * g.H * g.W;
-    k_surr_features<<<grid_stride_blocks(px), 256, 0, st>>>(g, n, s0, s->x0);
+    FeatImgs im;
+    std::memset(&im, 0, sizeof(im));
+    for (int k = 0; k < n; ++k) im.s0[k] = s0[k];
+    k_surr_features_list<<<grid_stride_blocks(px), 256, 0, st>>>(g, n, im, xbuf);
     int r = last_error();
     if (r) return r;
     NetArgs a;
     std::memset(&a, 0, sizeof(a));
     a.g = g;
     a.N = n;
-    a.s0 = s0;
-    a.p0 = p0;
+    for (int k = 0; k < n; ++k) { a.s0[k] = s0[k]; a.p0[k] = p0[k]; }
     for (int l = 0; l < sf_surrogate::kL; ++l) {
         a.w16[l] = s->w16[l];
         a.bias[l] = s->param + s->off[l] + 9 * s->cin[l] * s->cout[l];
@@ -2016,11 +2060,12 @@ int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, float4*
     auto units = [&](int strip) { return (long)n * a.tiles_x * ceil_div(g.H, strip); };
     while (a.strip > 16 && units(a.strip) * 2 <= kSmCount) a.strip /= 2;
     CUtensorMap map;
-    if (conv_input_map(s->x0, n, g.H, g.W, kSurrIn, &map)) return SF_ECUDA;
+    if (conv_input_map(xbuf, n, g.H, g.W, kSurrIn, &map)) return SF_ECUDA;
     if (set_smem_attr((const void*)k_surr_net, net_smem_bytes())) return SF_ECUDA;
     k_surr_net<<<(int)std::min<long>(units(a.strip), kSmCount), kNetThreads, net_smem_bytes(), st>>>(map, a);
     return last_error();
 }
+}  // extern "C++"
 
 }  // namespace
 
@@ -2168,8 +2213,19 @@ int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* 
     const size_t px = (size_t)n * g->H * g->W;
     if (px * kSurrHidden > 2147483647ull) return SF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int r = surrogate_capacity(s, px);
-    if (!r) r = net_forward(s, make_grid(*g), n, (const float4*)s0, (float4*)p0, st);
+    const Grid gg = make_grid(*g);
+    const size_t hw = (size_t)g->H * g->W;
+    int r = net_capacity(s, (size_t)std::min(n, kNetMaxImg) * hw);
+    for (int k0 = 0; k0 < n && !r; k0 += kNetMaxImg) {            // kNetMaxImg images per launch
+        const int m = std::min(kNetMaxImg, n - k0);
+        const float4* in[kNetMaxImg];
+        float4* out[kNetMaxImg];
+        for (int k = 0; k < m; ++k) {
+            in[k] = (const float4*)s0 + (size_t)(k0 + k) * hw;
+            out[k] = (float4*)p0 + (size_t)(k0 + k) * hw;
+        }
+        r = net_forward(s, gg, m, in, out, s->xnet, st);
+    }
     return r;
 }
 
@@ -2289,9 +2345,27 @@ int engine_attach(Engine& E, sf_surrogate* s)
     int r = SF_OK;
     if (s) {
         size_t mx = 0;
-        for (auto& es : E.st) mx = std::max(mx, (size_t)es.lv[es.L - 1].grid.H * es.lv[es.L - 1].grid.W);
-        r = surrogate_capacity(s, mx);
-        // the convolution's shared-memory limit is raised here, outside any stream capture
+        bool same = true;
+        const sf_grid& g0 = E.st[0].lv[E.st[0].L - 1].grid;
+        for (auto& es : E.st) {
+            const sf_grid& gt = es.lv[es.L - 1].grid;
+            mx = std::max(mx, (size_t)gt.H * gt.W);
+            same = same && gt.H == g0.H && gt.W == g0.W && gt.fx == g0.fx && gt.fy == g0.fy && gt.cx == g0.cx &&
+                   gt.cy == g0.cy;
+        }
+        // the features buffer of the fused forward belongs to the engine: captured
+        // graphs bake its address in, so it must outlive them
+        const size_t px = same ? (size_t)std::min((int)E.st.size(), kNetMaxImg) * mx : mx;
+        if (px > E.surr_x_px) {
+            cudaFree(E.surr_x);
+            E.surr_x = nullptr;
+            E.surr_x_px = 0;
+            if (cudaMalloc(&E.surr_x, px * kSurrIn * sizeof(__nv_bfloat16)) != cudaSuccess) { E.surr_x = nullptr; return SF_ENOMEM; }
+            E.surr_x_px = px;
+        }
+        E.surr_same_grid = same;
+        // the kernels' shared-memory limits are raised here, outside any stream capture
+        if (set_smem_attr((const void*)k_surr_net, net_smem_bytes())) r = SF_ECUDA;
         if (!r && set_smem_attr((const void*)k_conv3x3, conv_ws_smem_bytes(kSurrHidden, kSurrHidden))) r = SF_ECUDA;
         if (r) return r;
     }

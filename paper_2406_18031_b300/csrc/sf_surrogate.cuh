@@ -26,6 +26,7 @@ constexpr int kSurrIn = 16;        // input channels (6 used)
 constexpr int kSurrHidden = 32;
 constexpr int kSurrOut = 16;       // output channels (4 used)
 constexpr float kSurrFlowScale = 4.0f;
+constexpr int kNetMaxImg = 64;     // images of one fused forward launch (separate state planes)
 
 __device__ __forceinline__ float pixel_dmu(const Geo& g) { return g.dd * sqrtf(g.omx2); }
 
@@ -44,6 +45,26 @@ __global__ void k_surr_features(Grid g, int n, const float4* __restrict__ s0, __
         const Geo geo = pixel_geometry(g, i, j);
         const float s = 1.0f / (kSurrFlowScale * pixel_dmu(geo));
         const float4 f = s0[p];
+        uint4* o = reinterpret_cast<uint4*>(x0 + p * kSurrIn);
+        o[0] = make_uint4(pack_bf16x2(f.x * s, f.y * s), pack_bf16x2(f.z * s, f.w), pack_bf16x2(geo.ex, geo.ey), 0u);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// the same features for n images whose states are separate planes (the
+// fused forward of several streams), into one n x H x W x 16 tensor
+struct FeatImgs {
+    const float4* s0[kNetMaxImg];
+};
+
+__global__ void k_surr_features_list(Grid g, int n, FeatImgs im, __nv_bfloat16* __restrict__ x0)
+{
+    const size_t hw = (size_t)g.H * g.W, total = hw * n;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(p / hw), q = (int)(p % hw), i = q / g.W, j = q % g.W;
+        const Geo geo = pixel_geometry(g, i, j);
+        const float s = 1.0f / (kSurrFlowScale * pixel_dmu(geo));
+        const float4 f = im.s0[k][q];
         uint4* o = reinterpret_cast<uint4*>(x0 + p * kSurrIn);
         o[0] = make_uint4(pack_bf16x2(f.x * s, f.y * s), pack_bf16x2(f.z * s, f.w), pack_bf16x2(geo.ex, geo.ey), 0u);
         o[1] = make_uint4(0u, 0u, 0u, 0u);
@@ -237,9 +258,9 @@ __host__ __device__ constexpr size_t net_smem_bytes()
 
 struct NetArgs {
     Grid g;
-    int N;                              // images
-    const float4* s0;                   // N x H x W state (w, rho)
-    float4* p0;                         // N x H x W prediction
+    int N;                              // images (<= kNetMaxImg)
+    const float4* s0[kNetMaxImg];       // image k: H x W state (w, rho)
+    float4* p0[kNetMaxImg];             // image k: H x W prediction
     const __nv_bfloat16* w16[4];        // per layer 9 x Cout x Cin (tap-major)
     const float* bias[4];               // per layer Cout
     int tiles_x;                        // ceil(W / kNetValid)
@@ -521,10 +542,10 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                         const int px = x0 - 1 + m;
                         if (m >= 1 && m <= kNetValid && px < W) {
                             const float4 bl = *reinterpret_cast<const float4*>(bias_s + 96);
-                            const size_t pi = ((size_t)nn * H + x) * W + px;
+                            const size_t pi = (size_t)x * W + px;
                             const float dd = kSurrFlowScale * pixel_dmu(pixel_geometry(g, x, px));
-                            const float4 f = a.s0[pi];
-                            a.p0[pi] = make_float4(fmaf(dd, o[0] + bl.x, f.x), fmaf(dd, o[1] + bl.y, f.y),
+                            const float4 f = a.s0[nn][pi];
+                            a.p0[nn][pi] = make_float4(fmaf(dd, o[0] + bl.x, f.x), fmaf(dd, o[1] + bl.y, f.y),
                                                    fmaf(dd, o[2] + bl.z, f.z), f.w + (o[3] + bl.w));
                         }
                     }

@@ -207,12 +207,15 @@ def test_filter_top_level_predicted_by_the_surrogate():
     assert res > 0 and fell == 0
 
 
-def test_batch_with_the_surrogate_matches_single_filters():
+# widths 128 and 192: one fused launch per stream; three streams on one grid:
+# one fused launch for all three (separate state planes)
+@pytest.mark.parametrize("widths", [(128, 192), (128, 128, 128)])
+def test_batch_with_the_surrogate_matches_single_filters(widths):
     from paper_2406_18031_b300 import scenes
-    seqs = [scenes.plane64(frames=6, seed=21 + k, H=64, W=128 + 64 * k, levels=1, iters=[2]) for k in range(2)]
+    seqs = [scenes.plane64(frames=6, seed=21 + k, H=64, W=w, levels=1, iters=[2]) for k, w in enumerate(widths)]
     net = sf.Surrogate(seed=12)
     P = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth) for q in seqs]
-    batch = sf.Batch([q.shape for q in seqs], [1, 1], P)
+    batch = sf.Batch([q.shape for q in seqs], [1] * len(seqs), P)
     batch.set_surrogate(net)
     singles = [sf.Filter(*q.shape, 1, p) for q, p in zip(seqs, P)]
     net2 = sf.Surrogate(seed=12)            # same weights, its own buffers
@@ -230,7 +233,7 @@ def test_batch_with_the_surrogate_matches_single_filters():
                                 outs[s], stream=stream)
             batch.step(dt, stream=stream)
         stream.synchronize()
-        for s in range(2):
+        for s in range(len(seqs)):
             assert torch.equal(batch.slots[s][2], outs[s]), (k, s)
 
 
