@@ -145,6 +145,7 @@ struct Plan {
     bool c8 = false;     // propagation: some job transports 8 channels
     int nf = 0;          // propagation: sub-iterations of the launch's longest job
     int warps = 16;      // propagation: warps per CTA (prop_warps of nf)
+    bool resid = false;  // propagation: residual mode (k_propagate's RES form, 8 warps)
     int tile = 0;        // solve: tile edge (kSolveTSmall, else kSolveT)
 };
 
@@ -179,11 +180,11 @@ void add_tiles(std::vector<int4>& work, int job, int H, int W, int TX, int TY)
 // need 16-byte alignment whatever the size of the job struct
 inline size_t work_offset(size_t job_bytes) { return (job_bytes + 255) & ~(size_t)255; }
 
-template <bool C8, bool LIT, bool IMU, bool PE, int WARPS>
+template <bool C8, bool LIT, bool IMU, bool PE, int WARPS, bool RES = false>
 int launch_propagate_t(const Plan& p, int parity, float wscale, int flags, int* status, float mscale, cudaStream_t st,
                        bool pdl)
 {
-    auto* kern = k_propagate<C8, LIT, IMU, PE, WARPS>;
+    auto* kern = k_propagate<C8, LIT, IMU, PE, WARPS, RES>;
     if (set_smem_attr((const void*)kern, p.smem)) return SF_ECUDA;
     return launch_ex(pdl, kern, dim3(p.nwork), dim3(32 * WARPS), p.smem, st, (const PropJob*)p.jobs,
                      (const int4*)p.work, parity, wscale, flags, status, mscale);
@@ -195,6 +196,10 @@ int launch_propagate_i(const Plan& p, int parity, float wscale, int flags, int* 
 {
     // 8-warp CTAs for launches of few sub-iterations (prop_warps); the padded
     // form for launches of many (see kPrPaddedNf)
+    if (p.resid)   // the surrogate's check: one sub-iteration of top levels, 8-warp CTAs
+        return p.warps == 8 && !C8 ? launch_propagate_t<false, LIT, IMU, false, 8, true>(p, parity, wscale, flags, status,
+                                                                                          mscale, st, pdl)
+                                   : SF_EINVAL;
     if (p.warps == 8)
         return launch_propagate_t<C8, LIT, IMU, false, 8>(p, parity, wscale, flags, status, mscale, st, pdl);
     if (p.nf >= kPrPaddedNf)
@@ -401,12 +406,10 @@ struct Engine {
     void* surr_x = nullptr;          // the fused forward's features, owned by the engine (graphs bake it in)
     size_t surr_x_px = 0;
     bool surr_same_grid = false;     // every top level on one grid: one fused launch per 64 streams
-    float4* surr_one = nullptr;      // one plain step (N = 1) of every stream's top level
     unsigned* surr_res = nullptr;    // per stream: the frame's residual (float bits), zeroed every frame
     float* surr_thr = nullptr;       // per stream: threshold (px/frame)
     unsigned* surr_cnt = nullptr;    // per stream: frames whose prediction fell back to the plain propagation
     Plan surr_one_plan;
-    Plan surr_res_plan;
     std::vector<Plan> surr_fb;       // gated plain propagation of the top levels (one per segment)
 
     int launches_per_step() const
@@ -414,8 +417,10 @@ struct Engine {
         int n = (int)prop.size() + 1;
         for (auto& p : smooth) n += p.nwork ? 1 : 0;
         for (auto& p : recon) n += p.nwork ? 1 : 0;
-        if (surr) n += 6 * (int)st.size() + 2 + (int)surr_fb.size();   // per stream: features, four layers, head;
-                                                                        // one plain step, residual, fallback
+        if (surr) {   // per group of streams: features, the fused network; the check; the fallback segments
+            const int groups = surr_same_grid ? ((int)st.size() + kNetMaxImg - 1) / kNetMaxImg : (int)st.size();
+            n += 2 * groups + 1 + (int)surr_fb.size();
+        }
         return n;
     }
 };
@@ -442,7 +447,6 @@ void engine_solve_tile(Engine& E, int param)
 void engine_surr_free(Engine& E)
 {
     free_plan(E.surr_one_plan);
-    free_plan(E.surr_res_plan);
     for (auto& pl : E.surr_fb) free_plan(pl);
     E.surr_fb.clear();
 }
@@ -490,8 +494,10 @@ int engine_levels(EngineStream& s, cudaStream_t st)
 }
 
 // The surrogate's fallback plans (nothing without a surrogate): every
-// stream's top level once more with one plain sub-iteration (N = 1) into
-// surr_one; the residual launch; and the plain propagation of the top levels
+// stream's top level once more with one plain sub-iteration (N = 1), in the
+// propagation's residual mode (each tile reduces its largest difference to
+// the surrogate's prediction into the stream's residual word instead of
+// storing); and the plain propagation of the top levels
 // in segments of at most nf_max sub-iterations (as the plain engine splits
 // them), each job gated by its stream's residual word and threshold.  The
 // state is already rescaled for a frame-time change when these run
@@ -501,14 +507,10 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
     engine_surr_free(E);
     if (!E.surr) return SF_OK;
     const int n = (int)E.st.size();
-    size_t top_px = 0;
-    for (auto& s : E.st) top_px += (size_t)s.lv[s.L - 1].grid.H * s.lv[s.L - 1].grid.W;
     if (!E.surr_block) {
-        const size_t bytes = top_px * sizeof(float4) + 3 * ((n * sizeof(unsigned) + 255) & ~(size_t)255);
+        const size_t bytes = 3 * ((n * sizeof(unsigned) + 255) & ~(size_t)255);
         if (cudaMalloc(&E.surr_block, bytes) != cudaSuccess) { E.surr_block = nullptr; return SF_ENOMEM; }
         unsigned char* p = (unsigned char*)E.surr_block;
-        E.surr_one = (float4*)p;
-        p += top_px * sizeof(float4);
         const size_t wb = (n * sizeof(unsigned) + 255) & ~(size_t)255;
         E.surr_res = (unsigned*)p;
         E.surr_thr = (float*)(p + wb);
@@ -529,7 +531,8 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
             std::memset(&j, 0, sizeof(j));
             j.g = make_grid(lv.grid);
             j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
-            j.out0 = E.surr_one + off;
+            j.resid_ref = lv.p0;                       // the surrogate's prediction
+            j.resid_out = E.surr_res + (&s - E.st.data());
             j.nf = 1;
             j.dt = 1.0f;
             j.tiles_x = ceil_div(lv.grid.W, prop_tile(1));
@@ -539,30 +542,10 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
             off += (size_t)lv.grid.H * lv.grid.W;
         }
         E.surr_one_plan.nf = 1;
+        E.surr_one_plan.resid = true;
         E.surr_one_plan.warps = prop_warps(1);
         E.surr_one_plan.smem = prop_smem_bytes(E.surr_one_plan.warps);
         int r = upload_plan(jobs, work, E.surr_one_plan, st);
-        if (r) return r;
-    }
-    // the residual of the surrogate's prediction (p0) against that step
-    {
-        std::vector<SurrResJob> jobs;
-        std::vector<int4> work;
-        size_t off = 0;
-        for (int k = 0; k < n; ++k) {
-            sf_level_state& lv = E.st[k].lv[E.st[k].L - 1];
-            SurrResJob j;
-            std::memset(&j, 0, sizeof(j));
-            j.g = make_grid(lv.grid);
-            j.a = lv.p0;
-            j.b = E.surr_one + off;
-            j.res = E.surr_res + k;
-            jobs.push_back(j);
-            const int px = lv.grid.H * lv.grid.W;
-            for (int c = 0; c < px; c += kResChunk) work.push_back(make_int4((int)jobs.size() - 1, c, 0, 0));
-            off += (size_t)px;
-        }
-        int r = upload_plan(jobs, work, E.surr_res_plan, st);
         if (r) return r;
     }
     // the gated plain propagation of the top levels
@@ -1057,11 +1040,10 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
             NvtxRange nv("sf prediction: surrogate check and gated plain fallback");
             ProfScope ps(E.prof, slot++, st);
             if (cudaMemsetAsync(E.surr_res, 0, E.st.size() * sizeof(unsigned), st) != cudaSuccess) return SF_ECUDA;
+            // one plain sub-iteration of every top level, reduced on the fly to each
+            // stream's largest difference to the surrogate's prediction
             r = launch_propagate(E.surr_one_plan, E.parity, 1.0f, E.flags & ~SF_CHECK_CFL, nullptr, st, dt);
             if (r) return r;
-            k_surr_residual<<<E.surr_res_plan.nwork, 256, 0, st>>>((const SurrResJob*)E.surr_res_plan.jobs,
-                                                                     E.surr_res_plan.work);
-            if (last_error()) return SF_ECUDA;
             for (auto& pl : E.surr_fb) {
                 r = launch_propagate(pl, E.parity, 1.0f, E.flags, E.status, st, dt);
                 if (r) return r;

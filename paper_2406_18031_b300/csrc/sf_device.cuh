@@ -66,6 +66,9 @@ __device__ __forceinline__ Geo pixel_geometry(const Grid& g, int i, int j)
     return o;
 }
 
+// grid spacing dmu of a pixel, |P_eta eta_right| = a sqrt(1 - eta_x^2) / |m'|
+__device__ __forceinline__ float pixel_dmu(const Geo& g) { return g.dd * sqrtf(g.omx2); }
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream

@@ -52,6 +52,11 @@ struct PropJob {
     const unsigned* gate;
     const float* gate_thr;
     unsigned* gate_count;
+    // residual mode (the RES form of k_propagate): instead of writing out0 the
+    // job reduces the largest |w - resid_ref w| / dmu over its tile (px/frame;
+    // NaN counts as the largest) into *resid_out (atomicMax of the float's bits)
+    const float4* resid_ref;
+    unsigned* resid_out;
 };
 
 // Register-resident tiles: a CTA of WARPS warps holds a kPrW x (kPrRows WARPS) region
@@ -245,7 +250,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return false;
 }
 
-template <bool C8, bool LITERAL, bool IMU, bool PE, int WARPS>
+template <bool C8, bool LITERAL, bool IMU, bool PE, int WARPS, bool RES = false>
 __global__ void __launch_bounds__(32 * WARPS, kPrWarpsMax / WARPS)
 k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int parity, float wscale,
             int flags, int* __restrict__ status, float mscale)
@@ -330,6 +335,21 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
             const size_t gi = (size_t)ic * g.W + clampi(j, 0, g.W - 1);
             a[k][q] = in0[gi];
             b[k][q] = has1 ? in1[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    // residual mode: the reference values of my tile pixels, loaded with the state
+    float4 rref[RES ? kPrRows : 1][2];
+    if constexpr (RES) {
+#pragma unroll
+        for (int k = 0; k < kPrRows; ++k) {
+            const int i = oy + r0 + k;
+            const bool rin = r0 + k >= nf && r0 + k < nf + prop_tile_h(nf, WARPS) && i < g.H;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = c0 + q, j = j0 + q;
+                const bool in = rin && c >= nf && c < nf + prop_tile(nf) && j < g.W;
+                rref[k][q] = in ? J.resid_ref[(size_t)i * g.W + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
     }
     geometry();      // per-pixel geometry while the loads are in flight
@@ -512,17 +532,40 @@ k_propagate(const PropJob* __restrict__ jobs, const int4* __restrict__ work, int
     if (interior) passes(std::false_type{});
     else passes(std::true_type{});
 
-    // write the output tile (its in-image part)
+    if constexpr (RES) {
+        // residual mode: the largest flow difference to the reference over the tile
+        float m = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kPrRows; ++k) {
-        const int r = r0 + k, i = oy + r;
-        if (r < nf || r >= nf + TH || i >= g.H) continue;
+        for (int k = 0; k < kPrRows; ++k) {
+            const int r = r0 + k, i = oy + r;
+            if (r < nf || r >= nf + TH || i >= g.H) continue;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            if (!col_in[q]) continue;
-            const size_t gi = (size_t)i * g.W + (j0 + q);
-            J.out0[gi] = a[k][q];
-            if (has1) J.out1[gi] = b[k][q];
+            for (int q = 0; q < 2; ++q) {
+                if (!col_in[q]) continue;
+                // 1 / dmu = cu sqrt(1 - eta_x^2) from the pixel's geometry in shared memory
+                // (cu stored times dt / 2)
+                const float4 G = geo[r * kPrW + q * 32 + lane];
+                const float inv = (G.w * (2.0f / dt)) * sqrtf(fmaf(-G.x, G.x, 1.0f));
+                const float4 u = rref[k][q], v = a[k][q];
+                const float d = fmaxf(fabsf(u.x - v.x), fmaxf(fabsf(u.y - v.y), fabsf(u.z - v.z))) * inv;
+                m = fmaxf(m, d == d ? d : 3.0e38f);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(J.resid_out, __float_as_uint(m));
+    } else {
+        // write the output tile (its in-image part)
+#pragma unroll
+        for (int k = 0; k < kPrRows; ++k) {
+            const int r = r0 + k, i = oy + r;
+            if (r < nf || r >= nf + TH || i >= g.H) continue;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!col_in[q]) continue;
+                const size_t gi = (size_t)i * g.W + (j0 + q);
+                J.out0[gi] = a[k][q];
+                if (has1) J.out1[gi] = b[k][q];
+            }
         }
     }
     if (timed_out && status) atomicOr(status, kStatusTimeout);

@@ -5,8 +5,10 @@
 // trained on pairs that the plain propagation produces.  The convolutions are
 // k_conv3x3 (forward, and backward-data with flipped, transposed weights) and
 // k_wgrad_tc (the weight gradient), both on the tensor cores; this file holds
-// the per-pixel feature and head kernels, the loss gradient, the ReLU mask,
-// the Adam step and the fallback's residual.
+// the whole forward in one kernel (k_surr_net, inference), the per-pixel
+// feature and head kernels, the loss gradient, the ReLU mask, the Adam step
+// and the largest-difference reduction of the stand-alone fallback check (the
+// engine's check runs in k_propagate's residual mode).
 //
 // Features of a pixel: w / (4 dmu) (3, px/frame over 4), rho, eta_x, eta_y,
 // and 10 zero channels.  Output channels 0..3 are the change over one frame
@@ -28,7 +30,6 @@ constexpr int kSurrOut = 16;       // output channels (4 used)
 constexpr float kSurrFlowScale = 4.0f;
 constexpr int kNetMaxImg = 64;     // images of one fused forward launch (separate state planes)
 
-__device__ __forceinline__ float pixel_dmu(const Geo& g) { return g.dd * sqrtf(g.omx2); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -167,37 +168,6 @@ __global__ void k_surr_maxdiff(Grid g, int n, const float4* __restrict__ a, cons
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
-}
-
-// The residual of every attached stream's top-level prediction against one
-// plain step: per job (a stream) the largest |a - b| of the flow over its
-// pixels in px/frame (w / dmu), atomicMax-ed into *res as the bit pattern of
-// a non-negative float (NaN counts as the largest).  Work item = (job, first
-// pixel of a chunk of kResChunk pixels).
-struct SurrResJob {
-    Grid g;
-    const float4* a;
-    const float4* b;
-    unsigned* res;
-};
-constexpr int kResChunk = 4096;
-
-__global__ void k_surr_residual(const SurrResJob* __restrict__ jobs, const int4* __restrict__ work)
-{
-    const int4 wk = work[blockIdx.x];
-    const SurrResJob& J = jobs[wk.x];
-    const int n = J.g.H * J.g.W;
-    const int end = min(n, wk.y + kResChunk);
-    float m = 0.0f;
-    for (int p = wk.y + threadIdx.x; p < end; p += blockDim.x) {
-        const int i = p / J.g.W, j = p - i * J.g.W;
-        const float inv = 1.0f / pixel_dmu(pixel_geometry(J.g, i, j));
-        const float4 u = J.a[p], v = J.b[p];
-        const float d = fmaxf(fabsf(u.x - v.x), fmaxf(fabsf(u.y - v.y), fabsf(u.z - v.z))) * inv;
-        m = fmaxf(m, d == d ? d : 3.0e38f);
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(J.res, __float_as_uint(m));
 }
 
 // ---------------------------------------------------------------------------

@@ -200,11 +200,19 @@ def test_filter_top_level_predicted_by_the_surrogate():
     torch.cuda.synchronize()
     ref = torch.cat([n0.permute(2, 0, 1), n1.permute(2, 0, 1)])
     assert torch.equal(got, ref)
-    # surrogate (features, 4 layers, head), the fallback check (one plain
-    # step, residual, gated plain propagation), solve, smoothing
-    assert filt.kernels_per_step() == 6 + 3 + 1 + 1
+    # the fused surrogate (features, network), the fallback check (one plain
+    # step reduced to the residual, the gated plain propagation), solve, smoothing
+    assert filt.kernels_per_step() == 2 + 2 + 1 + 1
     res, fell = filt.surrogate_stats()
     assert res > 0 and fell == 0
+    # the residual is the stand-alone check's: the largest flow difference of the
+    # surrogate's prediction to one plain step, in px/frame
+    out = torch.empty_like(s0)
+    res_ref, used = net.propagate(g, seq.iters[0], s0[None], out[None], threshold_px=float("inf"))
+    torch.cuda.synchronize()
+    # (the engine's check takes dmu from the propagation's fast per-pixel geometry:
+    # a few ulp from the stand-alone reduction's)
+    assert not used and abs(res - res_ref) <= 1e-5 * res_ref, (res, res_ref)
 
 
 # widths 128 and 192: one fused launch per stream; three streams on one grid:
