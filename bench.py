@@ -49,9 +49,9 @@ def dist_env():
 # captures of these very workloads (profiles/traffic_scene512_and_batch.md), valid
 # only for the kernel sources they were taken with.
 TRAFFIC = {
-    "kernel_sources_sha256_16": "1564c7329668f78e",
-    "scene512_k_propagate_bytes": 9_507_072 + 4_096,
-    "batch_k_propagate_bytes": 1_070_214_400 + 1_022_731_520,
+    "kernel_sources_sha256_16": "e587800fd8de38a9",
+    "scene512_k_propagate_bytes": 9_502_464 + 2_816,
+    "batch_k_propagate_bytes": 1_070_838_016 + 1_022_817_792,
 }
 
 
