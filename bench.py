@@ -960,11 +960,14 @@ PAPER_HZ_1024 = 172.149   # the paper's rate at 1024x1024, 2 levels, max flow 8 
 
 def measure_1024(steps, evict_l2, dev):
     """The paper's second configuration: 1024 x 1024, 2 levels, N = [8, 4],
-    smoothing [2, 4] (the 512 x 512 scene tiled 2 x 2 with a 90-degree field
-    of view), autotuned, cold L2 before each timed frame."""
+    smoothing [2, 4] (the scene of the 512 x 512 workload rendered at 1024 x
+    1024 with the same 90-degree field of view, the camera scaled to the same
+    peak flow of 8 px/frame), autotuned, cold L2 before each timed frame."""
     import torch
-    from paper_2406_18031_b300 import sf
-    seq = make_sequence(1001, 8, 1024)
+    from paper_2406_18031_b300 import scenes, sf
+    w = WORKLOAD
+    seq = scenes.scene512(frames=8, seed=1001, H=1024, W=1024, rate=w["rate"], max_flow=w["max_flow"],
+                          levels=w["levels"], iters=tuple(w["iters"]), smooth=tuple(w["smooth"]))
     H, W = seq.shape
     images = torch.from_numpy(seq.image).to(dev)
     ranges = torch.from_numpy(seq.range).to(dev)
@@ -986,7 +989,8 @@ def measure_1024(steps, evict_l2, dev):
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     kernels = profiled_split(filt, seq, steps, lambda k: filt.step(images[1 + k % 7], ranges[1 + k % 7], seq.dt,
                                                                    flow, inv, stream=stream), evict_l2)
-    out = {"workload": "1024x1024, 2 levels, N=[8,4], smooth=[2,4] (scene512 tiled 2x2), cold L2",
+    out = {"workload": "1024x1024, 2 levels, N=[8,4], smooth=[2,4], peak flow 8 px/frame (the 512x512 scene "
+                       "rendered at 1024x1024), cold L2",
            "frames_per_s": 1e3 / ms, "ms_per_step": ms, "nf_max": filt.nf_max(),
            "update_mode": filt.update_mode(), "solve_tile": filt.solve_tile(), "vs_paper": 1e3 / ms / PAPER_HZ_1024,
            "hbm_gbs_algorithmic": algorithmic_bytes_per_frame(H, W, seq.levels) / (ms / 1e3) / 1e9,
