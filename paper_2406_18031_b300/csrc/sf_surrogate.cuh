@@ -239,16 +239,44 @@ struct NetArgs {
     int* status;                        // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
-// this thread's TMEM lane, 4 consecutive FP32 columns
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v)
+// tcgen05.ld without its wait (several loads then one tmem_ld_wait): the
+// registers hold the columns only after the wait, and tmem_ld_bind ties them
+// to a point after it so that no use is scheduled earlier
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r)
 {
-    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t* r)
+{
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld_bind32(uint32_t* r)
+{
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
+__device__ __forceinline__ void tmem_ld_bind4(uint32_t* r)
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
 }
 
 // zero 32 (X32) or 16 consecutive FP32 columns of this warp's 32 TMEM lanes
@@ -468,19 +496,43 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
         for (int u = blockIdx.x; u < n_units && !failed; u += gridDim.x) {
             const int sy = u % strips_y, tx = (u / strips_y) % a.tiles_x, nn = u / (strips_y * a.tiles_x);
             const int x0 = tx * kNetValid, y_b = sy * a.strip, S = min(H, y_b + a.strip) - y_b;
+            // the state under the head's output row of step t (row y_b - 14 + t), loaded one
+            // step ahead so that its latency overlaps the wait instead of the drain
+            const int px3 = x0 - 1 + m;
+            const bool lane3 = m >= 1 && m <= kNetValid && px3 < W;
+            auto s0_row = [&](int t) {
+                return (lane3 && t >= 14 && active(3, t, S)) ? a.s0[nn][(size_t)(y_b - 14 + t) * W + px3]
+                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            };
+            float4 f_next = s0_row(0);
             for (int t = 0; t < S + kTail; ++t, ++gs) {
+                const float4 f_cur = f_next;
+                f_next = s0_row(t + 1);
                 const int b = (int)(gs & 1);
                 const bool ok = mbar_wait_or_abort(acc_full(b), (uint32_t)((gs >> 1) & 1), a.spin_limit, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // every accumulator row this step drains, loaded before one wait
+                uint32_t hv[3][32], ov[4];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const int x = y_b - 5 - 3 * l + t;                    // warp-uniform tests
+                    if (active(l, t, S) && t >= 4 * l + 2 && x >= 0 && x < H)
+                        tmem_ld32_nowait(lanes + net_block_col(l, x), hv[l]);
+                }
+                if (active(3, t, S) && t >= 14) tmem_ld4_nowait(lanes + net_block_col(3, y_b - 14 + t), ov);
+                tmem_ld_wait();
+                tmem_ld_bind32(hv[0]);
+                tmem_ld_bind32(hv[1]);
+                tmem_ld_bind32(hv[2]);
+                tmem_ld_bind4(ov);
 #pragma unroll
                 for (int l = 0; l < 3; ++l) {
                     if (!active(l, t, S)) continue;                      // warp-uniform
                     const int q = y_b - 4 - 3 * l + t, x = q - 1;         // x: the row this step completed
                     if (t >= 4 * l + 2) {                                 // a row the next layer reads
                         const bool in_row = x >= 0 && x < H;              // warp-uniform
-                        float v[32];
-                        if (in_row) tmem_ld32(lanes + net_block_col(l, x), v);
+                        const uint32_t* v = hv[l];
                         const int px = x0 - 4 + l + m;                    // this lane's position
                         const bool in_img = in_row && px >= 0 && px < W;
                         const float4* bl = reinterpret_cast<const float4*>(bias_s + 32 * l);
@@ -492,7 +544,7 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                             const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                             float r[8];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) r[k] = in_img ? fmaxf(v[8 * c + k] + bb[k], 0.0f) : 0.0f;
+                            for (int k = 0; k < 8; ++k) r[k] = in_img ? fmaxf(__uint_as_float(v[8 * c + k]) + bb[k], 0.0f) : 0.0f;
                             *reinterpret_cast<uint4*>(dst + (size_t)c * kConvSlots * 16) =
                                 make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]), pack_bf16x2(r[4], r[5]),
                                            pack_bf16x2(r[6], r[7]));
@@ -508,13 +560,13 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                     const int q = y_b - 13 + t, x = q - 1;
                     if (t >= 14) {                                        // x in [y_b, y_e): the prediction
                         float o[4];
-                        tmem_ld4(lanes + net_block_col(3, x), o);
-                        const int px = x0 - 1 + m;
-                        if (m >= 1 && m <= kNetValid && px < W) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) o[k] = __uint_as_float(ov[k]);
+                        if (lane3) {
                             const float4 bl = *reinterpret_cast<const float4*>(bias_s + 96);
-                            const size_t pi = (size_t)x * W + px;
-                            const float dd = kSurrFlowScale * pixel_dmu(pixel_geometry(g, x, px));
-                            const float4 f = a.s0[nn][pi];
+                            const size_t pi = (size_t)x * W + px3;
+                            const float dd = kSurrFlowScale * pixel_dmu(pixel_geometry(g, x, px3));
+                            const float4 f = f_cur;
                             a.p0[nn][pi] = make_float4(fmaf(dd, o[0] + bl.x, f.x), fmaf(dd, o[1] + bl.y, f.y),
                                                    fmaf(dd, o[2] + bl.z, f.z), f.w + (o[3] + bl.w));
                         }
