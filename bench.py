@@ -1350,7 +1350,7 @@ def run_conv_line(args):
                         **{f"{f}_ms": v for f, v in net_ms.items()},
                         **{f"{f}_tflops": net_flops / (v / 1e3) / 1e12 for f, v in net_ms.items()},
                         "fused_frac_of_bf16_peak": net_flops / (net_ms["fused"] / 1e3) / 1e12 / peaks["bf16_tflops"],
-                        "kernels": "fused: k_surr_features + k_surr_net; layered: k_surr_features, 4 x k_conv3x3, "
+                        "kernels": "fused: k_surr_net (features computed in the kernel); layered: k_surr_features, 4 x k_conv3x3, "
                                    "k_surr_head"},
             "gpu_launches": 2 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)

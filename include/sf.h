@@ -480,10 +480,10 @@ int sf_surrogate_params(sf_surrogate* s, float* host, int set);
 int sf_surrogate_grads(sf_surrogate* s, float* host);
 /* Predict: s0 = n frames of the grid g's top-level state (device
  * n x H x W float4 (w_x, w_y, w_z, rho), w in rad/frame) -> p0 (same layout).
- * The four layers and the head run in one tensor-core kernel that keeps the
- * hidden activations in shared memory (only the features, the state and
- * the prediction touch HBM).  Activation buffers grow on demand (about 450
- * bytes per pixel). */
+ * The features, the four layers and the head run in one tensor-core kernel
+ * that keeps the features and the hidden activations in shared memory (only
+ * the state and the prediction touch HBM); it allocates nothing.  Up to 64
+ * frames per launch. */
 int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* s0, float* p0,
                          void* stream);
 /* The same prediction computed layer by layer (the forward pass of

@@ -403,8 +403,6 @@ struct Engine {
     // the plain propagation gated per stream by residual > threshold
     float surr_thr_default = 1.0f;   // px/frame, for streams attached later
     void* surr_block = nullptr;
-    void* surr_x = nullptr;          // the fused forward's features, owned by the engine (graphs bake it in)
-    size_t surr_x_px = 0;
     bool surr_same_grid = false;     // every top level on one grid: one fused launch per 64 streams
     unsigned* surr_res = nullptr;    // per stream: the frame's residual (float bits), zeroed every frame
     float* surr_thr = nullptr;       // per stream: threshold (px/frame)
@@ -417,9 +415,9 @@ struct Engine {
         int n = (int)prop.size() + 1;
         for (auto& p : smooth) n += p.nwork ? 1 : 0;
         for (auto& p : recon) n += p.nwork ? 1 : 0;
-        if (surr) {   // per group of streams: features, the fused network; the check; the fallback segments
+        if (surr) {   // per group of streams the fused network (features included); the check; the fallback segments
             const int groups = surr_same_grid ? ((int)st.size() + kNetMaxImg - 1) / kNetMaxImg : (int)st.size();
-            n += 2 * groups + 1 + (int)surr_fb.size();
+            n += groups + 1 + (int)surr_fb.size();
         }
         return n;
     }
@@ -457,7 +455,6 @@ void engine_free(Engine& E)
         if (E.graph[q]) cudaGraphExecDestroy(E.graph[q]);
     engine_surr_free(E);
     cudaFree(E.surr_block);
-    cudaFree(E.surr_x);
     for (auto& pl : E.prop) free_plan(pl);
     free_plan(E.solve);
     for (auto& pl : E.smooth) free_plan(pl);
@@ -805,8 +802,7 @@ int engine_smooth_plans(Engine& E, cudaStream_t st)
 // data-dependent branches, so the timing is that of any state, and the
 // propagation of zeros writes zeros, so the engine is left as created.
 int engine_update_launches(Engine& E, const UpdArgs& a, float dt, float* flow, float* inv, int slot, cudaStream_t st);
-int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0,
-                __nv_bfloat16* xbuf, cudaStream_t st);
+int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0, cudaStream_t st);
 
 constexpr int kTuneRounds = 2;
 
@@ -1029,7 +1025,7 @@ int engine_launches(Engine& E, const float* image, const float* range, float dt,
                     out[k] = lv.p0;
                 }
                 sf_level_state& lv0 = E.st[k0].lv[E.st[k0].L - 1];
-                r = net_forward(E.surr, make_grid(lv0.grid), m, in, out, (__nv_bfloat16*)E.surr_x, st);
+                r = net_forward(E.surr, make_grid(lv0.grid), m, in, out, st);
             }
             if (r) return r;
         }
@@ -1902,9 +1898,6 @@ struct sf_surrogate {
     void* ablock = nullptr;
     __nv_bfloat16 *x0 = nullptr, *a[3] = {}, *dy = nullptr, *dA = nullptr, *dB = nullptr;
     float* y32 = nullptr;
-    // the fused forward's features (32 bytes per pixel), sized for ncap pixels
-    size_t ncap = 0;
-    __nv_bfloat16* xnet = nullptr;
     float* loss = nullptr;
     int* status = nullptr;
     int steps = 0;
@@ -1916,7 +1909,6 @@ inline size_t layer_params(int cin, int cout) { return (size_t)9 * cin * cout + 
 
 void surrogate_free(sf_surrogate* s)
 {
-    if (s) cudaFree(s->xnet);
     if (!s) return;
     cudaFree(s->wblock);
     cudaFree(s->ablock);
@@ -1942,18 +1934,6 @@ int surrogate_capacity(sf_surrogate* s, size_t px)
     s->dB = (__nv_bfloat16*)take(b16 * kSurrHidden);
     s->y32 = (float*)take(px * kSurrOut * sizeof(float));
     s->cap = px;
-    return SF_OK;
-}
-
-// the fused forward's features buffer for px pixels (grows, never shrinks)
-int net_capacity(sf_surrogate* s, size_t px)
-{
-    if (px <= s->ncap) return SF_OK;
-    cudaFree(s->xnet);
-    s->xnet = nullptr;
-    s->ncap = 0;
-    if (cudaMalloc(&s->xnet, px * kSurrIn * sizeof(__nv_bfloat16)) != cudaSuccess) { s->xnet = nullptr; return SF_ENOMEM; }
-    s->ncap = px;
     return SF_OK;
 }
 
@@ -2008,24 +1988,15 @@ int surrogate_forward(sf_surrogate* s, const Grid& g, int n, const float4* s0, c
 }
 
 extern "C++" {   // an internal helper, declared ahead of the engine code
-// the features, then the whole network and the head in one launch
-// (k_surr_net) for n <= kNetMaxImg images of one grid whose states are
-// separate planes s0[k] -> p0[k]: strips of kNetStrip output rows, halved
-// while the launch would still fill at most half the SMs (down to 16); one
-// CTA per SM walks the units.  Measured on 16 frames of 1024 x 1024: strips
-// of 64, 128 and 256 rows ran 2.31, 2.21 and 2.16 ms.  xbuf: the features,
-// n x H x W x 16 BF16, sized by the caller.
-int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0,
-                __nv_bfloat16* xbuf, cudaStream_t st)
+// the features, the whole network and the head in one launch (k_surr_net)
+// for n <= kNetMaxImg images of one grid whose states are separate planes
+// s0[k] -> p0[k]: strips of kNetStrip output rows, halved while the launch
+// would still fill at most half the SMs (down to 16); one CTA per SM walks
+// the units.  Measured on 16 frames of 1024 x 1024: strips of 64, 128 and
+// 256 rows ran 2.31, 2.21 and 2.16 ms (the features then a launch of their own).
+int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, float4* const* p0, cudaStream_t st)
 {
     if (n < 1 || n > kNetMaxImg) return SF_EINVAL;
-    const size_t px = (size_t)n * g.H * g.W;
-    FeatImgs im;
-    std::memset(&im, 0, sizeof(im));
-    for (int k = 0; k < n; ++k) im.s0[k] = s0[k];
-    k_surr_features_list<<<grid_stride_blocks(px), 256, 0, st>>>(g, n, im, xbuf);
-    int r = last_error();
-    if (r) return r;
     NetArgs a;
     std::memset(&a, 0, sizeof(a));
     a.g = g;
@@ -2041,10 +2012,8 @@ int net_forward(sf_surrogate* s, const Grid& g, int n, const float4* const* s0, 
     a.strip = kNetStrip;
     auto units = [&](int strip) { return (long)n * a.tiles_x * ceil_div(g.H, strip); };
     while (a.strip > 16 && units(a.strip) * 2 <= kSmCount) a.strip /= 2;
-    CUtensorMap map;
-    if (conv_input_map(xbuf, n, g.H, g.W, kSurrIn, &map)) return SF_ECUDA;
     if (set_smem_attr((const void*)k_surr_net, net_smem_bytes())) return SF_ECUDA;
-    k_surr_net<<<(int)std::min<long>(units(a.strip), kSmCount), kNetThreads, net_smem_bytes(), st>>>(map, a);
+    k_surr_net<<<(int)std::min<long>(units(a.strip), kSmCount), kNetThreads, net_smem_bytes(), st>>>(a);
     return last_error();
 }
 }  // extern "C++"
@@ -2197,7 +2166,7 @@ int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* 
     cudaStream_t st = (cudaStream_t)stream;
     const Grid gg = make_grid(*g);
     const size_t hw = (size_t)g->H * g->W;
-    int r = net_capacity(s, (size_t)std::min(n, kNetMaxImg) * hw);
+    int r = SF_OK;
     for (int k0 = 0; k0 < n && !r; k0 += kNetMaxImg) {            // kNetMaxImg images per launch
         const int m = std::min(kNetMaxImg, n - k0);
         const float4* in[kNetMaxImg];
@@ -2206,7 +2175,7 @@ int sf_surrogate_forward(sf_surrogate* s, const sf_grid* g, int n, const float* 
             in[k] = (const float4*)s0 + (size_t)(k0 + k) * hw;
             out[k] = (float4*)p0 + (size_t)(k0 + k) * hw;
         }
-        r = net_forward(s, gg, m, in, out, s->xnet, st);
+        r = net_forward(s, gg, m, in, out, st);
     }
     return r;
 }
@@ -2326,24 +2295,12 @@ int engine_attach(Engine& E, sf_surrogate* s)
 {
     int r = SF_OK;
     if (s) {
-        size_t mx = 0;
         bool same = true;
         const sf_grid& g0 = E.st[0].lv[E.st[0].L - 1].grid;
         for (auto& es : E.st) {
             const sf_grid& gt = es.lv[es.L - 1].grid;
-            mx = std::max(mx, (size_t)gt.H * gt.W);
             same = same && gt.H == g0.H && gt.W == g0.W && gt.fx == g0.fx && gt.fy == g0.fy && gt.cx == g0.cx &&
                    gt.cy == g0.cy;
-        }
-        // the features buffer of the fused forward belongs to the engine: captured
-        // graphs bake its address in, so it must outlive them
-        const size_t px = same ? (size_t)std::min((int)E.st.size(), kNetMaxImg) * mx : mx;
-        if (px > E.surr_x_px) {
-            cudaFree(E.surr_x);
-            E.surr_x = nullptr;
-            E.surr_x_px = 0;
-            if (cudaMalloc(&E.surr_x, px * kSurrIn * sizeof(__nv_bfloat16)) != cudaSuccess) { E.surr_x = nullptr; return SF_ENOMEM; }
-            E.surr_x_px = px;
         }
         E.surr_same_grid = same;
         // the kernels' shared-memory limits are raised here, outside any stream capture

@@ -52,26 +52,6 @@ __global__ void k_surr_features(Grid g, int n, const float4* __restrict__ s0, __
     }
 }
 
-// the same features for n images whose states are separate planes (the
-// fused forward of several streams), into one n x H x W x 16 tensor
-struct FeatImgs {
-    const float4* s0[kNetMaxImg];
-};
-
-__global__ void k_surr_features_list(Grid g, int n, FeatImgs im, __nv_bfloat16* __restrict__ x0)
-{
-    const size_t hw = (size_t)g.H * g.W, total = hw * n;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(p / hw), q = (int)(p % hw), i = q / g.W, j = q % g.W;
-        const Geo geo = pixel_geometry(g, i, j);
-        const float s = 1.0f / (kSurrFlowScale * pixel_dmu(geo));
-        const float4 f = im.s0[k][q];
-        uint4* o = reinterpret_cast<uint4*>(x0 + p * kSurrIn);
-        o[0] = make_uint4(pack_bf16x2(f.x * s, f.y * s), pack_bf16x2(f.z * s, f.w), pack_bf16x2(geo.ex, geo.ey), 0u);
-        o[1] = make_uint4(0u, 0u, 0u, 0u);
-    }
-}
-
 // network output (FP32, 16 channels) + state -> predicted state
 __global__ void k_surr_head(Grid g, int n, const float4* __restrict__ s0, const float* __restrict__ y32,
                             float4* __restrict__ p0)
@@ -177,8 +157,9 @@ __global__ void k_surr_maxdiff(Grid g, int n, const float4* __restrict__ a, cons
 // k_surr_net runs the four layers and the head for tiles of kNetValid output
 // columns of a strip of output rows, keeping the hidden activations on chip:
 // the layered form writes and reads 3 x 64 bytes of BF16 activations per
-// pixel and layer through HBM, this form reads the features (32 bytes) and the
-// state (16) and writes the prediction (16).
+// pixel and layer through HBM, this form reads the state (16 bytes; the
+// producer warp turns it into the features in shared memory, and the head
+// reads it again, mostly from L2) and writes the prediction (16).
 //
 // The three vertical taps share one operand: an input row q of a layer feeds
 // output rows q - 1, q, q + 1 (taps dy = 2, 1, 0), so one MMA per horizontal
@@ -195,7 +176,7 @@ __global__ void k_surr_maxdiff(Grid g, int n, const float4* __restrict__ a, cons
 // image: the next layer's zero padding), and zeroes its block, which row
 // x + 4 first reaches two steps later.  Per step t of a strip the MMA thread
 // issues layer l for its input row q_l = y_b - 4 - 3 l + t (layer 1 reads
-// the TMA ring of features, layer l > 1 the row that layer l - 1 completed
+// the ring of features, layer l > 1 the row that layer l - 1 completed
 // at step t - 2), so step t waits for the epilogue of step t - 2 only.
 // Layer 4's first four channels become the prediction (k_surr_head's
 // arithmetic).  Columns: layer l computes the 128 positions x0 - 5 + l + m
@@ -211,6 +192,7 @@ constexpr int kNetHR = 2;             // rows of each hidden layer's ring in sha
 constexpr int kNetStrip = 256;        // the longest strip of output rows (each strip pays a 14-step fill)
 constexpr int kNetThreads = 192;      // 4 epilogue warps, producer warp, MMA warp
 constexpr int kNetInRow = (kSurrIn / 8) * kConvSlots * 16;         // bytes of a staged input row
+constexpr int kNetFeatPerLane = (kConvSlots + 31) / 32;           // input slots per producer lane
 constexpr int kNetHidRow = (kSurrHidden / 8) * kConvSlots * 16;    // ... of a hidden row
 constexpr int kNetW1 = 9 * (kSurrIn / 8) * kSurrHidden * 16;
 constexpr int kNetW2 = 9 * (kSurrHidden / 8) * kSurrHidden * 16;
@@ -304,11 +286,11 @@ __device__ __forceinline__ uint32_t net_block_col(int l, int x)
                  : (uint32_t)(3 * kNetRing * kSurrHidden + blk * kSurrOut);
 }
 
-__global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant__ CUtensorMap xmap, NetArgs a)
+__global__ void __launch_bounds__(kNetThreads) k_surr_net(NetArgs a)
 {
     extern __shared__ __align__(16) unsigned char nsm[];
     const uint32_t raw = smem_u32(nsm);
-    const uint32_t base = (raw + 127u) & ~127u;                    // TMA destinations: 128-byte aligned
+    const uint32_t base = (raw + 127u) & ~127u;                    // operand rows: 128-byte aligned
     unsigned char* basep = nsm + (base - raw);
     const uint32_t ring_in = base;
     const uint32_t ring_h = ring_in + kNetIR * kNetInRow;          // 3 layers x kNetHR rows
@@ -339,13 +321,17 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
                                       (size_t)((2 - dy) * Co + co) * 16) = v;
         }
     }
+    // chunk 1 (channels 8..15) of every input slot: zero features, never rewritten
+    for (int k = tid; k < kNetIR * kConvSlots; k += kNetThreads)
+        *reinterpret_cast<uint4*>(basep + (size_t)(k / kConvSlots) * kNetInRow + (size_t)(kConvSlots + k % kConvSlots) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
     for (int k = tid; k < kNetBias; k += kNetThreads) {
         const int l = k < 3 * kSurrHidden ? k / kSurrHidden : 3;
         const int c = k - kSurrHidden * l;
         bias_s[k] = a.bias[l] ? a.bias[l][c] : 0.0f;
     }
     if (tid == 0) {
-        for (int s = 0; s < kNetIR; ++s) { mbar_init(in_full(s), 1); mbar_init(in_empty(s), 1); }
+        for (int s = 0; s < kNetIR; ++s) { mbar_init(in_full(s), 32); mbar_init(in_empty(s), 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(acc_full(b), 1); mbar_init(epi_done(b), 4 * 32); }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -387,32 +373,52 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(const __grid_constant_
     auto active = [](int l, int t, int S) { return t >= 4 * l && t < S + 8 + 2 * l; };
     constexpr int kTail = 14;
     if (warp == 4) {
-        // ---------------- producer: input rows y_b - 4 .. y_e + 3 of every strip
-        if (lane == 0) {
-            long long cnt = 0;
-            long long last_use[kNetIR];
-            for (int s = 0; s < kNetIR; ++s) last_use[s] = -1;
-            for (int u = blockIdx.x; u < n_units && !failed; u += gridDim.x) {
-                const int sy = u % strips_y, tx = (u / strips_y) % a.tiles_x, nn = u / (strips_y * a.tiles_x);
-                const int x0 = tx * kNetValid, y_b = sy * a.strip, S = min(H, y_b + a.strip) - y_b;
-                for (int r = 0; r < S + 8; ++r, ++cnt) {
-                    const int s = (int)(cnt % kNetIR);
-                    const long long use = cnt / kNetIR;
-                    if (use > 0 && !mbar_wait_or_abort(in_empty(s), (uint32_t)((use - 1) & 1), a.spin_limit, abort_flag)) {
-                        failed = true;
-                        break;
-                    }
-                    mbar_expect_tx(in_full(s), kNetInRow);
-                    for (int c = 0; c < kSurrIn / 8; ++c)
-                        tma_load_row_chunk(ring_in + (uint32_t)s * kNetInRow + (uint32_t)(c * kConvSlots * 16), &xmap,
-                                           8 * c, x0 - 5, y_b - 4 + r, nn, in_full(s));
-                    last_use[s] = use;
+        // ---------------- producer (the whole warp): the features of input rows y_b - 4 ..
+        // y_e + 3 of every strip, computed from the state into chunk 0 of a ring slot (the
+        // arithmetic of k_surr_features; chunk 1 holds zero channels only and was cleared
+        // once); slot p is pixel x0 - 5 + p, zero outside the image
+        long long cnt = 0;
+        for (int u = blockIdx.x; u < n_units && !failed; u += gridDim.x) {
+            const int sy = u % strips_y, tx = (u / strips_y) % a.tiles_x, nn = u / (strips_y * a.tiles_x);
+            const int x0 = tx * kNetValid, y_b = sy * a.strip, S = min(H, y_b + a.strip) - y_b;
+            const float4* __restrict__ st0 = a.s0[nn];
+            for (int r = 0; r < S + 8; ++r, ++cnt) {
+                const int s = (int)(cnt % kNetIR);
+                const long long use = cnt / kNetIR;
+                const int iy = y_b - 4 + r;
+                // my pixels' state, loaded before the wait for the slot
+                float4 f[kNetFeatPerLane];
+#pragma unroll
+                for (int k = 0; k < kNetFeatPerLane; ++k) {
+                    const int x = x0 - 5 + lane + 32 * k;
+                    const bool in = lane + 32 * k < kConvSlots && iy >= 0 && iy < H && x >= 0 && x < W;
+                    f[k] = in ? st0[(size_t)iy * W + x] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+                if (use > 0) {
+                    const bool ok =
+                        mbar_wait_or_abort(in_empty(s), (uint32_t)((use - 1) & 1), a.spin_limit, abort_flag);
+                    if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+                }
+                unsigned char* row = basep + (ring_in - base) + (size_t)s * kNetInRow;
+#pragma unroll
+                for (int k = 0; k < kNetFeatPerLane; ++k) {
+                    const int p = lane + 32 * k, x = x0 - 5 + p;
+                    if (p >= kConvSlots) continue;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (iy >= 0 && iy < H && x >= 0 && x < W) {
+                        const Geo geo = pixel_geometry(g, iy, x);
+                        const float sc = 1.0f / (kSurrFlowScale * pixel_dmu(geo));
+                        v = make_uint4(pack_bf16x2(f[k].x * sc, f[k].y * sc), pack_bf16x2(f[k].z * sc, f[k].w),
+                                       pack_bf16x2(geo.ex, geo.ey), 0u);
+                    }
+                    *reinterpret_cast<uint4*>(row + (size_t)p * 16) = v;
+                }
+                // the row is visible to the tensor cores once in_full completes
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_one(in_full(s));
             }
-            if (failed) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
-            for (int s = 0; s < kNetIR; ++s)
-                if (last_use[s] >= 0) mbar_wait(in_full(s), (uint32_t)(last_use[s] & 1), a.spin_limit);
         }
+        if (failed && lane == 0) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
     } else if (warp == 5) {
         // ---------------- MMA issuer
         if (lane == 0) {

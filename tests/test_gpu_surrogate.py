@@ -201,9 +201,10 @@ def test_filter_top_level_predicted_by_the_surrogate():
     torch.cuda.synchronize()
     ref = torch.cat([n0.permute(2, 0, 1), n1.permute(2, 0, 1)])
     assert torch.equal(got, ref)
-    # the fused surrogate (features, network), the fallback check (one plain
-    # step reduced to the residual, the gated plain propagation), solve, smoothing
-    assert filt.kernels_per_step() == 2 + 2 + 1 + 1
+    # the fused surrogate (features and network in one launch), the fallback check
+    # (one plain step reduced to the residual, the gated plain propagation), solve,
+    # smoothing
+    assert filt.kernels_per_step() == 1 + 2 + 1 + 1
     res, fell = filt.surrogate_stats()
     assert res > 0 and fell == 0
     # the residual is the stand-alone check's: the largest flow difference of the
