@@ -117,14 +117,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// TMEM buffer `buf` (output row yy) -> bias, ReLU, global memory
-// (bias: the layer's bias in registers, zero beyond Cout or without one)
+// zero 32 (X32) or 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+template <bool X32>
+__device__ __forceinline__ void tmem_zero(uint32_t taddr)
+{
+    const uint32_t z = 0u;
+    if constexpr (X32)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1};" ::"r"(taddr), "r"(z)
+            : "memory");
+}
+
+// TMEM block `buf` (output row yy; blocks Cout columns wide, 32 columns read,
+// the ones beyond Cout unused) -> bias, ReLU, global memory (bias: the layer's
+// bias in registers, zero beyond Cout or without one)
 __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int buf, int nn, int yy, int x0,
                                               const float* bias)
 {
     const int warp = threadIdx.x >> 5;
     float v[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * buf), v);
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a.Cout * buf), v);
     const int px = x0 + 32 * warp + (threadIdx.x & 31);
     if (px >= a.W) return;
     const size_t o = (((size_t)nn * a.H + yy) * a.W + px) * a.Cout;
@@ -251,11 +269,16 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
     const uint32_t drain_bar = bars + 8u * (uint32_t)(2 * kConvRing + 2 * kConvAcc);   // the issuer's last MMAs
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights: B_tap[n][k] at tap * (C8 Cout 16) + chunk * (Cout 16) + n * 16
+    // weights: tap (dy, dx) of output channel co as row n = (2 - dy) Cout + co of
+    // B_dx, at dx (C8 3 Cout 16) + chunk (3 Cout 16) + n 16: the three vertical
+    // taps side by side, so that one MMA of N = 3 Cout serves three output rows
+    const int NW = 3 * a.Cout;
     for (int idx = tid; idx < 9 * a.Cout * C8; idx += kConvWsThreads) {
-        const int c = idx % C8, n = (idx / C8) % a.Cout, tap = idx / (C8 * a.Cout);
-        const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.Cout + n) * a.Cin + 8 * c);
-        *reinterpret_cast<uint4*>(Bs + (size_t)tap * C8 * a.Cout * 16 + (size_t)c * a.Cout * 16 + n * 16) = v;
+        const int c = idx % C8, co = (idx / C8) % a.Cout, tap = idx / (C8 * a.Cout);
+        const int dy = tap / 3, dx = tap % 3;
+        const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.Cout + co) * a.Cin + 8 * c);
+        *reinterpret_cast<uint4*>(Bs + (size_t)dx * C8 * NW * 16 + (size_t)c * NW * 16 +
+                                  (size_t)((2 - dy) * a.Cout + co) * 16) = v;
     }
     if (tid == 0) {
         for (int s = 0; s < kConvRing; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
@@ -275,6 +298,19 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
+    // every accumulator block starts at zero (the MMAs only accumulate; the
+    // epilogue zeroes a block again once it has drained it)
+    if (warp < 4) {
+        for (int b = 0; b < kConvAcc; ++b) {
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a.Cout * b);
+            if (a.Cout == 32) tmem_zero<true>(ta);
+            else tmem_zero<false>(ta);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     volatile int* abort_flag = &s_abort;
     bool failed = false;
 
@@ -309,53 +345,61 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
                 if (last_use[s] >= 0) mbar_wait(full(s), (uint32_t)(last_use[s] & 1), a.spin_limit);
         }
     } else if (warp == 5) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: per input row r of a strip, one MMA per horizontal tap
+        // and 16-channel chunk into the blocks of the output rows r - 1, r, r + 1 that lie in
+        // the strip (B rows of their vertical taps), split in two where the ring wraps
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc_bf16(a.Cout);
+            const int Co = a.Cout, NW = 3 * Co;
             long long cnt = 0;        // input rows, as the producer counts them
-            long long row = 0;        // output rows issued (accumulator ring)
+            long long orow = 0;       // output rows of the earlier strips (the accumulator ring)
             for (int t = blockIdx.x; t < n_strips && !failed; t += gridDim.x) {
                 const int sy = t % strips_y;
                 const int y_begin = sy * a.strip, y_end = min(a.H, y_begin + a.strip);
-                const long long first = cnt;                 // counter of input row y_begin - 1
+                const long long first = cnt;
                 cnt += (y_end - y_begin) + 2;
-                auto slot_of = [&](int r) { return (int)((first + (r - (y_begin - 1))) % kConvRing); };
-                auto use_of = [&](int r) { return (first + (r - (y_begin - 1))) / kConvRing; };
-                auto wait_row = [&](int r) {
-                    return mbar_wait_or_abort(full(slot_of(r)), (uint32_t)(use_of(r) & 1), a.spin_limit, abort_flag);
-                };
-                if (!wait_row(y_begin - 1) || !wait_row(y_begin)) { failed = true; break; }
-                for (int y = y_begin; y < y_end; ++y, ++row) {
-                    if (!wait_row(y + 1)) { failed = true; break; }
-                    const int b = (int)(row % kConvAcc);
-                    if (row >= kConvAcc &&
-                        !mbar_wait_or_abort(acc_empty(b), (uint32_t)(((row / kConvAcc) - 1) & 1), a.spin_limit,
-                                            abort_flag)) {
+                auto seq = [&](int y) { return orow + (y - y_begin); };   // ring position of output row y
+                for (int r = y_begin - 1; r <= y_end; ++r) {
+                    const long long ci = first + (r - (y_begin - 1));
+                    const int s = (int)(ci % kConvRing);
+                    if (!mbar_wait_or_abort(full(s), (uint32_t)((ci / kConvRing) & 1), a.spin_limit, abort_flag)) {
                         failed = true;
                         break;
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    if (!a.no_commit) {
-                        int first_mma = 1;
-                        for (int tap = 0; tap < 9; ++tap) {
-                            const int dy = tap / 3, dx = tap % 3;
-                            const uint32_t row_base = ring + (uint32_t)slot_of(y + dy - 1) * row_bytes;
-                            for (int k2 = 0; k2 < C8 / 2; ++k2) {
-                                const uint32_t aa = row_base + (uint32_t)(2 * k2 * kConvSlots * 16 + dx * 16);
-                                const uint32_t bb = b_base + (uint32_t)(tap * C8 * a.Cout * 16 + 2 * k2 * a.Cout * 16);
-                                umma_bf16(tmem + (uint32_t)(kConvTmemCols * b), umma_desc(aa, kConvSlots * 16, 128),
-                                          umma_desc(bb, a.Cout * 16, 128), idesc, first_mma ? 0 : 1);
-                                first_mma = 0;
-                            }
-                        }
-                        umma_commit(acc_full(b));
-                        umma_commit(empty(slot_of(y - 1)));          // row y - 1: this was its last reader
-                        if (y == y_end - 1) {                        // the strip's last two rows
-                            umma_commit(empty(slot_of(y)));
-                            umma_commit(empty(slot_of(y + 1)));
+                    // the row this input row starts (r + 1) reuses a block: drained and zeroed?
+                    if (r + 1 < y_end) {
+                        const long long q = seq(r + 1);
+                        if (q >= kConvAcc &&
+                            !mbar_wait_or_abort(acc_empty((int)(q % kConvAcc)), (uint32_t)(((q / kConvAcc) - 1) & 1),
+                                                a.spin_limit, abort_flag)) {
+                            failed = true;
+                            break;
                         }
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (!a.no_commit) {
+                        const int lo = max(r - 1, y_begin), hi = min(r + 1, y_end - 1);   // output rows fed
+                        const int nb = hi - lo + 1;                                     // 1 .. 3 blocks
+                        const int brow = (lo - (r - 1)) * Co;                           // their B rows
+                        const int fb = (int)(seq(lo) % kConvAcc);
+                        const int nb0 = min(nb, kConvAcc - fb);
+                        const int n0 = nb0 * Co, n1 = (nb - nb0) * Co;
+                        const uint32_t id0 = umma_idesc_bf16(n0), id1 = umma_idesc_bf16(n1 ? n1 : 16);
+                        const uint32_t row_base = ring + (uint32_t)s * row_bytes;
+                        for (int dx = 0; dx < 3; ++dx) {
+                            for (int k2 = 0; k2 < C8 / 2; ++k2) {
+                                const uint32_t aa = row_base + (uint32_t)(2 * k2 * kConvSlots * 16 + dx * 16);
+                                const uint32_t bb = b_base + (uint32_t)((dx * C8 + 2 * k2) * NW * 16 + brow * 16);
+                                const uint64_t ad = umma_desc(aa, kConvSlots * 16, 128);
+                                umma_bf16(tmem + (uint32_t)(Co * fb), ad, umma_desc(bb, NW * 16, 128), id0, 1);
+                                if (n1)
+                                    umma_bf16(tmem, ad, umma_desc(bb + (uint32_t)(n0 * 16), NW * 16, 128), id1, 1);
+                            }
+                        }
+                        umma_commit(empty(s));                                // input row r: this was its reader
+                        if (r - 1 >= y_begin) umma_commit(acc_full((int)(seq(r - 1) % kConvAcc)));   // row r - 1 done
+                    }
                 }
+                orow += y_end - y_begin;
             }
             if (failed) { *abort_flag = 1; if (a.status) atomicOr(a.status, kStatusTimeout); }
             // every MMA this thread issued has completed before the tensor memory is freed
@@ -378,6 +422,11 @@ __global__ void __launch_bounds__(kConvWsThreads) k_conv3x3(const __grid_constan
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 conv_epilogue(a, tmem, b, nn, y, x0, bias);
+                // the block starts the row kConvAcc rows on at zero
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a.Cout * b);
+                if (a.Cout == 32) tmem_zero<true>(ta);
+                else tmem_zero<false>(ta);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive_one(acc_empty(b));
             }

@@ -261,23 +261,6 @@ __device__ __forceinline__ void tmem_ld_bind4(uint32_t* r)
     asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
 }
 
-// zero 32 (X32) or 16 consecutive FP32 columns of this warp's 32 TMEM lanes
-template <bool X32>
-__device__ __forceinline__ void tmem_zero(uint32_t taddr)
-{
-    const uint32_t z = 0u;
-    if constexpr (X32)
-        asm volatile(
-            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-            "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
-            : "memory");
-    else
-        asm volatile(
-            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-            "%1};" ::"r"(taddr), "r"(z)
-            : "memory");
-}
-
 // TMEM column of layer l's block for row x (4 blocks of Cout columns per layer)
 __device__ __forceinline__ uint32_t net_block_col(int l, int x)
 {
