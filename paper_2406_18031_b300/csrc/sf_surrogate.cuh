@@ -193,6 +193,7 @@ constexpr int kNetStrip = 256;        // the longest strip of output rows (each 
 constexpr int kNetThreads = 192;      // 4 epilogue warps, producer warp, MMA warp
 constexpr int kNetInRow = (kSurrIn / 8) * kConvSlots * 16;         // bytes of a staged input row
 constexpr int kNetFeatPerLane = (kConvSlots + 31) / 32;           // input slots per producer lane
+static_assert(kSurrIn == 16, "the producer writes the features into chunk 0 and clears chunk 1 once");
 constexpr int kNetHidRow = (kSurrHidden / 8) * kConvSlots * 16;    // ... of a hidden row
 constexpr int kNetW1 = 9 * (kSurrIn / 8) * kSurrHidden * 16;
 constexpr int kNetW2 = 9 * (kSurrHidden / 8) * kSurrHidden * 16;
