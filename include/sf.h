@@ -457,6 +457,14 @@ int sf_conv3x3_wgrad(int N, int H, int W, int Cin, int Cout, const void* x, cons
  * device stays usable afterwards.  Waits for `stream`. */
 int sf_selftest_conv_timeout(void* stream);
 
+/* The same self-test for the fused surrogate network (sf_surrogate_forward's
+ * kernel): one 16 x 16 frame whose MMAs are never issued, so the epilogue's,
+ * the producer's and the MMA thread's bounded waits give up; the kernel sets
+ * the timeout bit, frees its tensor memory and returns.  Returns SF_ETIMEOUT
+ * when that happened (the expected outcome), SF_OK when a wait somehow
+ * completed, another code on a CUDA error.  Waits for `stream`. */
+int sf_selftest_net_timeout(void* stream);
+
 /* The surrogate network: 4 such layers, 16 -> 32 -> 32 -> 32 -> 16 channels,
  * ReLU after the first three.  Input features of a pixel of the top level:
  * w / (4 dmu) (3 channels, px/frame over 4), rho, eta_x, eta_y, 10 zeros;

@@ -2068,6 +2068,47 @@ int sf_selftest_conv_timeout(void* stream)
     return (s & kStatusTimeout) ? SF_ETIMEOUT : SF_OK;
 }
 
+int sf_selftest_net_timeout(void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    // one 16 x 16 frame, zero state and weights; the MMA thread issues nothing
+    const int H = 16, W = 16;
+    const size_t sb = (size_t)H * W * sizeof(float4);
+    const size_t wb = (size_t)(kNetW1 + 2 * kNetW2 + kNetW4);   // bytes of the four layers' BF16 weights
+    unsigned char* mem = nullptr;
+    if (cudaMallocAsync((void**)&mem, 2 * sb + wb + 256, st) != cudaSuccess) return SF_ENOMEM;
+    int r = cudaMemsetAsync(mem, 0, 2 * sb + wb + 256, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    sf_grid sg;
+    std::memset(&sg, 0, sizeof(sg));
+    sg.H = H; sg.W = W; sg.fx = sg.fy = 8.0f; sg.cx = sg.cy = 8.0f;
+    NetArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = make_grid(sg);
+    a.N = 1;
+    a.s0[0] = (const float4*)mem;
+    a.p0[0] = (float4*)(mem + sb);
+    a.w16[0] = (const __nv_bfloat16*)(mem + 2 * sb);
+    a.w16[1] = (const __nv_bfloat16*)(mem + 2 * sb + kNetW1);
+    a.w16[2] = (const __nv_bfloat16*)(mem + 2 * sb + kNetW1 + kNetW2);
+    a.w16[3] = (const __nv_bfloat16*)(mem + 2 * sb + kNetW1 + 2 * kNetW2);
+    a.tiles_x = 1;
+    a.strip = H;
+    a.status = (int*)(mem + 2 * sb + wb);
+    a.spin_limit = 1024;      // a short limit: the test ends in well under a second
+    a.no_commit = 1;          // nothing is issued, so the waits cannot complete
+    if (!r && set_smem_attr((const void*)k_surr_net, net_smem_bytes())) r = SF_ECUDA;
+    if (!r) {
+        k_surr_net<<<1, kNetThreads, net_smem_bytes(), st>>>(a);
+        r = last_error();
+    }
+    int s = 0;
+    if (!r) r = cudaMemcpyAsync(&s, a.status, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    cudaFreeAsync(mem, st);
+    if (!r) r = cudaStreamSynchronize(st) == cudaSuccess ? SF_OK : SF_ECUDA;
+    if (r) return r;
+    return (s & kStatusTimeout) ? SF_ETIMEOUT : SF_OK;
+}
+
 int sf_surrogate_create(unsigned long long seed, sf_surrogate** out)
 {
     if (!out) return SF_EINVAL;

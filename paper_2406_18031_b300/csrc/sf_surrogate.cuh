@@ -219,6 +219,7 @@ struct NetArgs {
     int tiles_x;                        // ceil(W / kNetValid)
     int strip;                          // output rows of a unit of work
     int spin_limit;
+    int no_commit;                      // self-test of the bounded waits: issue nothing, so no wait completes
     int* status;                        // bit kStatusTimeout when a bounded wait gave up (may be null)
 };
 
@@ -466,6 +467,7 @@ __global__ void __launch_bounds__(kNetThreads) k_surr_net(NetArgs a)
                             }
                         }
                     };
+                    if (a.no_commit) continue;
                     layer(std::integral_constant<int, 0>{});
                     layer(std::integral_constant<int, 1>{});
                     layer(std::integral_constant<int, 2>{});

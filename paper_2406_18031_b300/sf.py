@@ -47,7 +47,7 @@ EXPORTS = ["sf_params_default", "sf_create", "sf_reset", "sf_step", "sf_step_hos
            "sf_update", "sf_reconstruct", "sf_batch_create", "sf_batch_buffers", "sf_batch_step",
            "sf_batch_status", "sf_batch_launches_per_step", "sf_batch_nf_max", "sf_batch_update_mode", "sf_batch_solve_tile", "sf_batch_motion", "sf_batch_profile",
            "sf_batch_profile_read",
-           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_conv3x3_wgrad", "sf_selftest_conv_timeout", "sf_surrogate_create",
+           "sf_batch_destroy", "sf_remap_pinhole", "sf_remap_equirect", "sf_conv3x3", "sf_conv3x3_wgrad", "sf_selftest_conv_timeout", "sf_selftest_net_timeout", "sf_surrogate_create",
            "sf_surrogate_destroy", "sf_surrogate_num_params", "sf_surrogate_params", "sf_surrogate_grads",
            "sf_surrogate_forward", "sf_surrogate_forward_layered", "sf_surrogate_train_step", "sf_surrogate_propagate", "sf_set_surrogate",
            "sf_batch_set_surrogate", "sf_set_surrogate_threshold", "sf_batch_set_surrogate_threshold",
@@ -90,6 +90,7 @@ def lib():
         L.sf_conv3x3.argtypes = [i, i, i, i, i, vp, vp, vp, i, vp, vp, vp, vp]
         L.sf_conv3x3_wgrad.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
         L.sf_selftest_conv_timeout.argtypes = [vp]
+        L.sf_selftest_net_timeout.argtypes = [vp]
         L.sf_surrogate_create.argtypes = [ctypes.c_ulonglong, P(vp)]
         L.sf_surrogate_destroy.argtypes = [vp]
         L.sf_surrogate_destroy.restype = None
