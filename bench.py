@@ -925,7 +925,7 @@ def measure_surrogate(steps, dev, seq512):
         "flow_difference_px_after_timed_frames": {"mean": float(d.mean()), "max": float(d.max())},
         "epe_gap_vs_plain_px": out["surrogate"]["epe_vs_truth_px"] - out["plain"]["epe_vs_truth_px"],
         "tensor_tflops_in_surrogate": surrogate_flops_per_px() * px / (surr_ms / 1e3) / 1e12 if surr_ms else None,
-        "verdict": ("the surrogate-plus-batched form is faster than the plain GPU form"
+        "outcome": ("the surrogate-plus-batched form is faster than the plain GPU form"
                     if out["plain"]["ms_per_step"] > out["surrogate"]["ms_per_step"]
                     else "the surrogate-plus-batched form is slower than the plain GPU form"),
     }
