@@ -571,20 +571,24 @@ BATCH_SIZES = ((256, 16), (512, 32), (1024, 16))
 BATCH_FRAMES = 16        # frames per stream resident in HBM; also the period of the cameras' oscillation
 
 
-def measure_batch(steps, warmup, dev):
+def measure_batch(steps, warmup, dev, nf_max=0, update_mode=0, solve_tile=0):
     """Config 4: 64 independent streams (16 x 256^2 with 2 levels, 32 x 512^2
     and 16 x 1024^2 with 3 levels; peak flow just below 4 px/frame: N = [4, 2(, 1)],
     smoothing [2, 4(, 4)]) stepped together by one sf_batch.  The state
     (~4.5 GB) is far larger than L2, so no eviction is needed between steps;
     each step's inputs are copied into the batch's slots outside the timed
     events (16 rendered frames per stream: the cameras oscillate with a period
-    of 16 frames, so the sequence cycles without a jump)."""
+    of 16 frames, so the sequence cycles without a jump).  nf_max, update_mode
+    and solve_tile (0: the autotuner's choice) fix the launch configuration,
+    for profiling runs whose timings would mislead the autotuner."""
     import torch
     from paper_2406_18031_b300 import scenes, sf
     seqs = scenes.batch(frames=BATCH_FRAMES, sizes=BATCH_SIZES, period=BATCH_FRAMES)
     dt = seqs[0].dt
+    tuned = not (nf_max or update_mode or solve_tile)
     params = [sf.Params(fx=q.fx, fy=q.fy, cx=q.cx, cy=q.cy, iters=q.iters, smooth=q.smooth,
-                        flags=sf.CHECK_CFL | sf.AUTOTUNE) for q in seqs]
+                        flags=sf.CHECK_CFL | (sf.AUTOTUNE if tuned else 0), nf_max=nf_max or None,
+                        update_mode=update_mode or None, solve_tile=solve_tile or None) for q in seqs]
     batch = sf.Batch([q.shape for q in seqs], [q.levels for q in seqs], params)
     frames = [[(torch.from_numpy(q.image[f]).to(dev), torch.from_numpy(q.range[f]).to(dev))
                for f in range(BATCH_FRAMES)] for q in seqs]
@@ -630,7 +634,7 @@ def measure_batch(steps, warmup, dev):
                     "cameras oscillating with a 16-frame period, "
                     "N=[4,2(,1)], smooth=[2,4(,4)], plane scenes, 600 Hz",
         "streams": len(seqs), "mpx_per_step": px / 1e6, "nf_max": batch.nf_max(), "solve_tile": batch.solve_tile(),
-        "update_mode": batch.update_mode(), "autotune": True,
+        "update_mode": batch.update_mode(), "autotune": tuned,
         "frames_per_s_per_stream": 1.0 / step_s, "ms_per_step": step_s * 1e3,
         "stream_frames_per_s": len(seqs) / step_s, "mpx_per_s": px / step_s / 1e6,
         "hbm_gbs_algorithmic": frame_bytes / step_s / 1e9,
@@ -1256,7 +1260,7 @@ def run_batch_line(args):
     sfbuild.build()
     dev = torch.device("cuda", local)
     sampler = ClockSampler(local)
-    b = measure_batch(args.steps, args.warmup, dev)
+    b = measure_batch(args.steps, args.warmup, dev, args.nf_max, args.update_mode, args.solve_tile)
     clocks = sampler.stop()
     line = {"metric": METRIC, "value": b["frames_per_s_per_stream"], "unit": "frames/s per stream (64 streams)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
