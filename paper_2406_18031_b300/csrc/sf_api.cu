@@ -593,14 +593,165 @@ int engine_surr_plans(Engine& E, cudaStream_t st)
     return SF_OK;
 }
 
+// The propagation job of segment k (of nseg) of level h of stream s: the
+// last segment writes the prediction planes, earlier ones alternate with t0/t1
+// (so segments k - 1 and k + 1 share a buffer), the first reads the state of
+// the frame's parity and rescales w on load.
+PropJob make_prop_job(const EngineStream& s, const sf_level_state& lv, bool top, int k, int nseg, int nf)
+{
+    auto out_of = [&](int seg, float4*& o0, float4*& o1) {
+        const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
+        o0 = to_pred ? lv.p0 : lv.t0;
+        o1 = to_pred ? lv.p1 : lv.t1;
+    };
+    PropJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.g = make_grid(lv.grid);
+    if (k == 0) {
+        j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
+        j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
+        j.apply_wscale = 1;
+    } else {
+        float4 *o0, *o1;
+        out_of(k - 1, o0, o1);
+        j.in0[0] = j.in0[1] = o0;
+        j.in1[0] = j.in1[1] = top ? nullptr : o1;
+    }
+    out_of(k, j.out0, j.out1);
+    if (top) j.out1 = nullptr;
+    j.nf = nf;
+    j.dt = 1.0f / (float)lv.N;
+    j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
+    j.motion = s.motion;
+    return j;
+}
+
+// List schedule of the propagation of levels that need several segments.
+// Launch k of the segment-per-launch schedule holds segment k of every level;
+// a launch of more tiles than one wave leaves most SMs idle in its last wave
+// (384 x 1248 at 8 sub-iterations per segment: 208 tiles, two waves on 148
+// SMs, the second 40% full).  Here every (segment, tile) item goes into the
+// first launch with room (one wave of CTAs) after all launches holding an item
+// of the level's previous segment whose tile meets the item's region (values
+// it reads) or whose region meets the item's tile (values it overwrites:
+// segments k - 1 and k + 1 write the same buffer).  So within a launch no
+// item reads what another one writes, and items of later segments start while
+// the remaining tiles of earlier segments still run.  Used when it needs
+// fewer waves than the segment-per-launch schedule; returns false otherwise.
+bool engine_prop_list_schedule(Engine& E, cudaStream_t st, int& rc)
+{
+    const int nfmax = E.nf_max;
+    struct Seg { int s, h, k, nseg, nf, job, t0; };   // t0: first item of the segment
+    std::vector<Seg> segs;
+    std::vector<PropJob> jobs;
+    int nf_long = 0;
+    for (size_t si = 0; si < E.st.size(); ++si) {
+        const EngineStream& s = E.st[si];
+        for (int h = 0; h < s.L; ++h) {
+            if (h == s.L - 1 && E.surr) continue;
+            const int N = s.lv[h].N, nseg = ceil_div(N, nfmax);
+            for (int k = 0; k < nseg; ++k) {
+                const int nf = N / nseg + (k < N % nseg ? 1 : 0);
+                nf_long = std::max(nf_long, nf);
+                segs.push_back({(int)si, h, k, nseg, nf, (int)jobs.size(), 0});
+                jobs.push_back(make_prop_job(s, s.lv[h], h == s.L - 1, k, nseg, nf));
+            }
+        }
+    }
+    const int warps = prop_warps(nf_long);
+    const int cap = kSmCount * (warps == kPrWarpsMax ? 1 : 2);   // CTAs of one wave
+    // the waves of the segment-per-launch schedule (launch k's CTA shape set by
+    // its own longest job)
+    int waves_plain = 0, maxk = 0;
+    for (const Seg& g : segs) maxk = std::max(maxk, g.k);
+    if (maxk == 0) return false;
+    for (int k = 0; k <= maxk; ++k) {
+        int nfk = 0;
+        for (const Seg& g : segs)
+            if (g.k == k) nfk = std::max(nfk, g.nf);
+        const int wk = prop_warps(nfk);
+        long n = 0;
+        for (const Seg& g : segs)
+            if (g.k == k) {
+                const sf_level_state& lv = E.st[g.s].lv[g.h];
+                n += (long)ceil_div(lv.grid.H, prop_tile_h(g.nf, wk)) * ceil_div(lv.grid.W, prop_tile(g.nf));
+            }
+        const long capk = (long)kSmCount * (wk == kPrWarpsMax ? 1 : 2);
+        waves_plain += (int)((n + capk - 1) / capk);
+    }
+    // items in order of segment, then level and raster order; launch of each
+    std::vector<int4> item;        // (job, y0, x0, launch)
+    std::vector<int> load;
+    for (int k = 0; k <= maxk; ++k) {
+        for (size_t gi = 0; gi < segs.size(); ++gi) {
+            Seg& g = segs[gi];
+            if (g.k != k) continue;
+            const sf_level_state& lv = E.st[g.s].lv[g.h];
+            const int TW = prop_tile(g.nf), TH = prop_tile_h(g.nf, warps);
+            const Seg* pv = k ? &segs[gi - 1] : nullptr;   // the level's previous segment
+            const int PW = pv ? prop_tile(pv->nf) : 1, PH = pv ? prop_tile_h(pv->nf, warps) : 1;
+            const int ptx = pv ? ceil_div(lv.grid.W, PW) : 0, pty = pv ? ceil_div(lv.grid.H, PH) : 0;
+            g.t0 = (int)item.size();
+            for (int y0 = 0; y0 < lv.grid.H; y0 += TH)
+                for (int x0 = 0; x0 < lv.grid.W; x0 += TW) {
+                    int earliest = 0;
+                    if (pv) {
+                        const int m = std::max(g.nf, pv->nf);   // the item's tile grown by the larger halo
+                        const int ya = std::max(0, y0 - m), yb = std::min(lv.grid.H, y0 + TH + m) - 1;
+                        const int xa = std::max(0, x0 - m), xb = std::min(lv.grid.W, x0 + TW + m) - 1;
+                        for (int py = ya / PH; py <= std::min(pty - 1, yb / PH); ++py)
+                            for (int px = xa / PW; px <= std::min(ptx - 1, xb / PW); ++px)
+                                earliest = std::max(earliest, item[pv->t0 + py * ptx + px].w + 1);
+                    }
+                    int L = earliest;
+                    while (L < (int)load.size() && load[L] >= cap) ++L;
+                    if (L >= (int)load.size()) load.resize(L + 1, 0);
+                    ++load[L];
+                    item.push_back(make_int4(g.job, y0, x0, L));
+                }
+        }
+    }
+    if ((int)load.size() >= waves_plain) return false;
+    // one plan per launch: the launch's jobs (renumbered), longest tiles first
+    const int nl = (int)load.size();
+    E.prop.resize(nl);
+    for (int L = 0; L < nl && !rc; ++L) {
+        std::vector<PropJob> lj;
+        std::vector<int> map(jobs.size(), -1);
+        std::vector<int4> work;
+        bool c8 = false;
+        int nfl = 0;
+        for (int want = nfmax; want >= 1; --want)
+            for (const int4& it : item) {
+                if (it.w != L || jobs[it.x].nf != want) continue;
+                if (map[it.x] < 0) {
+                    map[it.x] = (int)lj.size();
+                    lj.push_back(jobs[it.x]);
+                    c8 |= jobs[it.x].out1 != nullptr;
+                    nfl = std::max(nfl, want);
+                }
+                work.push_back(make_int4(map[it.x], it.y, it.z, 0));
+            }
+        E.prop[L].c8 = c8;
+        E.prop[L].nf = nfl;
+        E.prop[L].warps = warps;
+        E.prop[L].smem = prop_smem_bytes(warps);
+        rc = upload_plan(lj, work, E.prop[L], st);
+    }
+    return true;
+}
+
 int engine_prop_plans(Engine& E, cudaStream_t st)
 {
     for (auto& pl : E.prop) free_plan(pl);
     E.prop.clear();
     const int nfmax = E.nf_max;
+    {
+        int rc = SF_OK;
+        if (engine_prop_list_schedule(E, st, rc)) return rc ? rc : engine_surr_plans(E, st);
+    }
     // ---- propagation: level h of stream s runs ceil(N / nfmax) launches;
-    // launch k holds segment k of every (stream, level) that has one.  The last
-    // segment writes the prediction planes, earlier ones alternate with t0/t1.
+    // launch k holds segment k of every (stream, level) that has one.
     int maxseg = 0;
     for (auto& s : E.st)
         for (int h = 0; h < s.L - (E.surr ? 1 : 0); ++h) maxseg = std::max(maxseg, ceil_div(s.lv[h].N, nfmax));
@@ -626,31 +777,7 @@ int engine_prop_plans(Engine& E, cudaStream_t st)
                     if (nf != want) continue;
                     const bool top = h == s.L - 1;
                     if (top && E.surr) continue;
-                    auto out_of = [&](int seg, float4*& o0, float4*& o1) {
-                        const bool to_pred = ((nseg - 1 - seg) % 2) == 0;
-                        o0 = to_pred ? lv.p0 : lv.t0;
-                        o1 = to_pred ? lv.p1 : lv.t1;
-                    };
-                    PropJob j;
-                    std::memset(&j, 0, sizeof(j));
-                    j.g = make_grid(lv.grid);
-                    if (k == 0) {
-                        j.in0[0] = lv.s0[0]; j.in0[1] = lv.s0[1];
-                        j.in1[0] = top ? nullptr : lv.s1[0]; j.in1[1] = top ? nullptr : lv.s1[1];
-                        j.apply_wscale = 1;
-                    } else {
-                        float4 *o0, *o1;
-                        out_of(k - 1, o0, o1);
-                        j.in0[0] = j.in0[1] = o0;
-                        j.in1[0] = j.in1[1] = top ? nullptr : o1;
-                    }
-                    out_of(k, j.out0, j.out1);
-                    if (top) j.out1 = nullptr;
-                    j.nf = nf;
-                    j.dt = 1.0f / (float)lv.N;
-                    j.tiles_x = ceil_div(lv.grid.W, prop_tile(nf));
-                    j.motion = s.motion;
-                    jobs.push_back(j);
+                    jobs.push_back(make_prop_job(s, lv, top, k, nseg, nf));
                     add_tiles(work, (int)jobs.size() - 1, lv.grid.H, lv.grid.W, prop_tile(nf), prop_tile_h(nf, warps));
                     c8 |= !top;
                 }

@@ -86,6 +86,25 @@ def test_propagation_split_into_launches(nf_max):
     assert filt[0].kernels_per_step() == -(-10 // nf_max) + 1 + 2
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("nf_max", [8, 4])
+def test_list_scheduled_propagation_full_size_driving(nf_max):
+    # 384 x 1248, N = [32, 16, 8]: at nf_max 8 a segment of level 1 has 208
+    # tiles (two waves of 16-warp CTAs on 148 SMs), so the propagation runs as
+    # a list schedule of one-wave launches (7 instead of 4 two-wave ones), later
+    # segments' tiles starting beside earlier segments' last tiles; at nf_max 4
+    # (8-warp CTAs, 368 tiles per level-1 segment) likewise.  Every pixel of
+    # three frames against the FP64 oracle.
+    seq = scenes.drive(frames=3)
+    filt = []
+    errs, _, _, st = _run(seq, 3, nf_max=nf_max, update_mode=1, filt=filt)
+    assert max(e for e, _ in errs) <= gu.FLOW_TOL_PX, errs
+    assert max(e for _, e in errs) <= gu.RHO_TOL
+    assert st >= 0
+    if nf_max == 8:
+        assert filt[0].kernels_per_step() == 7 + 1 + 3
+
+
 @pytest.mark.parametrize("solve_tile", [16, 32])
 @pytest.mark.parametrize("H,W,levels", [(128, 160, 2), (96, 312, 3), (40, 56, 2)])
 def test_solve_tile_edges_match_oracle(solve_tile, H, W, levels):
