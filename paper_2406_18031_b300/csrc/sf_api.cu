@@ -636,8 +636,9 @@ PropJob make_prop_job(const EngineStream& s, const sf_level_state& lv, bool top,
 // it reads) or whose region meets the item's tile (values it overwrites:
 // segments k - 1 and k + 1 write the same buffer).  So within a launch no
 // item reads what another one writes, and items of later segments start while
-// the remaining tiles of earlier segments still run.  Used when it needs
-// fewer waves than the segment-per-launch schedule; returns false otherwise.
+// the remaining tiles of earlier segments still run.  Used when its one-wave
+// launches come out ahead of the segment-per-launch schedule's waves, counting
+// a tenth of a wave per launch; returns false otherwise.
 bool engine_prop_list_schedule(Engine& E, cudaStream_t st, int& rc)
 {
     const int nfmax = E.nf_max;
@@ -711,7 +712,10 @@ bool engine_prop_list_schedule(Engine& E, cudaStream_t st, int& rc)
                 }
         }
     }
-    if ((int)load.size() >= waves_plain) return false;
+    // a launch costs about a tenth of a wave beyond its CTAs' work (its start and
+    // the drain of its last wave): keep the list schedule only where its waves
+    // and the extra launches together still come out ahead
+    if (11 * (int)load.size() >= 10 * waves_plain + (maxk + 1)) return false;
     // one plan per launch: the launch's jobs (renumbered), longest tiles first
     const int nl = (int)load.size();
     E.prop.resize(nl);
