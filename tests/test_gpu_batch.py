@@ -187,3 +187,51 @@ def test_batch_with_a_four_level_stream():
             assert e.max() <= gu.FLOW_TOL_PX, (k, s, e.max())
             assert np.abs(batch.slots[s][3].cpu().numpy() - outs[s][1].cpu().numpy()).max() <= gu.RHO_TOL
     assert batch.status() in (sf.OK, sf.WARN_CFL)
+
+
+@pytest.mark.slow
+def test_list_scheduled_batch_matches_single_stream_filters():
+    # A full-size driving stream (384 x 1248, N = [32, 16, 8]) and a full-size
+    # 512 x 512 stream (N = [8, 4]) in one batch: the driving levels' segments
+    # and the other stream's single segment are list-scheduled together into
+    # eight one-wave launches (1,096 tiles), while the single-stream filters
+    # run seven (driving) and one (512 x 512) launches.  Every tile computes
+    # the same arithmetic on the same inputs in either schedule, so the outputs
+    # agree bitwise; the driving stream is also held against the FP64 oracle.
+    # One frame time for both (the state is per frame: dt only scales the
+    # returned flow), the driving sequence's.
+    seqs = [scenes.drive(frames=3), scenes.scene512(frames=3)]
+    dt = seqs[0].dt
+
+    def params(seq):
+        return sf.Params(fx=seq.fx, fy=seq.fy, cx=seq.cx, cy=seq.cy, iters=seq.iters, smooth=seq.smooth,
+                         flags=sf.CHECK_CFL | sf.CHECK_FINITE, nf_max=8, update_mode=1, solve_tile=32)
+
+    batch = sf.Batch([s.shape for s in seqs], [s.levels for s in seqs], [params(s) for s in seqs])
+    singles = [sf.Filter(*s.shape, s.levels, params(s)) for s in seqs]
+    ref = oracle.Filter(*seqs[0].shape, seqs[0].levels,
+                        oracle.Params(seqs[0].fx, seqs[0].fy, seqs[0].cx, seqs[0].cy, iters=seqs[0].iters,
+                                      smooth=seqs[0].smooth))
+    _, _, dmu_ref = ref.geometry(0)
+    stream = torch.cuda.Stream()
+    outs = [(torch.empty((3, *s.shape), device="cuda"), torch.empty(s.shape, device="cuda")) for s in seqs]
+    for k in range(3):
+        with torch.cuda.stream(stream):
+            for s, seq in enumerate(seqs):
+                img, rng, _, _ = batch.slots[s]
+                img.copy_(torch.from_numpy(seq.image[k]).cuda())
+                rng.copy_(torch.from_numpy(seq.range[k]).cuda())
+                singles[s].step(torch.from_numpy(seq.image[k]).cuda(), torch.from_numpy(seq.range[k]).cuda(),
+                                dt, outs[s][0], outs[s][1], stream=stream)
+            batch.step(dt, stream=stream)
+        stream.synchronize()
+        for s in range(len(seqs)):
+            assert np.array_equal(batch.slots[s][2].cpu().numpy(), outs[s][0].cpu().numpy()), (k, s)
+            assert np.array_equal(batch.slots[s][3].cpu().numpy(), outs[s][1].cpu().numpy()), (k, s)
+        rf, _ = ref.step(seqs[0].image[k], seqs[0].range[k], dt)
+        e = np.abs(outs[0][0].cpu().numpy().astype(np.float64) - rf) * dt / dmu_ref[None]
+        assert e.max() <= gu.FLOW_TOL_PX, (k, e.max())
+    assert batch.launches_per_step() == 8 + 1 + 3          # eight one-wave propagation launches
+    assert singles[0].kernels_per_step() == 7 + 1 + 3
+    assert singles[1].kernels_per_step() == 1 + 1 + 2
+    assert batch.status() in (sf.OK, sf.WARN_CFL)
